@@ -1,0 +1,72 @@
+"""Oracle: D-optimality active set, MaxVol and the extrapolation grade (Sec. 2.3, Eq. 13).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+The paper fixes:
+  * b_alpha(cfg) = sum_i B_alpha(n_i); the rows b(cfg_k) stack into the tall matrix B (Eq. 13);
+  * the active set is the m rows of B whose m x m submatrix A has maximal |det A|;
+  * for a row b, c = b A^{-1} and gamma = max_j |c_j|; if gamma > 1 the row replaces row
+    argmax_j |c_j| of A and |det A| grows (the MaxVol step, Goreinov et al. 2010);
+  * if the active set is also the training set, the fitted xi reproduces the active energies
+    and then E(cfg) = sum_j c_j E(cfg_j) for any cfg.  The paper prints xi = (E_1 .. E_m) A^{-1};
+    the identity holds for the xi that solves A xi = (E_1 .. E_m)^T, which is how it is read here.
+
+Readings where the paper is silent (each stated in the design notes):
+  * start: the m pivot rows of Gaussian elimination with partial pivoting on B;
+  * a sweep computes C = B A^{-1} for every row, takes the largest |C_kj| (ties: the first in
+    row-major order, i.e. smallest row k, then smallest column j) and swaps while it exceeds
+    1 + tol (tol = 1e-9);
+  * at most max_iter = 100 m swaps.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+
+
+def b_rows(b_atoms, cfg_off):
+    """b(cfg_k) = sum of the per-atom basis rows of the atoms of configuration k (Sec. 2.3)."""
+    b_atoms = np.asarray(b_atoms, dtype=np.float64)
+    out = np.zeros((len(cfg_off) - 1, b_atoms.shape[1]))
+    for k in range(len(cfg_off) - 1):
+        out[k] = b_atoms[cfg_off[k]:cfg_off[k + 1]].sum(0)
+    return out
+
+
+def pivot_rows(B):
+    """Row indices chosen as pivots by LU with partial pivoting, in pivot order."""
+    B = np.asarray(B, dtype=np.float64)
+    m = B.shape[1]
+    perm, _, _ = scipy.linalg.lu(B, p_indices=True)
+    return np.asarray(perm[:m], dtype=np.int64)
+
+
+def maxvol(B, tol=1e-9, max_iter=None):
+    """Active set of m rows of the tall matrix B.  Returns (rows [m], swaps, final max |C|)."""
+    B = np.asarray(B, dtype=np.float64)
+    K, m = B.shape
+    if K < m:
+        raise ValueError("need at least m rows")
+    sel = pivot_rows(B)
+    if abs(np.linalg.det(B[sel])) == 0.0:
+        raise np.linalg.LinAlgError("singular start")
+    max_iter = 100 * m if max_iter is None else max_iter
+    swaps = 0
+    while True:
+        C = B @ np.linalg.inv(B[sel])
+        flat = int(np.argmax(np.abs(C)))
+        k, j = divmod(flat, m)
+        g = abs(C[k, j])
+        if g <= 1.0 + tol:
+            return sel, swaps, g
+        if swaps >= max_iter:
+            raise RuntimeError("maxvol did not converge")
+        sel[j] = k
+        swaps += 1
+
+
+def grades(B_rows, A):
+    """gamma = max_j |(b A^{-1})_j| for every row b (Sec. 2.3)."""
+    C = np.asarray(B_rows, dtype=np.float64) @ np.linalg.inv(np.asarray(A, dtype=np.float64))
+    return np.abs(C).max(axis=1)
