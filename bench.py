@@ -1,0 +1,303 @@
+"""Throughput of the MTP evaluation hot path on GB300.
+
+Workload (default): periodic fcc 16x16x16 supercell, 16,384 atoms, two species at random 50/50
+occupancy, Gaussian displacements sigma = 0.15 Angstrom, lev_max = 16, N_Q = 8, R_min = 2,
+R_cut = 5 Angstrom, random parameters (synthetic stand-in for the paper's DFT datasets).
+One step = neighbour search + energy, forces and virial (every kernel of the path), FP32 path.
+Metric: atoms/s (higher is better).  L2 is flushed (a 512 MiB write) between timed steps.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload (an 8x8x8 cell cut with the same recipe), as the reference arm.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MTP E+F+stress atoms/s at lev_max 16/20, FP32 batched vs FP64 path, same GB300"
+WORKLOAD = "fcc16^3 binary, 16384 atoms, lev_max=16, N_Q=8, R_cut=5"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lev", type=int, default=16)
+    ap.add_argument("--reps", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs(lev, reps, seed_offset=0):
+    from paper_2007_08555_gb300 import codegen, synth
+
+    cfg = synth.fcc_binary(reps=reps, seed=2 + seed_offset)
+    m = codegen.build_basis(lev).m
+    p = synth.random_params(lev, 2, 8, 2.0, 5.0, m, seed=2)
+    return cfg, p
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, nm in enumerate(names):
+                if "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2007_08555_gb300 import flops, mtp
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    cfg, p = make_inputs(args.lev, args.reps, seed_offset=rank)
+    n = cfg.n
+    dev = "cuda"
+    pos = torch.as_tensor(cfg.pos, dtype=torch.float64, device=dev)
+    types = torch.as_tensor(cfg.types, dtype=torch.int32, device=dev)
+    cells = torch.as_tensor(cfg.cell.reshape(1, 3, 3), dtype=torch.float64, device=dev)
+    off = torch.tensor([0, n], dtype=torch.int32, device=dev)
+    model = mtp.Model.from_params(p, "fp32")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(m):
+        return m.eval_batch(pos, types, cells, off)
+
+    for _ in range(args.warmup):
+        step(model)
+    torch.cuda.synchronize()
+    # neighbour pairs (for the algorithmic flop count)
+    counts, _, _, _ = model.neighbors(pos, cells, off)
+    n_pairs = int(counts.sum().item())
+    fl = flops.per_evaluation(args.lev, 8, n, n_pairs)
+
+    clocks = Clocks(local)
+    mtp.mtp_profile(model.h, True)
+    launches0 = model.launch_count
+    times = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(model)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    launches = model.launch_count - launches0
+    phase_ms, calls = mtp.mtp_profile_read(model.h)
+    mtp.mtp_profile(model.h, False)
+    ms = float(np.mean(times))
+    t_tot = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_tot, op=dist.ReduceOp.MAX)
+    ms_max = float(t_tot.item())
+    value = world * n / (ms_max * 1e-3)
+
+    # FP64 path on the same GPU (the speedup baseline)
+    model64 = mtp.Model.from_params(p, "fp64")
+    for _ in range(2):
+        step(model64)
+    torch.cuda.synchronize()
+    t64 = []
+    for _ in range(max(3, args.steps // 4)):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(model64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64.append(e0.elapsed_time(e1))
+    fp64_value = n / (np.mean(t64) * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    h_pos = torch.as_tensor(cfg.pos, dtype=torch.float64).pin_memory()
+    h_types = torch.as_tensor(cfg.types, dtype=torch.int32).pin_memory()
+    h_cells = torch.as_tensor(cfg.cell.reshape(1, 9), dtype=torch.float64).pin_memory()
+    h_off = torch.tensor([0, n], dtype=torch.int32).pin_memory()
+    h_e = torch.zeros(1, dtype=torch.float64).pin_memory()
+    h_f = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    h_w = torch.zeros((1, 9), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        mtp.mtp_eval_batch(model.h, 1, n, h_off, h_pos, h_types, h_cells, h_e, h_f, h_w,
+                           flags=mtp.HOST_MEMORY, stream=stream)
+
+    for _ in range(2):
+        e2e_step()
+    te = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        te.append(time.perf_counter() - t0)
+    e2e_value = n / float(np.mean(te))
+    h2d = h_pos.numel() * 8 + h_types.numel() * 4 + h_cells.numel() * 8 + h_off.numel() * 4
+    d2h = h_e.numel() * 8 + h_f.numel() * 8 + h_w.numel() * 8
+
+    # roofline of the dominant kernel phase
+    per_call = {k: v / max(calls, 1) for k, v in phase_ms.items()}
+    kern = {k: per_call[k] for k in ("moments", "contract", "pairgrad", "gather")}
+    dom = max(kern, key=kern.get)
+    peak = flops.fp32_peak_tflops()
+    achieved = fl[dom] / (kern[dom] * 1e-3) / 1e12
+    total_flops = sum(fl.values())
+    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_note": "FP32 FMA peak derived: 152 SM x 128 lanes x 2 flop x 2.07 GHz",
+                "path_frac": round(total_flops / (ms * 1e-3) / 1e12 / peak, 4)}
+    out = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(args.lev)
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": "atoms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.reps == 16 and args.lev == 16 else
+                       f"fcc{args.reps}^3 binary, {n} atoms, lev_max={args.lev}",
+                       "n_atoms": n, "n_pairs": n_pairs, "lev_max": args.lev, "l2": "flushed between steps (512 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": round(e2e_value, 1), "unit": "atoms/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": roofline,
+            "phases_ms": {k: round(v, 5) for k, v in per_call.items()},
+            "fp64_path": {"value": round(fp64_value, 1), "unit": "atoms/s", "speedup_fp32_over_fp64": round(value / world / fp64_value, 2)},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(lev, reps=16):
+    """The FP64 oracle as it stands, all host cores, one evaluation of the workload itself."""
+    import oracle
+
+    cfg, p = make_inputs(lev, reps)
+    pot = oracle.Potential(p)
+    t0 = time.perf_counter()
+    pot.eval(cfg)
+    dt = time.perf_counter() - t0
+    return {"value": round(cfg.n / dt, 2), "unit": "atoms/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one E+F+W evaluation of the fcc {reps}^3 cell ({cfg.n} atoms), lev_max={lev}"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    cfg, p = make_inputs(args.lev, 8)
+    pot = oracle.Potential(p)
+    for _ in range(max(0, min(args.warmup, 1))):
+        pot.eval(cfg)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pot.eval(cfg)
+        times.append(time.perf_counter() - t0)
+    ms = float(np.mean(times)) * 1e3
+    value = cfg.n / (ms * 1e-3)
+    sample = f"fcc 8^3 cell ({cfg.n} atoms) cut with the same recipe, one E+F+W evaluation per step, lev_max={args.lev}"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "atoms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": round(value, 2), "unit": "atoms/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 2), "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

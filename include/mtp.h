@@ -1,0 +1,168 @@
+/*
+ * mtp.h -- C ABI of the GB300 Moment Tensor Potential library (libmtp.so).
+ *
+ * Method: "The MLIP package: Moment Tensor Potentials with MPI and Active Learning",
+ * arXiv:2007.08555, Sec. 2.  Every entry point cites the passage that defines what it computes.
+ *
+ * Conventions (all entry points)
+ *   - Units: Angstrom, eV, eV/Angstrom.  The virial W = -dE/d(eps) (eV, extensive, row-major
+ *     3x3) is returned instead of the stress; stress in GPa is -W / volume * 160.21766.
+ *   - A cell is given by its three lattice vectors as rows: cell[3*k + d] = component d of a_k.
+ *     Positions need not lie inside the cell (they are used as given for r_ij = x_j + s H - x_i).
+ *   - Species indices are 0 .. n_species-1; anything else is MTP_EINVAL.
+ *   - Batches are CSR over configurations: the atoms of configuration k are
+ *     cfg_off[k] .. cfg_off[k+1]-1 (cfg_off[0] = 0, non-decreasing).
+ *   - Pointers are device pointers unless flags contains MTP_HOST_MEMORY, in which case every
+ *     array argument of that call is host memory (pinned memory makes the copies asynchronous).
+ *     The caller owns every array argument; the library owns the model, its device scratch and
+ *     its active set.  Output arrays that may be NULL are skipped when NULL.
+ *   - Calls are ordered on the CUDA stream passed as `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream).  Without MTP_ASYNC a call synchronises that stream before it
+ *     returns and reports device-detected errors in its status; with MTP_ASYNC it returns after
+ *     enqueueing and device-detected errors are reported by the next mtp_sync().
+ *   - No C++ exception crosses this boundary; every call returns an mtp_status.
+ *   - A model is not thread-safe: calls on one model must not overlap (they share scratch).
+ */
+#ifndef MTP_H
+#define MTP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mtp_model mtp_model;
+
+typedef enum {
+    MTP_OK = 0,
+    MTP_EINVAL = 1,        /* invalid argument (size, species index, level, null pointer) */
+    MTP_ENOMEM = 2,        /* device allocation failed */
+    MTP_ECUDA = 3,         /* a CUDA runtime call failed */
+    MTP_EOVERFLOW = 4,     /* an atom has more neighbours than the list capacity */
+    MTP_ESINGULAR = 5,     /* the active-set matrix is singular */
+    MTP_ETIMEOUT = 6,      /* an iteration limit was reached (MaxVol swaps) */
+    MTP_ENOACTIVESET = 7,  /* grades requested but no active set has been built */
+    MTP_EUNSUPPORTED = 8   /* valid request that this build does not support */
+} mtp_status;
+
+typedef enum {
+    MTP_FP64 = 0,  /* every step in double precision */
+    MTP_FP32 = 1   /* pair geometry, radial basis, moments, contractions and adjoint in float;
+                      per-configuration energy and virial sums in double */
+} mtp_precision;
+
+enum {
+    MTP_HOST_MEMORY = 1,      /* array arguments are host pointers */
+    MTP_ASYNC = 2,            /* do not synchronise the stream before returning */
+    MTP_REUSE_NEIGHBORS = 4   /* reuse the neighbour list of the previous call on this model
+                                 (same atoms, cfg_off and cells; positions may have moved) */
+};
+
+/* Human-readable name of a status code (static storage). */
+const char* mtp_status_str(mtp_status s);
+
+/*
+ * Create a potential (Sec. 2.1).
+ *   lev_max     maximum level of a basis function, Eq. 5 / Eq. 6; even, 2 <= lev_max <= 20
+ *               (basis levels are always even, an odd value is rounded down).
+ *   n_species   number of atomic types S (1..8).
+ *   n_radial    N_Q, the number of radial basis functions Q_b of Eq. 4 (1..16).
+ *   r_min, r_cut  the interval [R_min, R_cut] of the Chebyshev polynomials, Eq. 4; 0 <= r_min < r_cut.
+ *   xi          host array [m] of the linear coefficients of Eq. 2 in the order of
+ *               mtp_level_table(), or NULL for zeros.
+ *   c           host array [S][S][N_mu][N_Q] of the radial coefficients c_{mu,z_i,z_j}^{(b)} of
+ *               Eq. 3, first index z_i (the central atom), or NULL for zeros.
+ *   prec        MTP_FP64 or MTP_FP32.
+ *   out         receives the model; release it with mtp_destroy().
+ * Uses the current CUDA device.  Returns MTP_EINVAL for out-of-range arguments.
+ */
+mtp_status mtp_create(int lev_max, int n_species, int n_radial, double r_min, double r_cut, const double* xi,
+                      const double* c, mtp_precision prec, mtp_model** out);
+
+/* Release the model and all device memory it owns (NULL is allowed). */
+void mtp_destroy(mtp_model* model);
+
+/* m, the number of basis functions B_alpha (length of xi), Eq. 2. */
+int mtp_basis_count(const mtp_model* model);
+/* N_mu, the number of radial functions f_mu (Eq. 3): floor((lev_max - 2) / 4) + 1. */
+int mtp_radial_count(const mtp_model* model);
+/* C, the number of symmetric moment-tensor components stored per atom (Sec. 2.1). */
+int mtp_moment_count(const mtp_model* model);
+
+/*
+ * The canonical level table: the basis of Sec. 2.1 as loopless multigraphs (node = moment
+ * M_{mu,nu}, edge = one contracted index pair; a basis function is the product of its connected
+ * components).  Layout (int32): [m, then per basis function: level, n_components, then per
+ * component: n, mu_0, nu_0, ..., mu_{n-1}, nu_{n-1}, A[0][1], A[0][2], ..., A[n-2][n-1]].
+ * A component's node order is the one giving the lexicographically smallest such code;
+ * components are ordered by (level, n, code), basis functions by (level, total number of
+ * moments, ascending component numbers).  Writes min(cap, len) ints to buf (buf may be NULL)
+ * and the full length to *len.
+ */
+mtp_status mtp_level_table(const mtp_model* model, int32_t* buf, size_t cap, size_t* len);
+
+/* Replace theta = {xi, c} (host arrays, layouts as in mtp_create; NULL keeps the old value). */
+mtp_status mtp_set_params(mtp_model* model, const double* xi, const double* c);
+
+/* Capacity of the per-atom neighbour list (default 128).  MTP_EOVERFLOW reports the largest
+ * count seen through *max_seen of mtp_last_neighbor_max(). */
+mtp_status mtp_set_neighbor_capacity(mtp_model* model, int cap);
+int mtp_last_neighbor_max(const mtp_model* model);
+
+/*
+ * Neighbourhoods (Sec. 2.1, Eq. 1): for each atom i every (j, s), s an integer image shift, with
+ * |x_j + s H - x_i| < r_cut (strict), excluding (i, s = 0); skin adds to r_cut.  The decision is
+ * taken in double precision as d_k = (x_j[k] + ((s_0 H_0k + s_1 H_1k) + s_2 H_2k)) - x_i[k],
+ * r^2 = (d_0^2 + d_1^2) + d_2^2, without fused multiply-adds.  Lists are sorted by (j, s_0, s_1, s_2).
+ * Outputs (CSR over atoms): counts[n_atoms]; then, if nbr_j is not NULL, nbr_j[P], nbr_s[P][3] and
+ * r_ij[P][3] (double) with P = sum(counts) <= cap_pairs (else MTP_EOVERFLOW, counts still written).
+ * Shifts are limited to |s_k| <= 127 (positions more than ~120 cells outside their cell: MTP_EINVAL).
+ */
+mtp_status mtp_neighbors(mtp_model* model, int n_cfg, int n_atoms, const int32_t* cfg_off, const double* pos,
+                         const double* cells, double skin, int32_t* counts, int32_t* nbr_j, int32_t* nbr_s,
+                         double* r_ij, int64_t cap_pairs, int flags, void* stream);
+
+/*
+ * Energy, forces and virial of a batch of periodic configurations (Sec. 2.1, Eqs. 1-4):
+ *   E_k = sum_i V(n_i), V(n_i) = sum_alpha xi_alpha B_alpha(n_i),  F = -dE/dx,  W = -dE/d(eps).
+ * Inputs: n_cfg configurations, n_atoms atoms in total, cfg_off[n_cfg+1], pos[n_atoms][3],
+ * types[n_atoms], cells[n_cfg][9].
+ * Outputs (each may be NULL): energy[n_cfg], forces[n_atoms][3], virial[n_cfg][9],
+ *   site_energy[n_atoms] (V(n_i)), b_rows[n_cfg][m] (b_alpha(cfg) = sum_i B_alpha(n_i), Eq. 13),
+ *   b_atoms[n_atoms][m] (B_alpha(n_i)),
+ *   grade_cfg[n_cfg] (gamma = max_j |(b A^-1)_j|, Sec. 2.3) and grade_atom[n_atoms]
+ *   (max_j |(B(n_i) A^-1)_j|), both against the active set of mtp_select_active_set()
+ *   (MTP_ENOACTIVESET without one).
+ * flags: MTP_HOST_MEMORY, MTP_ASYNC, MTP_REUSE_NEIGHBORS.
+ */
+mtp_status mtp_eval_batch(mtp_model* model, int n_cfg, int n_atoms, const int32_t* cfg_off, const double* pos,
+                          const int32_t* types, const double* cells, double* energy, double* forces, double* virial,
+                          double* site_energy, double* b_rows, double* b_atoms, double* grade_cfg,
+                          double* grade_atom, int flags, void* stream);
+
+/* One configuration: mtp_eval_batch with n_cfg = 1 (cell[9], virial[9]). */
+mtp_status mtp_eval(mtp_model* model, int n_atoms, const double* pos, const int32_t* types, const double* cell,
+                    double* energy, double* forces, double* virial, double* site_energy, double* grade_cfg,
+                    double* grade_atom, int flags, void* stream);
+
+/* Wait for the model's work on `stream` and report errors detected on the device since the last
+ * check (MTP_EOVERFLOW, MTP_EINVAL for bad species or shifts). */
+mtp_status mtp_sync(mtp_model* model, void* stream);
+
+/* Number of kernel launches made by the model since creation (instrumentation). */
+int64_t mtp_launch_count(const mtp_model* model);
+
+/* Per-phase device timing (instrumentation).  While enabled, every synchronous evaluation records
+ * CUDA events on its stream around the neighbour build and the four evaluation kernels (moments,
+ * contraction, pair gradients, force/virial gather) and accumulates their elapsed times.
+ * mtp_profile() resets the accumulators; mtp_profile_read() writes up to n totals in
+ * milliseconds, in that order, and the number of evaluations accumulated. */
+mtp_status mtp_profile(mtp_model* model, int enable);
+mtp_status mtp_profile_read(const mtp_model* model, double* ms, int n, int64_t* calls);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTP_H */

@@ -1,0 +1,767 @@
+"""Build-time generator of the per-level tables and unrolled CUDA code of the MTP kernels.
+
+For a maximum level L it derives, from the basis definition of Sec. 2.1 (Eqs. 5-6):
+
+* the basis set: every scalar contraction of moments M_{mu,nu} (level 2 + 4 mu + nu) with total
+  level <= L, as loopless multigraphs (node = moment, edge = one contracted index pair),
+  products of connected contractions included;
+* the canonical level table (int32), in the order and format documented in include/mtp.h, so the
+  library's table can be compared bit for bit with an independent enumeration;
+* the moment components: for every moment in use, one entry per monomial x^a y^b z^c
+  (a + b + c = nu); symmetric storage of M_{mu,nu};
+* a contraction program: every connected contraction is evaluated as a sequence of pairwise
+  merges of sub-networks.  A merged sub-network S is a tensor whose open indices are grouped by
+  the node they belong to; inside a group the tensor is symmetric, so it is stored by monomial.
+  Merging S1 and S2 over the edge bundles (u in S1, v in S2, multiplicity h) sums, for every
+  bundle, over the monomials of degree h weighted by their multinomial count h!/(a! b! c!).
+  Every output entry is therefore a sum of terms  w * val[i] * val[j]  ("ops").  Identical
+  sub-networks are shared between contractions, merge orders are chosen by dynamic programming
+  over connected subsets to minimise the number of ops;
+* the ops arranged in dependency layers and spread over the 32 lanes of a warp, for the forward
+  and the adjoint (reverse-mode) pass;
+* unrolled per-slice code for the thread-per-atom moment and force kernels.
+
+Nothing here is shared with the test oracle; the canonical order is a documented convention.
+"""
+
+from __future__ import annotations
+
+import itertools
+import math
+import os
+from collections import defaultdict
+from dataclasses import dataclass, field
+
+SUPPORTED_LEVELS = tuple(range(2, 22, 2))
+WARP = 32
+
+
+def mlevel(mu, nu):
+    return 2 + 4 * mu + nu
+
+
+def monomials(g):
+    """Monomials (a, b, c) of degree g: a descending, then b descending."""
+    return [(a, b, g - a - b) for a in range(g, -1, -1) for b in range(g - a, -1, -1)]
+
+
+def mono_index(m):
+    a, b, c = m
+    g = a + b + c
+    return monomials(g).index(m)
+
+
+def n_monomials(g):
+    return (g + 1) * (g + 2) // 2
+
+
+def multinomial(m):
+    a, b, c = m
+    return math.factorial(a + b + c) // (math.factorial(a) * math.factorial(b) * math.factorial(c))
+
+
+# ---------------------------------------------------------------------------------------------
+# Basis enumeration (stub pairing + canonical code)
+# ---------------------------------------------------------------------------------------------
+def _code(labels, adj, order):
+    n = len(order)
+    out = [n]
+    for k in order:
+        out.extend(labels[k])
+    for x in range(n):
+        for y in range(x + 1, n):
+            out.append(adj[order[x]][order[y]])
+    return tuple(out)
+
+
+def canonical(labels, adj):
+    """(code, order): lexicographically smallest code over node orders.  Orders that do not sort
+    the labels ascending cannot win (labels precede the adjacency in the code)."""
+    n = len(labels)
+    by_label = defaultdict(list)
+    for k in range(n):
+        by_label[tuple(labels[k])].append(k)
+    keys = sorted(by_label)
+    best = None
+    for choice in itertools.product(*[list(itertools.permutations(by_label[k])) for k in keys]):
+        order = [x for part in choice for x in part]
+        code = _code(labels, adj, order)
+        if best is None or code < best[0]:
+            best = (code, order)
+    return best
+
+
+def _pairings(stubs, n):
+    """Yield adjacency matrices from matching node stubs pairwise (no loops), deduplicated."""
+    seen = set()
+
+    def rec(rest, adj):
+        if not rest:
+            key = tuple(tuple(r) for r in adj)
+            if key not in seen:
+                seen.add(key)
+                yield [r[:] for r in adj]
+            return
+        u = rest[0]
+        tried = set()
+        for k in range(1, len(rest)):
+            v = rest[k]
+            if v == u or v in tried:
+                continue
+            tried.add(v)
+            adj[u][v] += 1
+            adj[v][u] += 1
+            yield from rec(rest[1:k] + rest[k + 1:], adj)
+            adj[u][v] -= 1
+            adj[v][u] -= 1
+
+    yield from rec(stubs, [[0] * n for _ in range(n)])
+
+
+def _is_connected(adj):
+    n = len(adj)
+    seen, todo = {0}, [0]
+    while todo:
+        u = todo.pop()
+        for v in range(n):
+            if adj[u][v] and v not in seen:
+                seen.add(v)
+                todo.append(v)
+    return len(seen) == n
+
+
+def enumerate_components(L):
+    """Connected contractions with level <= L as {code: (labels, adj)} (labels/adj in canonical order)."""
+    comps = {}
+    for mu in range(L):
+        if mlevel(mu, 0) <= L:
+            comps[(1, mu, 0)] = ([(mu, 0)], [[0]])
+    pool = sorted((mu, nu) for mu in range(L) for nu in range(1, L) if mlevel(mu, nu) <= L)
+
+    def grow(start, labels, lev):
+        if len(labels) >= 2 and sum(nu for _, nu in labels) % 2 == 0:
+            stubs = [k for k, (_, nu) in enumerate(labels) for _ in range(nu)]
+            for adj in _pairings(stubs, len(labels)):
+                if _is_connected(adj):
+                    code, order = canonical(labels, adj)
+                    if code not in comps:
+                        comps[code] = ([labels[k] for k in order],
+                                       [[adj[order[x]][order[y]] for y in range(len(order))]
+                                        for x in range(len(order))])
+        for k in range(start, len(pool)):
+            if lev + mlevel(*pool[k]) <= L:
+                grow(k, labels + [pool[k]], lev + mlevel(*pool[k]))
+
+    grow(0, [], 0)
+    return comps
+
+
+@dataclass
+class Basis:
+    L: int
+    comps: list  # [(code, labels, adj, level)] sorted by (level, n, code)
+    funcs: list  # [(level, n_moments, tuple(component ids))] canonical order
+
+    @property
+    def m(self):
+        return len(self.funcs)
+
+
+def build_basis(L) -> Basis:
+    raw = enumerate_components(L)
+    comps = []
+    for code, (labels, adj) in raw.items():
+        comps.append((code, labels, adj, sum(mlevel(*x) for x in labels)))
+    comps.sort(key=lambda t: (t[3], len(t[1]), t[0]))
+    funcs = []
+    stack = [((), 0, 0, 0)]
+    while stack:
+        ids, lev, nm, start = stack.pop()
+        if ids:
+            funcs.append((lev, nm, ids))
+        for k in range(start, len(comps)):
+            if lev + comps[k][3] <= L:
+                stack.append((ids + (k,), lev + comps[k][3], nm + len(comps[k][1]), k))
+    funcs.sort()
+    return Basis(L, comps, funcs)
+
+
+def level_table(basis: Basis):
+    out = [basis.m]
+    for lev, _, ids in basis.funcs:
+        out += [lev, len(ids)]
+        for k in ids:
+            out += list(basis.comps[k][0])
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# Contraction program
+# ---------------------------------------------------------------------------------------------
+@dataclass
+class Program:
+    L: int
+    basis: Basis
+    moments: list  # used (mu, nu), sorted
+    comp_list: list  # moment components [(mu, (a, b, c))] in storage order
+    comp_index: dict  # (mu, (a,b,c)) -> index
+    n_values: int = 0
+    ops: list = field(default_factory=list)  # (k, i, j, w) in creation order
+    basis_value: list = field(default_factory=list)  # value index of each basis function
+    n_mu: int = 0
+    numax: int = 0
+
+
+class _Builder:
+    def __init__(self, basis: Basis):
+        self.basis = basis
+        L = basis.L
+        used = set()
+        for _, labels, _, _ in basis.comps:
+            used.update(tuple(x) for x in labels)
+        self.moments = sorted(used)
+        numax = max(nu for _, nu in self.moments)
+        n_mu = max(mu for mu, _ in self.moments) + 1
+        # components ordered by monomial (degree, index) then mu: a slice of monomials holds all
+        # of their radial channels
+        comp_list = []
+        for g in range(numax + 1):
+            for m in monomials(g):
+                for mu in range(n_mu):
+                    if (mu, g) in used:
+                        comp_list.append((mu, m))
+        self.prog = Program(L, basis, self.moments, comp_list, {c: k for k, c in enumerate(comp_list)},
+                            n_mu=n_mu, numax=numax)
+        self.n_values = len(comp_list)
+        self.ops = []
+        self.tensors = {}  # canonical key -> (order of nodes as (label, open) list, base index, group sizes)
+
+    # a sub-network: labels per node, internal adjacency, open index count per node
+    def _key(self, labels, adj, open_):
+        lab2 = [(labels[k][0], labels[k][1], open_[k]) for k in range(len(labels))]
+        code, order = canonical(lab2, adj)
+        return code, order
+
+    def _entries(self, open_):
+        size = 1
+        for g in open_:
+            if g > 0:
+                size *= n_monomials(g)
+        return size
+
+    def _entry_index(self, open_, monos):
+        """Mixed-radix index over the groups with g > 0 (first group most significant)."""
+        idx = 0
+        for g, m in zip(open_, monos):
+            if g > 0:
+                idx = idx * n_monomials(g) + mono_index(m)
+        return idx
+
+    def tensor(self, labels, adj, open_):
+        """Value base index of the (shared) tensor of a sub-network, building it if needed.
+        Returns (base, order) with order mapping canonical position -> local node."""
+        n = len(labels)
+        if n == 1:
+            return None, [0]
+        code, order = self._key(labels, adj, open_)
+        if code in self.tensors:
+            return self.tensors[code], order
+        raise KeyError(code)
+
+    def value_of(self, labels, adj, open_, order_base, monos_local):
+        """Value index of one entry of a sub-network tensor, monos given per local node."""
+        n = len(labels)
+        if n == 1:
+            return self.prog.comp_index[(labels[0][0], monos_local[0])]
+        base, order = order_base
+        open_c = [open_[k] for k in order]
+        monos_c = [monos_local[k] for k in order]
+        return base + self._entry_index(open_c, monos_c)
+
+    def build(self):
+        for code, labels, adj, lev in self.basis.comps:
+            if len(labels) > 1:
+                self._build_component(labels, adj)
+        comp_value = []
+        for code, labels, adj, lev in self.basis.comps:
+            if len(labels) == 1:
+                comp_value.append(self.prog.comp_index[(labels[0][0], (0, 0, 0))])
+            else:
+                base, _ = self.tensor(labels, adj, [0] * len(labels))
+                comp_value.append(base)
+        # basis functions: single components map to the component value; a product of k components
+        # is (the basis function of its first k-1 components) * (its last component)
+        func_value = {}
+        out = []
+        for lev, nm, ids in self.basis.funcs:
+            if len(ids) == 1:
+                v = comp_value[ids[0]]
+            else:
+                v = self.n_values
+                self.n_values += 1
+                self.ops.append((v, func_value[ids[:-1]], comp_value[ids[-1]], 1.0))
+            func_value[ids] = v
+            out.append(v)
+        self.prog.basis_value = out
+        self.prog.ops = self.ops
+        self.prog.n_values = self.n_values
+        return self.prog
+
+    # -- dynamic programme over connected subsets of one component --------------------------
+    def _build_component(self, labels, adj):
+        n = len(labels)
+        nu = [x[1] for x in labels]
+
+        def connected(S):
+            S = list(S)
+            seen, todo = {S[0]}, [S[0]]
+            while todo:
+                u = todo.pop()
+                for v in S:
+                    if adj[u][v] and v not in seen:
+                        seen.add(v)
+                        todo.append(v)
+            return len(seen) == len(S)
+
+        def sub(S):
+            S = sorted(S)
+            lab = [labels[u] for u in S]
+            a = [[adj[u][v] for v in S] for u in S]
+            op = [nu[u] - sum(adj[u][w] for w in S) for u in S]
+            return S, lab, a, op
+
+        memo = {}
+
+        def cost(S):
+            S = frozenset(S)
+            if len(S) == 1:
+                return 0, None
+            if S in memo:
+                return memo[S]
+            Sl, lab, a, op = sub(S)
+            code, _ = self._key(lab, a, op)
+            if code in self.tensors:
+                memo[S] = (0, None)
+                return memo[S]
+            best = None
+            first = min(S)
+            for r in range(1, len(S)):
+                for S1 in itertools.combinations(sorted(S), r):
+                    if first not in S1:
+                        continue
+                    S1 = frozenset(S1)
+                    S2 = S - S1
+                    if not connected(S1) or not connected(S2):
+                        continue
+                    if not any(adj[u][v] for u in S1 for v in S2):
+                        continue
+                    c = self._entries(op)
+                    for u in S1:
+                        for v in S2:
+                            if adj[u][v]:
+                                c *= n_monomials(adj[u][v])
+                    c1, _ = cost(S1)
+                    c2, _ = cost(S2)
+                    tot = c + c1 + c2
+                    if best is None or tot < best[0]:
+                        best = (tot, (S1, S2))
+            memo[S] = best
+            return best
+
+        def realise(S):
+            S = frozenset(S)
+            if len(S) == 1:
+                return
+            Sl, lab, a, op = sub(S)
+            code, order = self._key(lab, a, op)
+            if code in self.tensors:
+                return
+            _, split = cost(S)
+            S1, S2 = split
+            realise(S1)
+            realise(S2)
+            self._merge(Sl, lab, a, op, code, order, S1, S2, labels, adj)
+
+        cost(range(n))
+        realise(range(n))
+
+    def _merge(self, Sl, lab, a, op, code, order, S1, S2, labels, adj):
+        base = self.n_values
+        self.tensors[code] = base
+        size = self._entries(op)
+        self.n_values += size
+        nu = [x[1] for x in labels]
+        S1l, S2l = sorted(S1), sorted(S2)
+
+        def handle(Sx):
+            Sx_l = sorted(Sx)
+            lab_x = [labels[u] for u in Sx_l]
+            a_x = [[adj[u][v] for v in Sx_l] for u in Sx_l]
+            op_x = [nu[u] - sum(adj[u][w] for w in Sx_l) for u in Sx_l]
+            if len(Sx_l) == 1:
+                return Sx_l, lab_x, a_x, op_x, None
+            code_x, order_x = self._key(lab_x, a_x, op_x)
+            return Sx_l, lab_x, a_x, op_x, (self.tensors[code_x], order_x)
+
+        h1 = handle(S1)
+        h2 = handle(S2)
+        bundles = [(u, v, adj[u][v]) for u in S1l for v in S2l if adj[u][v]]
+        # output entries: canonical order of this tensor's groups
+        open_c = [op[k] for k in order]
+        nodes_c = [Sl[k] for k in order]
+        group_monos = [monomials(g) if g > 0 else [(0, 0, 0)] for g in open_c]
+        bundle_monos = [monomials(h) for (_, _, h) in bundles]
+        for out_monos in itertools.product(*group_monos):
+            out_of = dict(zip(nodes_c, out_monos))
+            k = base + self._entry_index(open_c, list(out_monos))
+            for bm in itertools.product(*bundle_monos):
+                w = 1
+                tot = {u: list(out_of[u]) for u in Sl}
+                for (u, v, h), m in zip(bundles, bm):
+                    w *= multinomial(m)
+                    for t in range(3):
+                        tot[u][t] += m[t]
+                        tot[v][t] += m[t]
+                i = self.value_of(h1[1], h1[2], h1[3], h1[4], [tuple(tot[u]) for u in h1[0]])
+                j = self.value_of(h2[1], h2[2], h2[3], h2[4], [tuple(tot[u]) for u in h2[0]])
+                self.ops.append((k, i, j, float(w)))
+
+
+def build_program(L) -> Program:
+    return _Builder(build_basis(L)).build()
+
+
+# ---------------------------------------------------------------------------------------------
+# Warp layout of the forward and adjoint programs
+# ---------------------------------------------------------------------------------------------
+def _lane_layers(groups_by_layer):
+    """groups_by_layer: list of layers, each a list of (target, [terms]).  Returns per layer a
+    list of 32 lane queues (longest-processing-time greedy)."""
+    out = []
+    for groups in groups_by_layer:
+        lanes = [[] for _ in range(WARP)]
+        load = [0] * WARP
+        for tgt, terms in sorted(groups, key=lambda g: -len(g[1])):
+            k = min(range(WARP), key=lambda x: load[x])
+            lanes[k].append((tgt, terms))
+            load[k] += len(terms)
+        out.append(lanes)
+    return out
+
+
+def forward_layout(prog: Program):
+    C = len(prog.comp_list)
+    depth = [0] * prog.n_values
+    by_k = defaultdict(list)
+    for (k, i, j, w) in prog.ops:
+        by_k[k].append((i, j, w))
+    for k in sorted(by_k):  # creation order is topological (inputs have smaller indices)
+        depth[k] = 1 + max(max(depth[i], depth[j]) for i, j, _ in by_k[k])
+    layers = defaultdict(list)
+    for k, terms in by_k.items():
+        layers[depth[k]].append((k, terms))
+    assert all(k >= C for k in by_k)
+    return _lane_layers([layers[d] for d in sorted(layers)])
+
+
+def adjoint_layout(prog: Program):
+    """Reverse pass: adj[t] = seed[t] + sum over ops consuming t of w * val[other] * adj[k]."""
+    contrib = defaultdict(list)
+    for (k, i, j, w) in prog.ops:
+        contrib[i].append((j, k, w))
+        contrib[j].append((i, k, w))
+    consumers = defaultdict(set)
+    for (k, i, j, w) in prog.ops:
+        consumers[i].add(k)
+        consumers[j].add(k)
+    rdepth = {}
+
+    def rd(v):
+        if v in rdepth:
+            return rdepth[v]
+        r = 0 if not consumers[v] else 1 + max(rd(k) for k in consumers[v])
+        rdepth[v] = r
+        return r
+
+    import sys
+    sys.setrecursionlimit(100000)
+    for v in range(prog.n_values - 1, -1, -1):
+        rd(v)
+    layers = defaultdict(list)
+    for t, terms in contrib.items():
+        layers[rdepth[t]].append((t, terms))
+    return _lane_layers([layers[d] for d in sorted(layers)])
+
+
+def encode_layout(layout):
+    """Flatten lanes into steps: rows of 32 entries (i, j, k, flags, w).
+    flags bit0: first term of a target (accumulator starts from the target's seed);
+          bit1: last term (store the accumulator); bit2: padding (no work)."""
+    rows = []
+    layer_rows = []
+    for lanes in layout:
+        start = len(rows)
+        seqs = []
+        for lane in lanes:
+            seq = []
+            for tgt, terms in lane:
+                for t, (a, b, w) in enumerate(terms):
+                    flags = (1 if t == 0 else 0) | (2 if t == len(terms) - 1 else 0)
+                    seq.append((a, b, tgt, flags, w))
+            seqs.append(seq)
+        steps = max((len(s) for s in seqs), default=0)
+        for s in range(steps):
+            row = []
+            for lane in range(WARP):
+                if s < len(seqs[lane]):
+                    row.append(seqs[lane][s])
+                else:
+                    row.append((0, 0, 0, 4, 0.0))
+            rows.append(row)
+        layer_rows.append((start, len(rows)))
+    return rows, layer_rows
+
+
+# ---------------------------------------------------------------------------------------------
+# Slices of the thread-per-atom kernels
+# ---------------------------------------------------------------------------------------------
+def slices(prog: Program, max_comps):
+    """Contiguous groups of monomials (with all their radial channels) of <= max_comps components."""
+    groups = []
+    cur, cur_n = [], 0
+    by_mono = defaultdict(list)
+    order = []
+    for idx, (mu, m) in enumerate(prog.comp_list):
+        if m not in by_mono:
+            order.append(m)
+        by_mono[m].append(idx)
+    for m in order:
+        k = len(by_mono[m])
+        if cur and cur_n + k > max_comps:
+            groups.append(cur)
+            cur, cur_n = [], 0
+        cur.append(m)
+        cur_n += k
+    if cur:
+        groups.append(cur)
+    return [(g, [i for m in g for i in by_mono[m]]) for g in groups]
+
+
+def _mono_name(m):
+    return "m%d_%d_%d" % m
+
+
+def _mono_code(needed, T):
+    """Statements computing every monomial in `needed` (closed under parents) from x, y, z."""
+    lines = []
+    done = {(0, 0, 0)}
+    for m in sorted(needed, key=lambda t: (sum(t), monomials(sum(t)).index(t))):
+        if m in done:
+            continue
+        a, b, c = m
+        if a > 0:
+            parent, var = (a - 1, b, c), "x"
+        elif b > 0:
+            parent, var = (a, b - 1, c), "y"
+        else:
+            parent, var = (a, b, c - 1), "z"
+        if parent == (0, 0, 0):
+            lines.append(f"const {T} {_mono_name(m)} = {var};")
+        else:
+            lines.append(f"const {T} {_mono_name(m)} = {_mono_name(parent)} * {var};")
+        done.add(m)
+    return lines
+
+
+def _closure(monos):
+    need = set()
+    for m in monos:
+        cur = m
+        while cur != (0, 0, 0):
+            need.add(cur)
+            a, b, c = cur
+            cur = (a - 1, b, c) if a > 0 else ((a, b - 1, c) if b > 0 else (a, b, c - 1))
+    return need
+
+
+def emit_slice_functions(prog: Program, slc, tag):
+    """Specialisations Slice<tag><S> for every slice S (a list of (monomials, component indices)):
+       mom(x,y,z,f,acc):   acc[t] += f[mu] * x^a y^b z^c                    (moments, Sec. 2.1)
+       grad(x,y,z,f,df,adj,s,gx,gy,gz):
+             s += sum adj * df[mu] * mono;  g += sum adj * f[mu] * grad(mono)   (adjoint)"""
+    name = "SliceF" if tag == "f" else "SliceD"
+    out = [f"template <int S> struct {name};"]
+    for si, (monos, comps) in enumerate(slc):
+        out.append(f"template <> struct {name}<{si}> {{")
+        out.append(f"  static constexpr int BEGIN = {min(comps)}, SIZE = {len(comps)};")
+        need = _closure(monos)
+        out.append("  template <class T> static __device__ __forceinline__ void mom(const T x, const T y, const T z, "
+                   "const T* __restrict__ f, T* __restrict__ acc) {")
+        out += ["    " + l for l in _mono_code(need, "T")]
+        for t, ci in enumerate(comps):
+            mu, m = prog.comp_list[ci]
+            mv = "T(1)" if m == (0, 0, 0) else _mono_name(m)
+            out.append(f"    acc[{t}] += f[{mu}] * {mv};")
+        out.append("  }")
+        grads = set()
+        for m in monos:
+            for k in range(3):
+                if m[k] > 0:
+                    mm = list(m)
+                    mm[k] -= 1
+                    grads.add(tuple(mm))
+        need = _closure(set(monos) | grads)
+        out.append("  template <class T> static __device__ __forceinline__ void grad(const T x, const T y, const T z, "
+                   "const T* __restrict__ f, const T* __restrict__ df, const T* __restrict__ adj, "
+                   "T& s, T& gx, T& gy, T& gz) {")
+        out += ["    " + l for l in _mono_code(need, "T")]
+        by_m = defaultdict(list)
+        for t, ci in enumerate(comps):
+            mu, m = prog.comp_list[ci]
+            by_m[m].append((t, mu))
+        for m in monos:
+            terms = by_m[m]
+            al = " + ".join(f"adj[{t}] * f[{mu}]" for t, mu in terms)
+            be = " + ".join(f"adj[{t}] * df[{mu}]" for t, mu in terms)
+            nm = "T(1)" if m == (0, 0, 0) else _mono_name(m)
+            out.append(f"    {{ const T al = {al}; const T be = {be};")
+            out.append(f"      s += be * {nm};")
+            for k, gv in enumerate(("gx", "gy", "gz")):
+                if m[k] > 0:
+                    mm = list(m)
+                    mm[k] -= 1
+                    mm = tuple(mm)
+                    src = "T(1)" if mm == (0, 0, 0) else _mono_name(mm)
+                    coef = "" if m[k] == 1 else f"T({m[k]}) * "
+                    out.append(f"      {gv} += {coef}al * {src};")
+            out.append("    }")
+        out.append("  }")
+        out.append("};")
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# Emission
+# ---------------------------------------------------------------------------------------------
+SLICE_F32 = 136
+SLICE_F64 = 64
+
+
+def flop_counts(prog: Program):
+    """Algorithmic floating-point operations of one atom (per pair and per atom parts)."""
+    C = len(prog.comp_list)
+    monos = {m for _, m in prog.comp_list}
+    n_mono = len([m for m in monos if m != (0, 0, 0)])
+    n_ops = len(prog.ops)
+    return {
+        "components": C,
+        "monomials": n_mono,
+        "program_ops": n_ops,
+        # per pair: moments 2C + monomials; adjoint: 4C (alpha, beta) + 2 per monomial (s) +
+        # 2 per nonzero gradient term + monomials; plus the geometry/radial terms added by the caller
+        "pair_moments": 2 * C + n_mono,
+        "pair_adjoint": 4 * C + 2 * n_mono + 2 * sum(sum(1 for k in range(3) if m[k] > 0) for m in monos)
+        + 2 * n_mono,
+        # per atom: forward 2 flops per op, adjoint 4 flops per op (two contributions of 2 flops)
+        "atom_program": 2 * n_ops + 4 * n_ops,
+    }
+
+
+def emit_level(L, outdir):
+    prog = build_program(L)
+    fwd_rows, fwd_layers = encode_layout(forward_layout(prog))
+    adj_rows, adj_layers = encode_layout(adjoint_layout(prog))
+    C = len(prog.comp_list)
+    V = prog.n_values
+    assert V < 65535
+    table = level_table(prog.basis)
+    s32 = slices(prog, SLICE_F32)
+    s64 = slices(prog, SLICE_F64)
+    fl = flop_counts(prog)
+    tag = f"L{L}"
+    lines = [f"// Generated by paper_2007_08555_gb300/codegen.py for lev_max = {L}. Do not edit.",
+             "#pragma once", "#include \"mtp_gen_common.h\"", f"namespace mtpgen_{tag} {{"]
+    lines.append(f"constexpr int L = {L}, C = {C}, V = {V}, M = {prog.basis.m}, NMU = {prog.n_mu}, "
+                 f"NUMAX = {prog.numax};")
+    lines.append(f"constexpr int NS32 = {len(s32)}, NS64 = {len(s64)};")
+    lines.append(f"constexpr int FWD_ROWS = {len(fwd_rows)}, ADJ_ROWS = {len(adj_rows)};")
+    lines.append(f"constexpr int FWD_LAYERS = {len(fwd_layers)}, ADJ_LAYERS = {len(adj_layers)};")
+    lines.append(f"constexpr int PROGRAM_OPS = {len(prog.ops)};")
+    lines.append(f"constexpr int FLOP_PAIR_MOMENTS = {fl['pair_moments']}, FLOP_PAIR_ADJOINT = {fl['pair_adjoint']}, "
+                 f"FLOP_ATOM_PROGRAM = {fl['atom_program']};")
+    lines.append("static const int level_table[] = {" + ",".join(map(str, table)) + "};")
+    lines.append(f"constexpr int LEVEL_TABLE_LEN = {len(table)};")
+    lines.append("static const int basis_value[] = {" + ",".join(map(str, prog.basis_value)) + "};")
+    lines.append("static const unsigned char comp_mu[] = {" + ",".join(str(mu) for mu, _ in prog.comp_list) + "};")
+    lines.append("static const unsigned char comp_abc[] = {" +
+                 ",".join(f"{a},{b},{c}" for _, (a, b, c) in prog.comp_list) + "};")
+
+    def rows_to_c(name, rows):
+        ij = []
+        kf = []
+        w = []
+        for row in rows:
+            for (a, b, k, f, ww) in row:
+                ij.append(f"{a | (b << 16)}u")
+                kf.append(f"{k | (f << 16)}u")
+                w.append(repr(float(ww)))
+        lines.append(f"static const unsigned {name}_ij[] = {{" + ",".join(ij or ["0u"]) + "};")
+        lines.append(f"static const unsigned {name}_kf[] = {{" + ",".join(kf or ["0u"]) + "};")
+        lines.append(f"static const float {name}_w[] = {{" + ",".join(w or ["0.0"]) + "};")
+
+    rows_to_c("fwd", fwd_rows)
+    rows_to_c("adj", adj_rows)
+    lines.append("static const int fwd_layer_rows[] = {" + ",".join(str(e) for _, e in fwd_layers) + "};")
+    lines.append("static const int adj_layer_rows[] = {" + ",".join(str(e) for _, e in adj_layers) + "};")
+    # slices
+    for name, sl in (("s32", s32), ("s64", s64)):
+        lines.append(f"static const int {name}_begin[] = {{" +
+                     ",".join(str(min(c)) for _, c in sl) + "};")
+        lines.append(f"static const int {name}_size[] = {{" + ",".join(str(len(c)) for _, c in sl) + "};")
+        for s, (_, comps) in enumerate(sl):
+            assert comps == list(range(min(comps), min(comps) + len(comps)))
+    lines += emit_slice_functions(prog, s32, "f")
+    lines += emit_slice_functions(prog, s64, "d")
+    lines.append("struct Traits {")
+    lines.append("  static constexpr int L_ = L, C_ = C, V_ = V, M_ = M, NMU_ = NMU, NUMAX_ = NUMAX, NS32_ = NS32, NS64_ = NS64;")
+    lines.append("  template <int S> using F32 = SliceF<S>;")
+    lines.append("  template <int S> using F64 = SliceD<S>;")
+    lines.append("};")
+    lines.append(f"}}  // namespace mtpgen_{tag}")
+    path = os.path.join(outdir, f"mtp_gen_{tag}.h")
+    text = "\n".join(lines) + "\n"
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as fh:
+            fh.write(text)
+    return path, {"C": C, "V": V, "m": prog.basis.m, "ops": len(prog.ops), "fwd_rows": len(fwd_rows),
+                  "adj_rows": len(adj_rows), "slices32": len(s32), "slices64": len(s64), **fl}
+
+
+def emit_tu(L, outdir):
+    """One translation unit per level: instantiates the kernels of mtp_level_impl.cuh."""
+    text = (f"// Generated by paper_2007_08555_gb300/codegen.py for lev_max = {L}. Do not edit.\n"
+            f"#include \"mtp_gen_L{L}.h\"\n"
+            f"#define MTP_GEN_NS mtpgen_L{L}\n"
+            f"#define MTP_LEVEL_FN mtp_level_ops_L{L}\n"
+            f"#include \"mtp_level_impl.cuh\"\n")
+    path = os.path.join(outdir, f"mtp_level_L{L}.cu")
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as fh:
+            fh.write(text)
+    return path
+
+
+def emit_all(outdir, levels=SUPPORTED_LEVELS):
+    os.makedirs(outdir, exist_ok=True)
+    info = {}
+    for L in levels:
+        info[L] = emit_level(L, outdir)[1]
+        emit_tu(L, outdir)
+    return info
+
+
+if __name__ == "__main__":
+    import sys
+    import json
+
+    print(json.dumps(emit_all(sys.argv[1] if len(sys.argv) > 1 else "generated"), indent=1))

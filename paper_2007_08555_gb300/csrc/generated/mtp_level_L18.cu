@@ -1,0 +1,5 @@
+// Generated by paper_2007_08555_gb300/codegen.py for lev_max = 18. Do not edit.
+#include "mtp_gen_L18.h"
+#define MTP_GEN_NS mtpgen_L18
+#define MTP_LEVEL_FN mtp_level_ops_L18
+#include "mtp_level_impl.cuh"

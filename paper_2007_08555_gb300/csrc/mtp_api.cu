@@ -1,0 +1,478 @@
+// C ABI of the MTP library (declared in include/mtp.h).
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mtp.h"
+#include "mtp_internal.h"
+
+namespace mtp {
+const LevelOps* mtp_level_ops_L2();
+const LevelOps* mtp_level_ops_L4();
+const LevelOps* mtp_level_ops_L6();
+const LevelOps* mtp_level_ops_L8();
+const LevelOps* mtp_level_ops_L10();
+const LevelOps* mtp_level_ops_L12();
+const LevelOps* mtp_level_ops_L14();
+const LevelOps* mtp_level_ops_L16();
+const LevelOps* mtp_level_ops_L18();
+const LevelOps* mtp_level_ops_L20();
+
+const LevelOps* level_ops(int L) {
+    switch (L) {
+        case 2: return mtp_level_ops_L2();
+        case 4: return mtp_level_ops_L4();
+        case 6: return mtp_level_ops_L6();
+        case 8: return mtp_level_ops_L8();
+        case 10: return mtp_level_ops_L10();
+        case 12: return mtp_level_ops_L12();
+        case 14: return mtp_level_ops_L14();
+        case 16: return mtp_level_ops_L16();
+        case 18: return mtp_level_ops_L18();
+        case 20: return mtp_level_ops_L20();
+        default: return nullptr;
+    }
+}
+}  // namespace mtp
+
+using mtp::DevBuf;
+
+struct mtp_model {
+    int L = 0, S = 0, NQ = 0, m = 0, nmu = 0, C = 0, V = 0;
+    double rmin = 0, rcut = 0;
+    mtp_precision prec = MTP_FP64;
+    const mtp::LevelOps* ops = nullptr;
+    int device = 0, n_sm = 152;
+    std::vector<double> xi, c;
+    DevBuf d_xi, d_c, d_seed, d_basis_value;
+    DevBuf d_fwd_ij, d_fwd_kf, d_fwd_w, d_fwd_layers, d_adj_ij, d_adj_kf, d_adj_w, d_adj_layers;
+    mtp::NbrState nb;
+    DevBuf mom, adjm, gx, gy, gz;
+    // staging for MTP_HOST_MEMORY calls
+    DevBuf s_off, s_pos, s_types, s_cells, s_energy, s_forces, s_virial, s_site, s_brows, s_batoms;
+    int cap = 128;
+    int last_max = 0;
+    int64_t launches = 0;
+    // profiling: events around the neighbour build and each evaluation phase
+    bool profiling = false;
+    cudaEvent_t ev_nbr[2] = {nullptr, nullptr};
+    cudaEvent_t ev_phase[mtp::kPhases + 1] = {};
+    double prof_ms[mtp::kPhases + 1] = {};  // neighbours, moments, contract, pairgrad, gather
+    int64_t prof_calls = 0;
+};
+
+namespace {
+
+bool is_fp64(const mtp_model* m) { return m->prec == MTP_FP64; }
+
+template <class T>
+mtp_status upload(DevBuf& b, const T* host, size_t count) {
+    if (b.reserve(sizeof(T) * count ? sizeof(T) * count : 8)) return MTP_ENOMEM;
+    if (count && cudaMemcpy(b.p, host, sizeof(T) * count, cudaMemcpyHostToDevice) != cudaSuccess) return MTP_ECUDA;
+    return MTP_OK;
+}
+
+mtp_status upload_params(mtp_model* M) {
+    const size_t nc = (size_t)M->S * M->S * M->nmu * M->NQ;
+    std::vector<double> seed(M->V, 0.0);
+    for (int a = 0; a < M->m; ++a) seed[M->ops->basis_value[a]] += M->xi[a];
+    mtp_status st;
+    if (is_fp64(M)) {
+        if ((st = upload(M->d_xi, M->xi.data(), M->xi.size()))) return st;
+        if ((st = upload(M->d_c, M->c.data(), nc))) return st;
+        if ((st = upload(M->d_seed, seed.data(), seed.size()))) return st;
+    } else {
+        std::vector<float> xf(M->xi.begin(), M->xi.end()), cf(M->c.begin(), M->c.end()), sf(seed.begin(), seed.end());
+        if ((st = upload(M->d_xi, xf.data(), xf.size()))) return st;
+        if ((st = upload(M->d_c, cf.data(), nc))) return st;
+        if ((st = upload(M->d_seed, sf.data(), sf.size()))) return st;
+    }
+    return MTP_OK;
+}
+
+mtp_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return MTP_OK;
+    if (e == cudaErrorMemoryAllocation) return MTP_ENOMEM;
+    return MTP_ECUDA;
+}
+
+mtp_status status_from_err(int err) {
+    if (err & mtp::kErrSpecies) return MTP_EINVAL;
+    if (err & mtp::kErrShift) return MTP_EINVAL;
+    if (err & mtp::kErrCellThin) return MTP_EINVAL;
+    if (err & mtp::kErrOverflow) return MTP_EOVERFLOW;
+    if (err & mtp::kErrSingular) return MTP_ESINGULAR;
+    if (err & mtp::kErrTimeout) return MTP_ETIMEOUT;
+    return MTP_OK;
+}
+
+int choose_tpa(int n_atoms, int n_sm) {
+    const long want = (long)n_sm * 512;
+    if (n_atoms >= want) return 1;
+    if (n_atoms * 2L >= want) return 2;
+    if (n_atoms * 4L >= want) return 4;
+    return 8;
+}
+
+template <class T>
+mtp_status run_eval(mtp_model* M, int K, int n, const int* cfg_off, const int* types, double* energy,
+                    double* forces, double* virial, double* site, double* brows, double* batoms, cudaStream_t st) {
+    const size_t N = (size_t)n;
+    const size_t tiles = (N + 31) / 32;
+    const int cap = M->nb.cap;
+    if (M->mom.reserve(tiles * M->C * 32 * sizeof(T)) || M->adjm.reserve(tiles * M->C * 32 * sizeof(T)) ||
+        M->gx.reserve(N * cap * sizeof(T)) || M->gy.reserve(N * cap * sizeof(T)) || M->gz.reserve(N * cap * sizeof(T)))
+        return MTP_ENOMEM;
+    if (energy) cudaMemsetAsync(energy, 0, sizeof(double) * K, st);
+    if (virial) cudaMemsetAsync(virial, 0, sizeof(double) * 9 * K, st);
+    if (brows) cudaMemsetAsync(brows, 0, sizeof(double) * (size_t)M->m * K, st);
+    mtp::EvalCtx<T> a;
+    a.n_atoms = n;
+    a.n_cfg = K;
+    a.cap = cap;
+    a.S = M->S;
+    a.NQ = M->NQ;
+    a.rmin = (T)M->rmin;
+    a.rcut = (T)M->rcut;
+    a.inv_span = (T)(1.0 / (M->rcut - M->rmin));
+    a.types = types;
+    a.cfg_of = M->nb.cfg_of.as<int>();
+    a.count = M->nb.count.as<int>();
+    a.jz = M->nb.jz.as<int>();
+    a.rev = M->nb.rev.as<int>();
+    a.rx = M->nb.rx.as<T>();
+    a.ry = M->nb.ry.as<T>();
+    a.rz = M->nb.rz.as<T>();
+    a.c = M->d_c.as<T>();
+    a.xi = M->d_xi.as<T>();
+    a.seed = M->d_seed.as<T>();
+    a.basis_value = M->d_basis_value.as<int>();
+    a.fwd_ij = M->d_fwd_ij.as<unsigned>();
+    a.fwd_kf = M->d_fwd_kf.as<unsigned>();
+    a.fwd_w = M->d_fwd_w.as<float>();
+    a.fwd_layer_end = M->d_fwd_layers.as<int>();
+    a.fwd_layers = M->ops->fwd_layers;
+    a.adj_ij = M->d_adj_ij.as<unsigned>();
+    a.adj_kf = M->d_adj_kf.as<unsigned>();
+    a.adj_w = M->d_adj_w.as<float>();
+    a.adj_layer_end = M->d_adj_layers.as<int>();
+    a.adj_layers = M->ops->adj_layers;
+    a.tpa = choose_tpa(n, M->n_sm);
+    a.mom = M->mom.as<T>();
+    a.adjm = M->adjm.as<T>();
+    a.gx = M->gx.as<T>();
+    a.gy = M->gy.as<T>();
+    a.gz = M->gz.as<T>();
+    a.energy = energy;
+    a.site = site;
+    a.b_atoms = batoms;
+    a.b_rows = brows;
+    a.forces = forces;
+    a.virial = virial;
+    a.err = M->nb.err.as<int>();
+    int l;
+    cudaEvent_t* marks = M->profiling ? M->ev_phase : nullptr;
+    if constexpr (sizeof(T) == 8)
+        l = M->ops->eval_f64(a, st, M->n_sm, marks);
+    else
+        l = M->ops->eval_f32(a, st, M->n_sm, marks);
+    if (l < 0) return MTP_EUNSUPPORTED;
+    M->launches += l;
+    return cuda_status(cudaGetLastError());
+}
+
+void collect_profile(mtp_model* M) {
+    if (!M->profiling || !M->ev_nbr[0]) return;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, M->ev_nbr[0], M->ev_nbr[1]) == cudaSuccess) M->prof_ms[0] += ms;
+    for (int k = 0; k < mtp::kPhases; ++k)
+        if (cudaEventElapsedTime(&ms, M->ev_phase[k], M->ev_phase[k + 1]) == cudaSuccess) M->prof_ms[k + 1] += ms;
+    M->prof_calls += 1;
+}
+
+mtp_status finish(mtp_model* M, cudaStream_t st) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    collect_profile(M);
+    int err = 0, mx = 0;
+    if (M->nb.err.p) {
+        cudaMemcpy(&err, M->nb.err.p, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&mx, M->nb.max_seen.p, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaMemset(M->nb.err.p, 0, sizeof(int));
+    }
+    M->last_max = mx;
+    return status_from_err(err);
+}
+
+template <class T>
+T* stage_in(DevBuf& b, const T* host, size_t count, cudaStream_t st, bool* ok) {
+    if (b.reserve(sizeof(T) * count + 16)) {
+        *ok = false;
+        return nullptr;
+    }
+    if (count) cudaMemcpyAsync(b.p, host, sizeof(T) * count, cudaMemcpyHostToDevice, st);
+    return b.as<T>();
+}
+
+double* stage_out(DevBuf& b, double* host, size_t count, bool* ok) {
+    if (!host) return nullptr;
+    if (b.reserve(sizeof(double) * count + 16)) {
+        *ok = false;
+        return nullptr;
+    }
+    return b.as<double>();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mtp_status_str(mtp_status s) {
+    switch (s) {
+        case MTP_OK: return "ok";
+        case MTP_EINVAL: return "invalid argument";
+        case MTP_ENOMEM: return "out of device memory";
+        case MTP_ECUDA: return "CUDA error";
+        case MTP_EOVERFLOW: return "neighbour list capacity exceeded";
+        case MTP_ESINGULAR: return "singular active-set matrix";
+        case MTP_ETIMEOUT: return "iteration limit reached";
+        case MTP_ENOACTIVESET: return "no active set";
+        case MTP_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+mtp_status mtp_create(int lev_max, int n_species, int n_radial, double r_min, double r_cut, const double* xi,
+                      const double* c, mtp_precision prec, mtp_model** out) {
+    if (!out) return MTP_EINVAL;
+    *out = nullptr;
+    lev_max -= lev_max % 2;
+    const mtp::LevelOps* ops = mtp::level_ops(lev_max);
+    if (!ops || n_species < 1 || n_species > mtp::kMaxSpecies || n_radial < 1 || n_radial > mtp::kMaxRadial ||
+        !(r_min >= 0.0) || !(r_cut > r_min) || (prec != MTP_FP64 && prec != MTP_FP32))
+        return MTP_EINVAL;
+    mtp_model* M = new (std::nothrow) mtp_model;
+    if (!M) return MTP_ENOMEM;
+    M->L = lev_max;
+    M->S = n_species;
+    M->NQ = n_radial;
+    M->rmin = r_min;
+    M->rcut = r_cut;
+    M->prec = prec;
+    M->ops = ops;
+    M->m = ops->M;
+    M->nmu = ops->NMU;
+    M->C = ops->C;
+    M->V = ops->V;
+    cudaGetDevice(&M->device);
+    cudaDeviceGetAttribute(&M->n_sm, cudaDevAttrMultiProcessorCount, M->device);
+    const size_t nc = (size_t)n_species * n_species * M->nmu * n_radial;
+    M->xi.assign(M->m, 0.0);
+    M->c.assign(nc, 0.0);
+    if (xi) std::copy(xi, xi + M->m, M->xi.begin());
+    if (c) std::copy(c, c + nc, M->c.begin());
+    mtp_status st = MTP_OK;
+    const int fr = ops->fwd_rows * 32, ar = ops->adj_rows * 32;
+    if (!st) st = upload(M->d_basis_value, ops->basis_value, M->m);
+    if (!st) st = upload(M->d_fwd_ij, ops->fwd_ij, fr);
+    if (!st) st = upload(M->d_fwd_kf, ops->fwd_kf, fr);
+    if (!st) st = upload(M->d_fwd_w, ops->fwd_w, fr);
+    if (!st) st = upload(M->d_fwd_layers, ops->fwd_layer_end, ops->fwd_layers);
+    if (!st) st = upload(M->d_adj_ij, ops->adj_ij, ar);
+    if (!st) st = upload(M->d_adj_kf, ops->adj_kf, ar);
+    if (!st) st = upload(M->d_adj_w, ops->adj_w, ar);
+    if (!st) st = upload(M->d_adj_layers, ops->adj_layer_end, ops->adj_layers);
+    if (!st) st = upload_params(M);
+    if (st) {
+        mtp_destroy(M);
+        return st;
+    }
+    *out = M;
+    return MTP_OK;
+}
+
+void mtp_destroy(mtp_model* M) {
+    if (!M) return;
+    DevBuf* bufs[] = {&M->d_xi, &M->d_c, &M->d_seed, &M->d_basis_value, &M->d_fwd_ij, &M->d_fwd_kf, &M->d_fwd_w,
+                      &M->d_fwd_layers, &M->d_adj_ij, &M->d_adj_kf, &M->d_adj_w, &M->d_adj_layers, &M->mom,
+                      &M->adjm, &M->gx, &M->gy, &M->gz, &M->s_off, &M->s_pos, &M->s_types, &M->s_cells,
+                      &M->s_energy, &M->s_forces, &M->s_virial, &M->s_site, &M->s_brows, &M->s_batoms,
+                      &M->nb.count, &M->nb.jz, &M->nb.shift, &M->nb.rev, &M->nb.rx, &M->nb.ry, &M->nb.rz,
+                      &M->nb.cfg_of, &M->nb.desc, &M->nb.atom_bin, &M->nb.atom_wrap, &M->nb.atom_local,
+                      &M->nb.bin_count, &M->nb.bin_start, &M->nb.bin_fill, &M->nb.bin_atoms, &M->nb.scan_tmp,
+                      &M->nb.err, &M->nb.max_seen};
+    for (DevBuf* b : bufs) b->release();
+    for (cudaEvent_t& e : M->ev_nbr)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t& e : M->ev_phase)
+        if (e) cudaEventDestroy(e);
+    delete M;
+}
+
+int mtp_basis_count(const mtp_model* M) { return M ? M->m : 0; }
+int mtp_radial_count(const mtp_model* M) { return M ? M->nmu : 0; }
+int mtp_moment_count(const mtp_model* M) { return M ? M->C : 0; }
+int64_t mtp_launch_count(const mtp_model* M) { return M ? M->launches : 0; }
+int mtp_last_neighbor_max(const mtp_model* M) { return M ? M->last_max : 0; }
+
+mtp_status mtp_profile(mtp_model* M, int enable) {
+    if (!M) return MTP_EINVAL;
+    if (enable && !M->ev_nbr[0]) {
+        for (cudaEvent_t& e : M->ev_nbr)
+            if (cudaEventCreate(&e) != cudaSuccess) return MTP_ECUDA;
+        for (cudaEvent_t& e : M->ev_phase)
+            if (cudaEventCreate(&e) != cudaSuccess) return MTP_ECUDA;
+    }
+    M->profiling = enable != 0;
+    for (double& x : M->prof_ms) x = 0.0;
+    M->prof_calls = 0;
+    return MTP_OK;
+}
+
+mtp_status mtp_profile_read(const mtp_model* M, double* ms, int n, int64_t* calls) {
+    if (!M || !ms || n < 1) return MTP_EINVAL;
+    for (int k = 0; k < n && k <= mtp::kPhases; ++k) ms[k] = M->prof_ms[k];
+    if (calls) *calls = M->prof_calls;
+    return MTP_OK;
+}
+
+mtp_status mtp_level_table(const mtp_model* M, int32_t* buf, size_t cap, size_t* len) {
+    if (!M || !len) return MTP_EINVAL;
+    *len = (size_t)M->ops->level_table_len;
+    if (buf) std::memcpy(buf, M->ops->level_table, sizeof(int32_t) * std::min(cap, *len));
+    return MTP_OK;
+}
+
+mtp_status mtp_set_params(mtp_model* M, const double* xi, const double* c) {
+    if (!M) return MTP_EINVAL;
+    if (xi) std::copy(xi, xi + M->m, M->xi.begin());
+    if (c) std::copy(c, c + M->c.size(), M->c.begin());
+    return upload_params(M);
+}
+
+mtp_status mtp_set_neighbor_capacity(mtp_model* M, int cap) {
+    if (!M || cap < 1 || cap > 1024) return MTP_EINVAL;
+    M->cap = cap;
+    return MTP_OK;
+}
+
+mtp_status mtp_sync(mtp_model* M, void* stream) {
+    if (!M) return MTP_EINVAL;
+    return finish(M, (cudaStream_t)stream);
+}
+
+static mtp_status check_batch(mtp_model* M, int K, int n, const int32_t* off, const double* pos, const double* cells) {
+    if (!M || K < 1 || n < 0 || n >= (1 << 24) || !off || (n > 0 && !pos) || !cells) return MTP_EINVAL;
+    return MTP_OK;
+}
+
+static mtp_status prepare_neighbors(mtp_model* M, int K, int n, const int* off, const double* pos,
+                                    const int* types, const double* cells, double skin, cudaStream_t st) {
+    if (M->nb.err.reserve(4) || M->nb.max_seen.reserve(4)) return MTP_ENOMEM;
+    cudaMemsetAsync(M->nb.max_seen.p, 0, sizeof(int), st);
+    if (M->profiling) cudaEventRecord(M->ev_nbr[0], st);
+    const int l = mtp::build_neighbors(M->nb, K, n, off, pos, types, cells, M->rcut + skin, is_fp64(M), M->cap,
+                                       st, M->S);
+    if (M->profiling) cudaEventRecord(M->ev_nbr[1], st);
+    if (l < 0) return cuda_status(cudaGetLastError());
+    M->launches += l;
+    return MTP_OK;
+}
+
+mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, const double* pos,
+                          const int32_t* types, const double* cells, double* energy, double* forces, double* virial,
+                          double* site, double* b_rows, double* b_atoms, double* grade_cfg, double* grade_atom,
+                          int flags, void* stream) {
+    mtp_status s = check_batch(M, K, n, cfg_off, pos, cells);
+    if (s) return s;
+    if (n > 0 && !types) return MTP_EINVAL;
+    if (grade_cfg || grade_atom) return MTP_ENOACTIVESET;
+    if (flags & MTP_REUSE_NEIGHBORS) return MTP_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool host = flags & MTP_HOST_MEMORY;
+    double *h_energy = energy, *h_forces = forces, *h_virial = virial, *h_site = site, *h_brows = b_rows,
+           *h_batoms = b_atoms;
+    if (host) {
+        std::vector<int> offs(cfg_off, cfg_off + K + 1);
+        if (offs[0] != 0 || offs[K] != n) return MTP_EINVAL;
+        for (int k = 0; k < K; ++k)
+            if (offs[k + 1] < offs[k]) return MTP_EINVAL;
+        bool ok = true;
+        cfg_off = stage_in(M->s_off, cfg_off, K + 1, st, &ok);
+        pos = stage_in(M->s_pos, pos, 3 * (size_t)n, st, &ok);
+        types = stage_in(M->s_types, types, (size_t)n, st, &ok);
+        cells = stage_in(M->s_cells, cells, 9 * (size_t)K, st, &ok);
+        energy = stage_out(M->s_energy, energy, K, &ok);
+        forces = stage_out(M->s_forces, forces, 3 * (size_t)n, &ok);
+        virial = stage_out(M->s_virial, virial, 9 * (size_t)K, &ok);
+        site = stage_out(M->s_site, site, n, &ok);
+        b_rows = stage_out(M->s_brows, b_rows, (size_t)K * M->m, &ok);
+        b_atoms = stage_out(M->s_batoms, b_atoms, (size_t)n * M->m, &ok);
+        if (!ok) return MTP_ENOMEM;
+    }
+    if ((s = prepare_neighbors(M, K, n, cfg_off, pos, types, cells, 0.0, st))) return s;
+    if (is_fp64(M))
+        s = run_eval<double>(M, K, n, cfg_off, types, energy, forces, virial, site, b_rows, b_atoms, st);
+    else
+        s = run_eval<float>(M, K, n, cfg_off, types, energy, forces, virial, site, b_rows, b_atoms, st);
+    if (s) return s;
+    if (host) {
+        if (h_energy) cudaMemcpyAsync(h_energy, energy, sizeof(double) * K, cudaMemcpyDeviceToHost, st);
+        if (h_forces) cudaMemcpyAsync(h_forces, forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st);
+        if (h_virial) cudaMemcpyAsync(h_virial, virial, sizeof(double) * 9 * K, cudaMemcpyDeviceToHost, st);
+        if (h_site) cudaMemcpyAsync(h_site, site, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+        if (h_brows) cudaMemcpyAsync(h_brows, b_rows, sizeof(double) * K * M->m, cudaMemcpyDeviceToHost, st);
+        if (h_batoms)
+            cudaMemcpyAsync(h_batoms, b_atoms, sizeof(double) * (size_t)n * M->m, cudaMemcpyDeviceToHost, st);
+    }
+    if (flags & MTP_ASYNC) return cuda_status(cudaGetLastError());
+    return finish(M, st);
+}
+
+mtp_status mtp_eval(mtp_model* M, int n, const double* pos, const int32_t* types, const double* cell, double* energy,
+                    double* forces, double* virial, double* site, double* grade_cfg, double* grade_atom, int flags,
+                    void* stream) {
+    if (!M) return MTP_EINVAL;
+    int32_t off_h[2] = {0, n};
+    const int32_t* off = off_h;
+    if (!(flags & MTP_HOST_MEMORY)) {
+        if (M->s_off.reserve(16)) return MTP_ENOMEM;
+        cudaMemcpyAsync(M->s_off.p, off_h, sizeof off_h, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+        off = M->s_off.as<int32_t>();
+    }
+    return mtp_eval_batch(M, 1, n, off, pos, types, cell, energy, forces, virial, site, nullptr, nullptr, grade_cfg,
+                          grade_atom, flags, stream);
+}
+
+mtp_status mtp_neighbors(mtp_model* M, int K, int n, const int32_t* cfg_off, const double* pos, const double* cells,
+                         double skin, int32_t* counts, int32_t* nbr_j, int32_t* nbr_s, double* r_ij, int64_t cap_pairs,
+                         int flags, void* stream) {
+    mtp_status s = check_batch(M, K, n, cfg_off, pos, cells);
+    if (s || !counts || skin < 0) return s ? s : MTP_EINVAL;
+    if (flags & MTP_HOST_MEMORY) return MTP_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    // species are not needed for the geometry: use zeros
+    DevBuf& zt = M->s_types;
+    if (zt.reserve(sizeof(int) * (size_t)(n + 1))) return MTP_ENOMEM;
+    cudaMemsetAsync(zt.p, 0, sizeof(int) * (size_t)(n + 1), st);
+    if ((s = prepare_neighbors(M, K, n, cfg_off, pos, zt.as<int>(), cells, skin, st))) return s;
+    cudaMemcpyAsync(counts, M->nb.count.p, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
+    if ((s = finish(M, st))) return s;
+    if (!nbr_j) return MTP_OK;
+    DevBuf& offs = M->s_site;  // n+1 ints of scratch
+    DevBuf& tmp = M->s_brows;
+    if (offs.reserve(sizeof(int) * (size_t)(n + 1)) || tmp.reserve(sizeof(int) * (mtp::scan_tmp_ints(n) + 8)))
+        return MTP_ENOMEM;
+    mtp::scan_exclusive(M->nb.count.as<int>(), offs.as<int>(), n, tmp.as<int>(), st);
+    int total = 0;
+    cudaMemcpyAsync(&total, offs.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (total > cap_pairs) return MTP_EOVERFLOW;
+    mtp::export_neighbors(M->nb, pos, offs.as<int>(), nbr_j, nbr_s, r_ij, st);
+    return finish(M, st);
+}
+
+}  // extern "C"

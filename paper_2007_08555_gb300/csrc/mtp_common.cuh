@@ -1,0 +1,78 @@
+// Shared device structures and helpers of the MTP library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mtp {
+
+constexpr int kWarp = 32;
+constexpr int kMaxSpecies = 8;  // S*S*N_mu*N_Q coefficients stay within 40 KB of shared memory
+constexpr int kMaxRadial = 16;
+
+// device error word bits
+enum : int {
+    kErrOverflow = 1,   // neighbour list capacity exceeded
+    kErrSpecies = 2,    // species index outside [0, S)
+    kErrShift = 4,      // |image shift| beyond the packed range
+    kErrCellThin = 8,   // cell thinner than the cutoff allows with the supported image range
+    kErrTimeout = 16,   // an iteration limit was reached
+    kErrSingular = 32   // singular matrix in the active-set LU
+};
+
+// Inputs and outputs of one evaluation; every array is device memory.
+template <class T>
+struct EvalCtx {
+    int n_atoms;      // atoms in the batch
+    int n_cfg;        // configurations in the batch
+    int cap;          // neighbour slots per atom (slot-major arrays have stride n_atoms)
+    int S, NQ;        // species, radial basis size
+    T rmin, rcut, inv_span;
+    const int* types;     // [n]
+    const int* cfg_of;    // [n] atom -> configuration
+    const int* count;     // [n] neighbours of each atom
+    const int* jz;        // [cap][n] neighbour index | species << 24
+    const int* rev;       // [cap][n] slot of the reverse pair in the neighbour's list, -1 if absent
+    const T* rx;          // [cap][n] r_ij components
+    const T* ry;
+    const T* rz;
+    const T* c;           // [S][S][NMU][NQ] radial coefficients
+    const T* xi;          // [M]
+    const T* seed;        // [V] adjoint seed: xi at the value index of each basis function
+    const int* basis_value;  // [M]
+    const unsigned* fwd_ij;  // forward program rows (32 lanes per row)
+    const unsigned* fwd_kf;
+    const float* fwd_w;
+    const int* fwd_layer_end;
+    int fwd_layers;
+    const unsigned* adj_ij;  // adjoint program rows
+    const unsigned* adj_kf;
+    const float* adj_w;
+    const int* adj_layer_end;
+    int adj_layers;
+    int tpa;              // threads per atom in the pair kernels (1, 2, 4 or 8)
+    T* mom;               // [ceil(n/32)][C][32] moment components (tile layout)
+    T* adjm;              // [ceil(n/32)][C][32] dV/dM
+    T* gx;                // [cap][n] dV_i/dr_ij
+    T* gy;
+    T* gz;
+    double* energy;       // [n_cfg] (accumulated; zeroed by the caller) or NULL
+    double* site;         // [n] or NULL
+    double* b_atoms;      // [n][M] or NULL
+    double* b_rows;       // [n_cfg][M] (accumulated) or NULL
+    double* forces;       // [n][3] or NULL
+    double* virial;       // [n_cfg][9] (accumulated) or NULL
+    int* err;
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace mtp

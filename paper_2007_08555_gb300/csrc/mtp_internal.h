@@ -1,0 +1,64 @@
+// Host-side internals of the MTP library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+#include "mtp_level.h"
+
+namespace mtp {
+
+// A device buffer that only grows.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t want) {
+        if (want <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        size_t b = want + want / 4 + 256;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e == cudaSuccess) bytes = b;
+        return e;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+struct CellDesc {
+    double H[9], Hi[9];
+    float hn[9];  // lattice vectors divided by the bin counts, rows
+    int n[3], c[3];
+    int bin0, nbins;
+};
+
+// Neighbour list in slot-major layout (stride = number of atoms).
+struct NbrState {
+    int n_atoms = 0, n_cfg = 0, cap = 0;
+    bool fp64 = false;
+    double rsearch = 0.0;
+    DevBuf count, jz, shift, rev, rx, ry, rz;
+    DevBuf cfg_of, desc, atom_bin, atom_wrap, atom_local, bin_count, bin_start, bin_fill, bin_atoms, scan_tmp;
+    DevBuf err, max_seen;
+};
+
+// Build the neighbour list of a batch (device inputs).  r_ij are written in float or double.
+// Returns the number of kernels launched, or -1 on a CUDA error (cudaGetLastError holds it).
+int build_neighbors(NbrState& nb, int n_cfg, int n_atoms, const int* cfg_off, const double* pos,
+                    const int* types, const double* cells, double rsearch, bool fp64, int cap,
+                    cudaStream_t st, int n_species);
+
+// Exclusive prefix sum of n ints: out[0..n] with out[n] = total; tmp holds >= scan_tmp_ints(n) ints.
+size_t scan_tmp_ints(int n);
+int scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_t st);
+
+// CSR export of the neighbour list with exact double-precision r_ij.
+int export_neighbors(const NbrState& nb, const double* pos, const int* offsets, int* nbr_j, int* nbr_s,
+                     double* r_ij, cudaStream_t st);
+
+}  // namespace mtp

@@ -1,0 +1,35 @@
+// Per-level registry: generated tables and kernel launchers of one lev_max.
+#pragma once
+#include <cuda_runtime.h>
+#include "mtp_common.cuh"
+
+namespace mtp {
+
+struct LevelOps {
+    int L, C, V, M, NMU, NUMAX;
+    const int* level_table;
+    int level_table_len;
+    const int* basis_value;        // [M] value index of each basis function
+    const unsigned* fwd_ij;
+    const unsigned* fwd_kf;
+    const float* fwd_w;
+    const int* fwd_layer_end;
+    int fwd_rows, fwd_layers;
+    const unsigned* adj_ij;
+    const unsigned* adj_kf;
+    const float* adj_w;
+    const int* adj_layer_end;
+    int adj_rows, adj_layers;
+    int program_ops;
+    int flop_pair_moments, flop_pair_adjoint, flop_atom_program;
+    // launchers (stream-ordered, no synchronisation); return the number of kernels launched
+    int (*eval_f32)(const EvalCtx<float>&, cudaStream_t, int n_sm, cudaEvent_t* marks);
+    int (*eval_f64)(const EvalCtx<double>&, cudaStream_t, int n_sm, cudaEvent_t* marks);
+};
+
+// Phases timed when profiling is on: marks[k] is recorded before phase k, marks[kPhases] after.
+enum { kPhaseMoments = 0, kPhaseContract = 1, kPhasePairgrad = 2, kPhaseGather = 3, kPhases = 4 };
+
+const LevelOps* level_ops(int L);  // nullptr when lev_max is not built
+
+}  // namespace mtp

@@ -1,0 +1,516 @@
+// Neighbourhoods of Sec. 2.1 (Eq. 1): for every atom i all (j, s) with |x_j + s H - x_i| < R_cut.
+//
+// Cell lists per configuration: atoms are binned by fractional coordinate into n_k bins along
+// each lattice direction (bin width >= R_cut unless the cell is thinner), and each atom visits
+// the bins within c_k = ceil(R_cut / bin width) along every direction, periodic images included
+// (small cells are visited several times with different image shifts).  Distances are first
+// taken in float from bin-local coordinates; pairs within 1e-3 Angstrom of the cutoff are decided
+// in double precision with the fixed operation order documented in mtp.h, so the lists are
+// identical to a brute-force double-precision search.  Each warp owns one atom: lanes test
+// candidates, accepted pairs are compacted with a ballot, rank-sorted by (j, s) and written in
+// slot-major layout.  A last kernel records, for every pair, the slot of the reverse pair in
+// the neighbour's list (used by the deterministic force gather).
+#include "mtp_internal.h"
+#include "mtp_common.cuh"
+
+namespace mtp {
+
+namespace {
+
+constexpr int kScanItems = 4;
+constexpr int kScanThreads = 512;
+constexpr int kScanBlock = kScanItems * kScanThreads;
+constexpr int kMaxImageReach = 16;
+constexpr int kMaxShift = 50;  // |wrap| per atom; image shifts then stay within +-117
+constexpr double kBand = 1e-3;
+
+__device__ __forceinline__ int floordiv(int a, int b) {
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+__device__ __forceinline__ int find_cfg(const int* cfg_off, int K, int i) {
+    int lo = 0, hi = K;  // cfg_off[lo] <= i < cfg_off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (cfg_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Per-configuration geometry: inverse cell, perpendicular widths, bin counts and reach.
+__global__ void k_cells(int K, const double* cells, const int* cfg_off, double rsearch, CellDesc* d,
+                        int* nbins, int* err) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    CellDesc D;
+    const double* H = cells + 9 * (size_t)k;
+    for (int q = 0; q < 9; ++q) D.H[q] = H[q];
+    const double a = H[0], b = H[1], c = H[2], e = H[3], f = H[4], g = H[5], h = H[6], ii = H[7], jj = H[8];
+    const double det = a * (f * jj - g * ii) - b * (e * jj - g * h) + c * (e * ii - f * h);
+    D.Hi[0] = (f * jj - g * ii) / det; D.Hi[1] = (c * ii - b * jj) / det; D.Hi[2] = (b * g - c * f) / det;
+    D.Hi[3] = (g * h - e * jj) / det; D.Hi[4] = (a * jj - c * h) / det; D.Hi[5] = (c * e - a * g) / det;
+    D.Hi[6] = (e * ii - f * h) / det; D.Hi[7] = (b * h - a * ii) / det; D.Hi[8] = (a * f - b * e) / det;
+    const double vol = fabs(det);
+    double w[3];
+    for (int q = 0; q < 3; ++q) {
+        const double* u = H + ((q + 1) % 3) * 3;
+        const double* v = H + ((q + 2) % 3) * 3;
+        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+        w[q] = vol / sqrt(cx * cx + cy * cy + cz * cz);
+        int nq = (int)floor(w[q] / rsearch);
+        D.n[q] = nq < 1 ? 1 : (nq > 1024 ? 1024 : nq);
+    }
+    const long natoms = cfg_off[k + 1] - cfg_off[k];
+    const long limit = natoms > 1 ? natoms : 1;
+    while ((long)D.n[0] * D.n[1] * D.n[2] > limit) {  // never more bins than atoms
+        int q = 0;
+        if (D.n[1] > D.n[q]) q = 1;
+        if (D.n[2] > D.n[q]) q = 2;
+        D.n[q] = D.n[q] / 2 > 0 ? D.n[q] / 2 : 1;
+        if (D.n[0] * D.n[1] * D.n[2] == 1) break;
+    }
+    for (int q = 0; q < 3; ++q) {
+        const double width = w[q] / D.n[q];
+        int cq = (int)ceil((rsearch + kBand) / width);
+        if (cq < 1) cq = 1;
+        if (cq > kMaxImageReach) {
+            atomicOr(err, kErrCellThin);
+            cq = kMaxImageReach;
+        }
+        D.c[q] = cq;
+        for (int t = 0; t < 3; ++t) D.hn[3 * q + t] = (float)(H[3 * q + t] / D.n[q]);
+    }
+    D.nbins = D.n[0] * D.n[1] * D.n[2];
+    D.bin0 = 0;
+    d[k] = D;
+    nbins[k] = D.nbins;
+}
+
+__global__ void k_cells_offsets(int K, const int* bin0, CellDesc* d) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K) d[k].bin0 = bin0[k];
+}
+
+__global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, int S, const int* cfg_off,
+                            const CellDesc* d, int* cfg_of, int* atom_bin, int* atom_wrap, float4* local,
+                            int* bin_count, int* err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = find_cfg(cfg_off, K, i);
+    cfg_of[i] = k;
+    if (types[i] < 0 || types[i] >= S) atomicOr(err, kErrSpecies);
+    const CellDesc& D = d[k];
+    const double x[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
+    int w[3], b[3];
+    double frac[3];
+    for (int q = 0; q < 3; ++q) {
+        const double fq = x[0] * D.Hi[0 * 3 + q] + x[1] * D.Hi[1 * 3 + q] + x[2] * D.Hi[2 * 3 + q];
+        const double fl = floor(fq);
+        w[q] = (int)fl;
+        double fr = fq - fl;
+        int bq = (int)(fr * D.n[q]);
+        if (bq < 0) bq = 0;
+        if (bq >= D.n[q]) bq = D.n[q] - 1;
+        b[q] = bq;
+        frac[q] = (double)w[q] + (double)bq / (double)D.n[q];
+        if (w[q] > kMaxShift || w[q] < -kMaxShift) atomicOr(err, kErrShift);
+    }
+    double o[3];
+    for (int t = 0; t < 3; ++t) o[t] = frac[0] * D.H[0 * 3 + t] + frac[1] * D.H[1 * 3 + t] + frac[2] * D.H[2 * 3 + t];
+    local[i] = make_float4((float)(x[0] - o[0]), (float)(x[1] - o[1]), (float)(x[2] - o[2]), 0.f);
+    const int bin = D.bin0 + (b[0] * D.n[1] + b[1]) * D.n[2] + b[2];
+    atom_bin[i] = bin;
+    atom_wrap[i] = ((w[0] + 128) & 255) | (((w[1] + 128) & 255) << 8) | (((w[2] + 128) & 255) << 16);
+    atomicAdd(&bin_count[bin], 1);
+}
+
+__global__ void k_bin_scatter(int n, const int* atom_bin, const int* bin_start, int* bin_fill, int* bin_atoms) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int bin = atom_bin[i];
+    const int slot = atomicAdd(&bin_fill[bin], 1);
+    bin_atoms[bin_start[bin] + slot] = i;
+}
+
+__device__ __forceinline__ int unpack(int packed, int q) { return ((packed >> (8 * q)) & 255) - 128; }
+
+// exact decision and displacement, written in the documented double-precision order
+__device__ __forceinline__ double exact_r2(const double* xi, const double* xj, const double* H, const int* s,
+                                           double* d) {
+    for (int k = 0; k < 3; ++k) {
+        double sh = __dmul_rn((double)s[0], H[0 * 3 + k]);
+        sh = __dadd_rn(sh, __dmul_rn((double)s[1], H[1 * 3 + k]));
+        sh = __dadd_rn(sh, __dmul_rn((double)s[2], H[2 * 3 + k]));
+        d[k] = __dsub_rn(__dadd_rn(xj[k], sh), xi[k]);
+    }
+    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+struct BuildArgs {
+    int n, cap, S;
+    double rs2;      // rsearch^2 (double)
+    float lo2, hi2;  // (rsearch -/+ band)^2
+    const double* pos;
+    const int* types;
+    const int* cfg_of;
+    const CellDesc* desc;
+    const int* atom_bin;
+    const int* atom_wrap;
+    const float4* local;
+    const int* bin_start;
+    const int* bin_atoms;
+    int* count;
+    int* jz;
+    int* shift;
+    void* rx;
+    void* ry;
+    void* rz;
+    int* err;
+    int* max_seen;
+};
+
+template <class T>
+__global__ void __launch_bounds__(128) k_build(const BuildArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw) + (size_t)warp * a.cap;
+    T* rbuf = reinterpret_cast<T*>(reinterpret_cast<unsigned long long*>(smem_raw) + (size_t)wpb * a.cap) +
+              (size_t)warp * 3 * a.cap;
+    T* RX = static_cast<T*>(a.rx);
+    T* RY = static_cast<T*>(a.ry);
+    T* RZ = static_cast<T*>(a.rz);
+    for (int i = blockIdx.x * wpb + warp; i < a.n; i += gridDim.x * wpb) {
+        const int k = a.cfg_of[i];
+        const CellDesc& D = a.desc[k];
+        const int lb = a.atom_bin[i] - D.bin0;
+        const int b2 = lb % D.n[2], b1 = (lb / D.n[2]) % D.n[1], b0 = lb / (D.n[2] * D.n[1]);
+        const int wi = a.atom_wrap[i];
+        const float4 li = a.local[i];
+        const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1], a.pos[3 * (size_t)i + 2]};
+        int cnt = 0;
+        for (int o0 = -D.c[0]; o0 <= D.c[0]; ++o0) {
+            const int bb0 = b0 + o0, t0 = floordiv(bb0, D.n[0]), w0 = bb0 - t0 * D.n[0];
+            for (int o1 = -D.c[1]; o1 <= D.c[1]; ++o1) {
+                const int bb1 = b1 + o1, t1 = floordiv(bb1, D.n[1]), w1 = bb1 - t1 * D.n[1];
+                for (int o2 = -D.c[2]; o2 <= D.c[2]; ++o2) {
+                    const int bb2 = b2 + o2, t2 = floordiv(bb2, D.n[2]), w2 = bb2 - t2 * D.n[2];
+                    const float ox = o0 * D.hn[0] + o1 * D.hn[3] + o2 * D.hn[6];
+                    const float oy = o0 * D.hn[1] + o1 * D.hn[4] + o2 * D.hn[7];
+                    const float oz = o0 * D.hn[2] + o1 * D.hn[5] + o2 * D.hn[8];
+                    const int bin = D.bin0 + (w0 * D.n[1] + w1) * D.n[2] + w2;
+                    const int start = a.bin_start[bin], end = a.bin_start[bin + 1];
+                    for (int q0 = start; q0 < end; q0 += 32) {
+                        const int q = q0 + lane;
+                        bool acc = false;
+                        int j = 0, s[3] = {0, 0, 0};
+                        float dx = 0.f, dy = 0.f, dz = 0.f;
+                        double dd[3] = {0.0, 0.0, 0.0};
+                        if (q < end) {
+                            j = a.bin_atoms[q];
+                            const int wj = a.atom_wrap[j];
+                            s[0] = t0 - unpack(wj, 0) + unpack(wi, 0);
+                            s[1] = t1 - unpack(wj, 1) + unpack(wi, 1);
+                            s[2] = t2 - unpack(wj, 2) + unpack(wi, 2);
+                            if (!(j == i && s[0] == 0 && s[1] == 0 && s[2] == 0)) {
+                                const float4 lj = a.local[j];
+                                dx = (lj.x - li.x) + ox;
+                                dy = (lj.y - li.y) + oy;
+                                dz = (lj.z - li.z) + oz;
+                                const float r2 = dx * dx + dy * dy + dz * dz;
+                                const bool exact_needed = sizeof(T) == 8 ? (r2 <= a.hi2) : (r2 >= a.lo2 && r2 <= a.hi2);
+                                if (exact_needed) {
+                                    const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1],
+                                                          a.pos[3 * (size_t)j + 2]};
+                                    acc = exact_r2(xi, xj, D.H, s, dd) < a.rs2;
+                                } else {
+                                    acc = r2 < a.lo2;
+                                }
+                            }
+                        }
+                        const unsigned ball = __ballot_sync(0xffffffffu, acc);
+                        if (acc) {
+                            const int pos_ = cnt + __popc(ball & ((1u << lane) - 1u));
+                            if (pos_ < a.cap) {
+                                keys[pos_] = ((unsigned long long)j << 24) |
+                                             (unsigned long long)(((s[0] + 128) << 16) | ((s[1] + 128) << 8) | (s[2] + 128));
+                                if (sizeof(T) == 8) {
+                                    rbuf[3 * pos_] = (T)dd[0];
+                                    rbuf[3 * pos_ + 1] = (T)dd[1];
+                                    rbuf[3 * pos_ + 2] = (T)dd[2];
+                                } else {
+                                    rbuf[3 * pos_] = (T)dx;
+                                    rbuf[3 * pos_ + 1] = (T)dy;
+                                    rbuf[3 * pos_ + 2] = (T)dz;
+                                }
+                            }
+                        }
+                        cnt += __popc(ball);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        int keep = cnt;
+        if (cnt > a.cap) {
+            keep = a.cap;
+            if (lane == 0) {
+                atomicOr(a.err, kErrOverflow);
+                atomicMax(a.max_seen, cnt);
+            }
+        } else if (lane == 0) {
+            atomicMax(a.max_seen, cnt);
+        }
+        const size_t n = (size_t)a.n;
+        for (int e = lane; e < keep; e += 32) {
+            const unsigned long long key = keys[e];
+            int rank = 0;
+            for (int f = 0; f < keep; ++f) rank += keys[f] < key ? 1 : 0;
+            const int j = (int)(key >> 24);
+            const size_t o = (size_t)rank * n + i;
+            int tj = a.types[j];
+            tj = tj < 0 ? 0 : (tj >= a.S ? a.S - 1 : tj);  // invalid species are reported by k_bin_atoms
+            a.jz[o] = j | (tj << 24);
+            a.shift[o] = (int)(key & 0xffffffull);
+            RX[o] = rbuf[3 * e];
+            RY[o] = rbuf[3 * e + 1];
+            RZ[o] = rbuf[3 * e + 2];
+        }
+        if (lane == 0) a.count[i] = keep;
+        __syncwarp();
+    }
+}
+
+__global__ void k_reverse(int n, const int* count, const int* jz, const int* shift, int* rev) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int cnt = count[i];
+    const size_t N = (size_t)n;
+    for (int p = 0; p < cnt; ++p) {
+        const size_t o = (size_t)p * N + i;
+        const int j = jz[o] & 0xffffff;
+        const int sp = shift[o];
+        const int neg = ((256 - (sp & 255)) & 255) | (((256 - ((sp >> 8) & 255)) & 255) << 8) |
+                        (((256 - ((sp >> 16) & 255)) & 255) << 16);
+        const unsigned long long want = ((unsigned long long)i << 24) | (unsigned long long)neg;
+        int lo = 0, hi = count[j] - 1, found = -1;
+        while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            const size_t om = (size_t)mid * N + j;
+            const unsigned long long key = ((unsigned long long)(jz[om] & 0xffffff) << 24) |
+                                           (unsigned long long)(shift[om] & 0xffffff);
+            if (key == want) {
+                found = mid;
+                break;
+            }
+            if (key < want) lo = mid + 1; else hi = mid - 1;
+        }
+        rev[o] = found;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// exclusive scan
+// ---------------------------------------------------------------------------------------------
+__global__ void k_scan_blocks(const int* in, int* out, int n, int* block_sums) {
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int local = 0;
+    for (int t = 0; t < kScanItems; ++t) {
+        v[t] = (base + t < n) ? in[base + t] : 0;
+        local += v[t];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int wt = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wt, o);
+            if (lane >= o) wt += y;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = wt;
+    }
+    __syncthreads();
+    int run = incl - local + (warp > 0 ? warp_tot[warp - 1] : 0);
+    for (int t = 0; t < kScanItems; ++t) {
+        if (base + t < n) out[base + t] = run;
+        run += v[t];
+    }
+    if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = run;
+}
+
+__global__ void k_scan_sums(int* sums, int nb, int* total_out) {
+    // one block: sequential over chunks of 1024
+    __shared__ int carry;
+    __shared__ int tmp[1024];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < nb ? sums[i] : 0;
+        tmp[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int y = threadIdx.x >= o ? tmp[threadIdx.x - o] : 0;
+            __syncthreads();
+            tmp[threadIdx.x] += y;
+            __syncthreads();
+        }
+        if (i < nb) sums[i] = carry + tmp[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += tmp[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(int* out, int n, const int* sums) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += sums[i / kScanBlock];
+}
+
+__global__ void k_export(int n, const double* pos, const CellDesc* desc, const int* cfg_of, const int* count,
+                         const int* jz, const int* shift, const int* offsets, int* nbr_j, int* nbr_s, double* r_ij) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const CellDesc& D = desc[cfg_of[i]];
+    const double xi[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
+    const int cnt = count[i];
+    for (int p = 0; p < cnt; ++p) {
+        const size_t o = (size_t)p * n + i;
+        const int j = jz[o] & 0xffffff;
+        const int sp = shift[o];
+        const int s[3] = {((sp >> 16) & 255) - 128, ((sp >> 8) & 255) - 128, (sp & 255) - 128};
+        const size_t q = (size_t)offsets[i] + p;
+        nbr_j[q] = j;
+        if (nbr_s)
+            for (int t = 0; t < 3; ++t) nbr_s[3 * q + t] = s[t];
+        if (r_ij) {
+            const double xj[3] = {pos[3 * (size_t)j], pos[3 * (size_t)j + 1], pos[3 * (size_t)j + 2]};
+            double d[3];
+            exact_r2(xi, xj, D.H, s, d);
+            for (int t = 0; t < 3; ++t) r_ij[3 * q + t] = d[t];
+        }
+    }
+}
+
+}  // namespace
+
+size_t scan_tmp_ints(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 8; }
+
+int scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_t st) {
+    const int nb = (n + kScanBlock - 1) / kScanBlock;
+    if (nb == 0) {
+        cudaMemsetAsync(out, 0, sizeof(int), st);
+        return 1;
+    }
+    k_scan_blocks<<<nb, kScanThreads, 0, st>>>(in, out, n, tmp);
+    k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb, out + n);
+    k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, n, tmp);
+    return 3;
+}
+
+int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double* pos, const int* types,
+                    const double* cells, double rsearch, bool fp64, int cap, cudaStream_t st, int S) {
+    int launches = 0;
+    const size_t N = (size_t)n;
+    const size_t realsz = fp64 ? 8 : 4;
+    const size_t bins_max = N + K + 1;
+    if (nb.count.reserve(N * 4) || nb.jz.reserve(N * cap * 4) || nb.shift.reserve(N * cap * 4) ||
+        nb.rev.reserve(N * cap * 4) || nb.rx.reserve(N * cap * realsz) || nb.ry.reserve(N * cap * realsz) ||
+        nb.rz.reserve(N * cap * realsz) || nb.cfg_of.reserve(N * 4) || nb.desc.reserve(sizeof(CellDesc) * K) ||
+        nb.atom_bin.reserve(N * 4) || nb.atom_wrap.reserve(N * 4) || nb.atom_local.reserve(N * 16) ||
+        nb.bin_count.reserve(bins_max * 4) || nb.bin_start.reserve((bins_max + 1) * 4) ||
+        nb.bin_fill.reserve(bins_max * 4) || nb.bin_atoms.reserve(N * 4 + 4) ||
+        nb.scan_tmp.reserve(4 * (scan_tmp_ints((int)bins_max) + scan_tmp_ints(K + 1) + 16)) ||
+        nb.err.reserve(4) || nb.max_seen.reserve(4))
+        return -1;
+    nb.n_atoms = n;
+    nb.n_cfg = K;
+    nb.cap = cap;
+    nb.fp64 = fp64;
+    nb.rsearch = rsearch;
+    CellDesc* desc = nb.desc.as<CellDesc>();
+    int* bin_count = nb.bin_count.as<int>();
+    int* bin_start = nb.bin_start.as<int>();
+    int* tmp = nb.scan_tmp.as<int>();
+    // bins per configuration -> offsets (reuse bin_fill as scratch for the per-config counts)
+    int* cfg_bins = nb.bin_fill.as<int>();
+    k_cells<<<(K + 127) / 128, 128, 0, st>>>(K, cells, cfg_off, rsearch, desc, cfg_bins, nb.err.as<int>());
+    ++launches;
+    int* cfg_bin0 = nb.bin_start.as<int>();  // temporary: K+1 ints
+    launches += scan_exclusive(cfg_bins, cfg_bin0, K, tmp, st);
+    k_cells_offsets<<<(K + 127) / 128, 128, 0, st>>>(K, cfg_bin0, desc);
+    ++launches;
+    const int total_bins_upper = n + K;  // every configuration has at most max(1, atoms) bins
+    cudaMemsetAsync(bin_count, 0, (size_t)(total_bins_upper + 1) * 4, st);
+    cudaMemsetAsync(nb.bin_fill.p, 0, (size_t)(total_bins_upper + 1) * 4, st);
+    k_bin_atoms<<<(n + 255) / 256, 256, 0, st>>>(n, K, pos, types, S, cfg_off, desc, nb.cfg_of.as<int>(),
+                                                nb.atom_bin.as<int>(), nb.atom_wrap.as<int>(),
+                                                nb.atom_local.as<float4>(), bin_count, nb.err.as<int>());
+    ++launches;
+    launches += scan_exclusive(bin_count, bin_start, total_bins_upper, tmp, st);
+    k_bin_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, nb.atom_bin.as<int>(), bin_start, nb.bin_fill.as<int>(),
+                                                  nb.bin_atoms.as<int>());
+    ++launches;
+    BuildArgs a;
+    a.n = n;
+    a.cap = cap;
+    a.S = S;
+    a.rs2 = rsearch * rsearch;
+    a.lo2 = (float)((rsearch - kBand) * (rsearch - kBand));
+    a.hi2 = (float)((rsearch + kBand) * (rsearch + kBand));
+    a.pos = pos;
+    a.types = types;
+    a.cfg_of = nb.cfg_of.as<int>();
+    a.desc = desc;
+    a.atom_bin = nb.atom_bin.as<int>();
+    a.atom_wrap = nb.atom_wrap.as<int>();
+    a.local = nb.atom_local.as<float4>();
+    a.bin_start = bin_start;
+    a.bin_atoms = nb.bin_atoms.as<int>();
+    a.count = nb.count.as<int>();
+    a.jz = nb.jz.as<int>();
+    a.shift = nb.shift.as<int>();
+    a.rx = nb.rx.p;
+    a.ry = nb.ry.p;
+    a.rz = nb.rz.p;
+    a.err = nb.err.as<int>();
+    a.max_seen = nb.max_seen.as<int>();
+    const int threads = 128, wpb = threads / 32;
+    const size_t smem = (size_t)wpb * cap * (8 + 3 * realsz);
+    int blocks = (n + wpb - 1) / wpb;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (fp64) {
+        cudaFuncSetAttribute(k_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_build<double><<<blocks, threads, smem, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_build<float><<<blocks, threads, smem, st>>>(a);
+    }
+    ++launches;
+    k_reverse<<<(n + 127) / 128, 128, 0, st>>>(n, nb.count.as<int>(), nb.jz.as<int>(), nb.shift.as<int>(),
+                                              nb.rev.as<int>());
+    ++launches;
+    return cudaGetLastError() == cudaSuccess ? launches : -1;
+}
+
+int export_neighbors(const NbrState& nb, const double* pos, const int* offsets, int* nbr_j, int* nbr_s,
+                     double* r_ij, cudaStream_t st) {
+    const int n = nb.n_atoms;
+    k_export<<<(n + 127) / 128, 128, 0, st>>>(n, pos, nb.desc.as<CellDesc>(), nb.cfg_of.as<int>(),
+                                              nb.count.as<int>(), nb.jz.as<int>(), nb.shift.as<int>(), offsets,
+                                              nbr_j, nbr_s, r_ij);
+    return 1;
+}
+
+}  // namespace mtp

@@ -1,0 +1,273 @@
+"""Python binding of libmtp.so (the C ABI declared in include/mtp.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA kernels.
+torch provides device memory and streams.  The library is loaded from the package's in-tree
+build directory; if it is missing the import of this module still works but load() raises, so a
+GPU run can never fall back to another implementation.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmtp.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "mtp.h")
+
+FP64, FP32 = 0, 1
+HOST_MEMORY, ASYNC, REUSE_NEIGHBORS = 1, 2, 4
+STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EOVERFLOW", 5: "ESINGULAR", 6: "ETIMEOUT",
+          7: "ENOACTIVESET", 8: "EUNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MTPError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+
+
+def header_functions():
+    """Names of the functions declared in include/mtp.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\*?\s+\**(mtp_[a-z_0-9]+)\s*\(", text, re.M)))
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_L = ctypes.c_int64
+_Z = ctypes.c_size_t
+
+_SIGS = {
+    "mtp_status_str": (ctypes.c_char_p, [_I]),
+    "mtp_create": (_I, [_I, _I, _I, _D, _D, _P, _P, _I, ctypes.POINTER(_P)]),
+    "mtp_destroy": (None, [_P]),
+    "mtp_basis_count": (_I, [_P]),
+    "mtp_radial_count": (_I, [_P]),
+    "mtp_moment_count": (_I, [_P]),
+    "mtp_level_table": (_I, [_P, _P, _Z, ctypes.POINTER(_Z)]),
+    "mtp_set_params": (_I, [_P, _P, _P]),
+    "mtp_set_neighbor_capacity": (_I, [_P, _I]),
+    "mtp_last_neighbor_max": (_I, [_P]),
+    "mtp_neighbors": (_I, [_P, _I, _I, _P, _P, _P, _D, _P, _P, _P, _P, _L, _I, _P]),
+    "mtp_eval_batch": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
+    "mtp_eval": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
+    "mtp_sync": (_I, [_P, _P]),
+    "mtp_launch_count": (_L, [_P]),
+    "mtp_profile": (_I, [_P, _I]),
+    "mtp_profile_read": (_I, [_P, _P, _I, ctypes.POINTER(_L)]),
+}
+
+PHASES = ("neighbors", "moments", "contract", "pairgrad", "gather")
+
+
+def load():
+    """Load the in-tree libmtp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libmtp.so not built ({LIB_PATH}); run __graft_entry__.build()")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                if hasattr(lib, name):
+                    fn = getattr(lib, name)
+                    fn.restype = res
+                    fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(code, what):
+    if code != 0:
+        raise MTPError(code, what)
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _stream(stream):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# -- functions with the names of the C ABI (thin forwards) ---------------------------------------
+def mtp_status_str(code):
+    return load().mtp_status_str(code).decode()
+
+
+def mtp_create(lev_max, n_species, n_radial, r_min, r_cut, xi=None, c=None, precision=FP64):
+    lib = load()
+    h = ctypes.c_void_p()
+    xi_a = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64)
+    c_a = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+    _check(lib.mtp_create(int(lev_max), int(n_species), int(n_radial), float(r_min), float(r_cut), _ptr(xi_a),
+                          _ptr(c_a), int(precision), ctypes.byref(h)), "mtp_create")
+    return h
+
+
+def mtp_destroy(h):
+    load().mtp_destroy(h)
+
+
+def mtp_level_table(h):
+    lib = load()
+    n = ctypes.c_size_t()
+    _check(lib.mtp_level_table(h, None, 0, ctypes.byref(n)), "mtp_level_table")
+    buf = np.zeros(n.value, dtype=np.int32)
+    _check(lib.mtp_level_table(h, _ptr(buf), n.value, ctypes.byref(n)), "mtp_level_table")
+    return buf
+
+
+def mtp_set_params(h, xi=None, c=None):
+    xi_a = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64)
+    c_a = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+    _check(load().mtp_set_params(h, _ptr(xi_a), _ptr(c_a)), "mtp_set_params")
+
+
+def mtp_eval_batch(h, n_cfg, n_atoms, cfg_off, pos, types, cells, energy=None, forces=None, virial=None,
+                   site_energy=None, b_rows=None, b_atoms=None, grade_cfg=None, grade_atom=None, flags=0,
+                   stream=None):
+    s = None if flags & HOST_MEMORY else _stream(stream)
+    code = load().mtp_eval_batch(h, int(n_cfg), int(n_atoms), _ptr(cfg_off), _ptr(pos), _ptr(types), _ptr(cells),
+                                 _ptr(energy), _ptr(forces), _ptr(virial), _ptr(site_energy), _ptr(b_rows),
+                                 _ptr(b_atoms), _ptr(grade_cfg), _ptr(grade_atom), int(flags), s)
+    _check(code, "mtp_eval_batch")
+
+
+def mtp_neighbors(h, n_cfg, n_atoms, cfg_off, pos, cells, skin, counts, nbr_j=None, nbr_s=None, r_ij=None,
+                  cap_pairs=0, flags=0, stream=None):
+    code = load().mtp_neighbors(h, int(n_cfg), int(n_atoms), _ptr(cfg_off), _ptr(pos), _ptr(cells), float(skin),
+                                _ptr(counts), _ptr(nbr_j), _ptr(nbr_s), _ptr(r_ij), int(cap_pairs), int(flags),
+                                _stream(stream))
+    _check(code, "mtp_neighbors")
+
+
+def mtp_sync(h, stream=None):
+    _check(load().mtp_sync(h, _stream(stream)), "mtp_sync")
+
+
+def mtp_launch_count(h):
+    return int(load().mtp_launch_count(h))
+
+
+def mtp_profile(h, enable):
+    _check(load().mtp_profile(h, int(bool(enable))), "mtp_profile")
+
+
+def mtp_profile_read(h):
+    """{phase: total ms} and the number of evaluations accumulated."""
+    ms = np.zeros(len(PHASES))
+    calls = ctypes.c_int64()
+    _check(load().mtp_profile_read(h, _ptr(ms), len(PHASES), ctypes.byref(calls)), "mtp_profile_read")
+    return dict(zip(PHASES, ms.tolist())), int(calls.value)
+
+
+# -- convenience wrapper ----------------------------------------------------------------------------
+class Model:
+    """One potential on the current CUDA device (theta = {xi, c}, Sec. 2.1)."""
+
+    def __init__(self, lev_max, n_species, n_radial, r_min, r_cut, xi=None, c=None, precision="fp64"):
+        prec = {"fp64": FP64, "fp32": FP32}[precision] if isinstance(precision, str) else int(precision)
+        self.precision = prec
+        self.h = mtp_create(lev_max, n_species, n_radial, r_min, r_cut, xi, c, prec)
+        lib = load()
+        self.m = lib.mtp_basis_count(self.h)
+        self.n_mu = lib.mtp_radial_count(self.h)
+        self.n_components = lib.mtp_moment_count(self.h)
+
+    @classmethod
+    def from_params(cls, p, precision="fp64"):
+        return cls(p.lev_max, p.n_species, p.n_radial, p.r_min, p.r_cut, p.xi, p.c, precision)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mtp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_table(self):
+        return mtp_level_table(self.h)
+
+    def set_params(self, xi=None, c=None):
+        mtp_set_params(self.h, xi, c)
+
+    def set_neighbor_capacity(self, cap):
+        _check(load().mtp_set_neighbor_capacity(self.h, int(cap)), "mtp_set_neighbor_capacity")
+
+    @property
+    def launch_count(self):
+        return mtp_launch_count(self.h)
+
+    def eval_batch(self, pos, types, cells, cfg_off, forces=True, virial=True, site=False, b_rows=False,
+                   b_atoms=False, stream=None, flags=0):
+        """Device tensors in (float64 pos [N,3], int32 types [N], float64 cells [K,3,3], int32 cfg_off [K+1]);
+        device tensors out."""
+        import torch
+
+        dev = pos.device
+        K = cells.shape[0]
+        N = pos.shape[0]
+        f64 = dict(dtype=torch.float64, device=dev)
+        out = {"energy": torch.empty(K, **f64)}
+        if forces:
+            out["forces"] = torch.empty((N, 3), **f64)
+        if virial:
+            out["virial"] = torch.empty((K, 3, 3), **f64)
+        if site:
+            out["site"] = torch.empty(N, **f64)
+        if b_rows:
+            out["b_rows"] = torch.empty((K, self.m), **f64)
+        if b_atoms:
+            out["b_atoms"] = torch.empty((N, self.m), **f64)
+        mtp_eval_batch(self.h, K, N, cfg_off, pos, types, cells, out["energy"], out.get("forces"), out.get("virial"),
+                       out.get("site"), out.get("b_rows"), out.get("b_atoms"), None, None, flags, stream)
+        return out
+
+    def eval(self, pos, types, cell, **kw):
+        import torch
+
+        off = torch.tensor([0, pos.shape[0]], dtype=torch.int32, device=pos.device)
+        out = self.eval_batch(pos, types, cell.reshape(1, 3, 3), off, **kw)
+        out["energy"] = out["energy"][0]
+        if "virial" in out:
+            out["virial"] = out["virial"][0]
+        if "b_rows" in out:
+            out["b_rows"] = out["b_rows"][0]
+        return out
+
+    def neighbors(self, pos, cells, cfg_off, skin=0.0):
+        """Canonical neighbour lists: (counts [N], j [P], s [P,3], r_ij [P,3] float64), device tensors."""
+        import torch
+
+        N = pos.shape[0]
+        K = cells.shape[0]
+        counts = torch.empty(N, dtype=torch.int32, device=pos.device)
+        mtp_neighbors(self.h, K, N, cfg_off, pos, cells, skin, counts)
+        P = int(counts.sum().item())
+        j = torch.empty(max(P, 1), dtype=torch.int32, device=pos.device)
+        s = torch.empty((max(P, 1), 3), dtype=torch.int32, device=pos.device)
+        r = torch.empty((max(P, 1), 3), dtype=torch.float64, device=pos.device)
+        mtp_neighbors(self.h, K, N, cfg_off, pos, cells, skin, counts, j, s, r, P)
+        return counts, j[:P], s[:P], r[:P]
