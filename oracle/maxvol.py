@@ -15,8 +15,11 @@ Readings where the paper is silent (each stated in the design notes):
   * start: the m pivot rows of Gaussian elimination with partial pivoting on B;
   * a sweep computes C = B A^{-1} for every row, takes the largest |C_kj| (ties: the first in
     row-major order, i.e. smallest row k, then smallest column j) and swaps while it exceeds
-    1 + tol (tol = 1e-9);
-  * at most max_iter = 100 m swaps.
+    1 + tol (tol = 1e-6: rounding noise of C on ill-conditioned rows exceeds 1e-9 and would
+    make the swaps cycle);
+  * at most max_iter = 100 m swaps;
+  * the columns of B are first scaled by 1 / max |column|: C = B A^{-1} is unchanged by B -> B D
+    (it becomes B D (A D)^{-1}), so this only conditions the arithmetic.
 """
 
 from __future__ import annotations
@@ -34,17 +37,27 @@ def b_rows(b_atoms, cfg_off):
     return out
 
 
+def equilibrate(B):
+    """Column scaling D = diag(1 / max_r |B_rc|) and B D."""
+    B = np.asarray(B, dtype=np.float64)
+    mx = np.abs(B).max(axis=0)
+    if np.any(mx == 0.0):
+        raise np.linalg.LinAlgError("zero column")
+    return B / mx, 1.0 / mx
+
+
 def pivot_rows(B):
-    """Row indices chosen as pivots by LU with partial pivoting, in pivot order."""
+    """Row indices chosen as pivots by LU with partial pivoting, in pivot order: B = P L U, and
+    row k of P^T B (the k-th pivot row) is row argmax_r P[r, k] of B."""
     B = np.asarray(B, dtype=np.float64)
     m = B.shape[1]
-    perm, _, _ = scipy.linalg.lu(B, p_indices=True)
-    return np.asarray(perm[:m], dtype=np.int64)
+    P, _, _ = scipy.linalg.lu(B)
+    return np.asarray([int(np.argmax(P[:, k])) for k in range(m)], dtype=np.int64)
 
 
-def maxvol(B, tol=1e-9, max_iter=None):
+def maxvol(B, tol=1e-6, max_iter=None):
     """Active set of m rows of the tall matrix B.  Returns (rows [m], swaps, final max |C|)."""
-    B = np.asarray(B, dtype=np.float64)
+    B, _ = equilibrate(B)
     K, m = B.shape
     if K < m:
         raise ValueError("need at least m rows")
@@ -67,6 +80,8 @@ def maxvol(B, tol=1e-9, max_iter=None):
 
 
 def grades(B_rows, A):
-    """gamma = max_j |(b A^{-1})_j| for every row b (Sec. 2.3)."""
-    C = np.asarray(B_rows, dtype=np.float64) @ np.linalg.inv(np.asarray(A, dtype=np.float64))
+    """gamma = max_j |(b A^{-1})_j| for every row b (Sec. 2.3), evaluated as (b D)(A D)^{-1}."""
+    A = np.asarray(A, dtype=np.float64)
+    _, d = equilibrate(A)
+    C = (np.asarray(B_rows, dtype=np.float64) * d) @ np.linalg.inv(A * d)
     return np.abs(C).max(axis=1)
