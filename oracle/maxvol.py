@@ -62,7 +62,8 @@ def maxvol(B, tol=1e-6, max_iter=None):
     if K < m:
         raise ValueError("need at least m rows")
     sel = pivot_rows(B)
-    if abs(np.linalg.det(B[sel])) == 0.0:
+    _, _, U = scipy.linalg.lu(B)
+    if np.any(np.diag(U)[:m] == 0.0):  # an exactly zero pivot; det() would underflow long before
         raise np.linalg.LinAlgError("singular start")
     max_iter = 100 * m if max_iter is None else max_iter
     swaps = 0
