@@ -147,6 +147,32 @@ mtp_status mtp_eval(mtp_model* model, int n_atoms, const double* pos, const int3
                     double* energy, double* forces, double* virial, double* site_energy, double* grade_cfg,
                     double* grade_atom, int flags, void* stream);
 
+/*
+ * Active set by MaxVol (Sec. 2.3, Eq. 13; Goreinov et al. 2010).  Chooses m of the n_rows >= m rows of
+ * the tall matrix b_rows [n_rows][m] (double) so that |det A| of the m x m submatrix cannot grow by
+ * exchanging one row: start from the pivot rows of Gaussian elimination with partial pivoting, then
+ * repeatedly let the row and column of the largest |c| of C = B A^-1 swap in, while it exceeds 1 + 1e-6
+ * (ties: smallest row, then smallest column), at most 100 m swaps.  Columns are first scaled by
+ * 1 / max |column|, which changes neither C nor the selection but conditions the arithmetic.  A and A^-1 (double) stay in the
+ * model for grades.  selected[m] receives the chosen row indices (position j = row of A), n_swaps the
+ * number of exchanges and max_grade the final max |C| (each may be NULL).  MTP_HOST_MEMORY: b_rows and
+ * selected are host arrays.  Synchronous.  MTP_ESINGULAR: B has rank < m; MTP_ETIMEOUT: swap limit.
+ */
+mtp_status mtp_select_active_set(mtp_model* model, int n_rows, const double* b_rows, int32_t* selected, int* n_swaps,
+                                 double* max_grade, int flags, void* stream);
+
+/* Install an active set given its m x m matrix A (host, row-major; rows = b of the active configurations);
+ * A^-1 is computed on the device.  MTP_ESINGULAR if A is singular. */
+mtp_status mtp_set_active_set(mtp_model* model, const double* A);
+
+/* Copy out A, A^-1 (host [m][m], may be NULL) and the selected row indices (host [m], -1 when A was set
+ * directly; may be NULL).  MTP_ENOACTIVESET without an active set. */
+mtp_status mtp_get_active_set(const mtp_model* model, double* A, double* A_inv, int32_t* rows);
+
+/* Extrapolation grade of arbitrary rows (Sec. 2.3): gamma[r] = max_j |(b_r A^-1)_j| for b_rows
+ * [n_rows][m] (double), in double precision.  Device arrays unless MTP_HOST_MEMORY. */
+mtp_status mtp_grade(mtp_model* model, int n_rows, const double* b_rows, double* gamma, int flags, void* stream);
+
 /* Wait for the model's work on `stream` and report errors detected on the device since the last
  * check (MTP_EOVERFLOW, MTP_EINVAL for bad species or shifts). */
 mtp_status mtp_sync(mtp_model* model, void* stream);

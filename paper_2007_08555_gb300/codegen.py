@@ -667,6 +667,60 @@ def flop_counts(prog: Program):
     }
 
 
+UNROLLED_MAX_LEVEL = 16  # above this the straight-line code no longer fits the register file
+
+
+def emit_unrolled(prog: Program):
+    """Straight-line thread-per-atom contraction (float): forward program in creation order, site
+    energy, then the adjoint in reverse creation order, every value an SSA register (the compiler
+    spills what does not fit).  Moments are read from and dV/dM written to the tile layout
+    [tile][C][32] at src[c * 32] / dst[c * 32]."""
+    C = len(prog.comp_list)
+    by_k = defaultdict(list)
+    for (k, i, j, w) in prog.ops:
+        by_k[k].append((i, j, w))
+    out = ["template <bool WANT_B>",
+           "__device__ __forceinline__ float contract_unrolled(const float* __restrict__ src, float* __restrict__ dst, "
+           "const float* __restrict__ xi, double* __restrict__ bout) {"]
+    for c in range(C):
+        out.append(f"  const float v{c} = src[{c * 32}];")
+
+    def lit(w):
+        return "" if w == 1.0 else f"{w!r}f * "
+
+    for k in sorted(by_k):
+        terms = [f"{lit(w)}v{i} * v{j}" for (i, j, w) in by_k[k]]
+        out.append(f"  const float v{k} = " + " + ".join(terms) + ";")
+    out.append("  float e = 0.f;")
+    for a, v in enumerate(prog.basis_value):
+        out.append(f"  e += xi[{a}] * v{v};")
+        out.append(f"  if (WANT_B) bout[{a}] = (double)v{v};")
+    seed = defaultdict(list)
+    for a, v in enumerate(prog.basis_value):
+        seed[v].append(a)
+    declared = set()
+
+    def aref(v):
+        if v not in declared:
+            declared.add(v)
+            init = " + ".join(f"xi[{a}]" for a in seed.get(v, [])) or "0.f"
+            out.append(f"  float a{v} = {init};")
+        return f"a{v}"
+
+    for k in sorted(by_k, reverse=True):
+        ak = aref(k)
+        for (i, j, w) in by_k[k]:
+            ai = aref(i)
+            aj = aref(j)
+            out.append(f"  {ai} += {lit(w)}v{j} * {ak};")
+            out.append(f"  {aj} += {lit(w)}v{i} * {ak};")
+    for c in range(C):
+        out.append(f"  dst[{c * 32}] = {aref(c)};")
+    out.append("  return e;")
+    out.append("}")
+    return out
+
+
 def emit_level(L, outdir):
     prog = build_program(L)
     fwd_rows, fwd_layers = encode_layout(forward_layout(prog))
@@ -696,19 +750,20 @@ def emit_level(L, outdir):
     lines.append("static const unsigned char comp_abc[] = {" +
                  ",".join(f"{a},{b},{c}" for _, (a, b, c) in prog.comp_list) + "};")
 
+    # one 64-bit word per (row, lane): i | j << 16 | k << 32 | flags << 48 | weight index << 51
+    weights = sorted({float(ww) for rows in (fwd_rows, adj_rows) for row in rows for (_, _, _, _, ww) in row})
+    widx = {w: k for k, w in enumerate(weights)}
+    assert len(weights) < (1 << 13)
+
     def rows_to_c(name, rows):
-        ij = []
-        kf = []
-        w = []
+        words = []
         for row in rows:
             for (a, b, k, f, ww) in row:
-                ij.append(f"{a | (b << 16)}u")
-                kf.append(f"{k | (f << 16)}u")
-                w.append(repr(float(ww)))
-        lines.append(f"static const unsigned {name}_ij[] = {{" + ",".join(ij or ["0u"]) + "};")
-        lines.append(f"static const unsigned {name}_kf[] = {{" + ",".join(kf or ["0u"]) + "};")
-        lines.append(f"static const float {name}_w[] = {{" + ",".join(w or ["0.0"]) + "};")
+                words.append(f"{a | (b << 16) | (k << 32) | (f << 48) | (widx[float(ww)] << 51)}ull")
+        lines.append(f"static const unsigned long long {name}_ops[] = {{" + ",".join(words or ["0ull"]) + "};")
 
+    lines.append(f"constexpr int NWEIGHTS = {len(weights)};")
+    lines.append("static const float weights[] = {" + ",".join(repr(w) for w in weights) + "};")
     rows_to_c("fwd", fwd_rows)
     rows_to_c("adj", adj_rows)
     lines.append("static const int fwd_layer_rows[] = {" + ",".join(str(e) for _, e in fwd_layers) + "};")
@@ -720,6 +775,11 @@ def emit_level(L, outdir):
         lines.append(f"static const int {name}_size[] = {{" + ",".join(str(len(c)) for _, c in sl) + "};")
         for s, (_, comps) in enumerate(sl):
             assert comps == list(range(min(comps), min(comps) + len(comps)))
+    if L <= UNROLLED_MAX_LEVEL and prog.ops:
+        lines.append("#define MTPGEN_HAS_UNROLLED 1")
+        lines += emit_unrolled(prog)
+    else:
+        lines.append("#define MTPGEN_HAS_UNROLLED 0")
     lines += emit_slice_functions(prog, s32, "f")
     lines += emit_slice_functions(prog, s64, "d")
     lines.append("struct Traits {")

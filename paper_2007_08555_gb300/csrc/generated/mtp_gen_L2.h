@@ -13,18 +13,17 @@ constexpr int LEVEL_TABLE_LEN = 6;
 static const int basis_value[] = {0};
 static const unsigned char comp_mu[] = {0};
 static const unsigned char comp_abc[] = {0,0,0};
-static const unsigned fwd_ij[] = {0u};
-static const unsigned fwd_kf[] = {0u};
-static const float fwd_w[] = {0.0};
-static const unsigned adj_ij[] = {0u};
-static const unsigned adj_kf[] = {0u};
-static const float adj_w[] = {0.0};
+constexpr int NWEIGHTS = 0;
+static const float weights[] = {};
+static const unsigned long long fwd_ops[] = {0ull};
+static const unsigned long long adj_ops[] = {0ull};
 static const int fwd_layer_rows[] = {};
 static const int adj_layer_rows[] = {};
 static const int s32_begin[] = {0};
 static const int s32_size[] = {1};
 static const int s64_begin[] = {0};
 static const int s64_size[] = {1};
+#define MTPGEN_HAS_UNROLLED 0
 template <int S> struct SliceF;
 template <> struct SliceF<0> {
   static constexpr int BEGIN = 0, SIZE = 1;

@@ -13,18 +13,33 @@ constexpr int LEVEL_TABLE_LEN = 14;
 static const int basis_value[] = {0,1};
 static const unsigned char comp_mu[] = {0};
 static const unsigned char comp_abc[] = {0,0,0};
-static const unsigned fwd_ij[] = {0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u};
-static const unsigned fwd_kf[] = {196609u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u};
-static const float fwd_w[] = {1.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0};
-static const unsigned adj_ij[] = {65536u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,65536u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u,0u};
-static const unsigned adj_kf[] = {65536u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,131072u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u,262144u};
-static const float adj_w[] = {1.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,1.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0,0.0};
+constexpr int NWEIGHTS = 2;
+static const float weights[] = {0.0,1.0};
+static const unsigned long long fwd_ops[] = {3096229038784512ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull};
+static const unsigned long long adj_ops[] = {2533274790461440ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,2814749767172096ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull,1125899906842624ull};
 static const int fwd_layer_rows[] = {1};
 static const int adj_layer_rows[] = {2};
 static const int s32_begin[] = {0};
 static const int s32_size[] = {1};
 static const int s64_begin[] = {0};
 static const int s64_size[] = {1};
+#define MTPGEN_HAS_UNROLLED 1
+template <bool WANT_B>
+__device__ __forceinline__ float contract_unrolled(const float* __restrict__ src, float* __restrict__ dst, const float* __restrict__ xi, double* __restrict__ bout) {
+  const float v0 = src[0];
+  const float v1 = v0 * v0;
+  float e = 0.f;
+  e += xi[0] * v0;
+  if (WANT_B) bout[0] = (double)v0;
+  e += xi[1] * v1;
+  if (WANT_B) bout[1] = (double)v1;
+  float a1 = xi[1];
+  float a0 = xi[0];
+  a0 += v0 * a1;
+  a0 += v0 * a1;
+  dst[0] = a0;
+  return e;
+}
 template <int S> struct SliceF;
 template <> struct SliceF<0> {
   static constexpr int BEGIN = 0, SIZE = 1;

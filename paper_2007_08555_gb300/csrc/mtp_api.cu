@@ -48,7 +48,7 @@ struct mtp_model {
     int device = 0, n_sm = 152;
     std::vector<double> xi, c;
     DevBuf d_xi, d_c, d_seed, d_basis_value;
-    DevBuf d_fwd_ij, d_fwd_kf, d_fwd_w, d_fwd_layers, d_adj_ij, d_adj_kf, d_adj_w, d_adj_layers;
+    DevBuf d_fwd_ops, d_fwd_layers, d_adj_ops, d_adj_layers, d_weights;
     mtp::NbrState nb;
     DevBuf mom, adjm, gx, gy, gz;
     // staging for MTP_HOST_MEMORY calls
@@ -56,6 +56,10 @@ struct mtp_model {
     int cap = 128;
     int last_max = 0;
     int64_t launches = 0;
+    // active set (Sec. 2.3): rows of the last selection, A and A^-1 in double precision
+    bool has_active = false;
+    std::vector<int> active_rows;
+    DevBuf d_A, d_Ai, mv_Bs, mv_D, mv_W, mv_perm, mv_sel, mv_C, mv_status, mv_swaps, mv_gmax, s_rows, s_gamma, g_brows, g_batoms;
     // profiling: events around the neighbour build and each evaluation phase
     bool profiling = false;
     cudaEvent_t ev_nbr[2] = {nullptr, nullptr};
@@ -140,6 +144,7 @@ mtp_status run_eval(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     a.inv_span = (T)(1.0 / (M->rcut - M->rmin));
     a.types = types;
     a.cfg_of = M->nb.cfg_of.as<int>();
+    a.cfg_off = cfg_off;
     a.count = M->nb.count.as<int>();
     a.jz = M->nb.jz.as<int>();
     a.rev = M->nb.rev.as<int>();
@@ -150,16 +155,14 @@ mtp_status run_eval(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     a.xi = M->d_xi.as<T>();
     a.seed = M->d_seed.as<T>();
     a.basis_value = M->d_basis_value.as<int>();
-    a.fwd_ij = M->d_fwd_ij.as<unsigned>();
-    a.fwd_kf = M->d_fwd_kf.as<unsigned>();
-    a.fwd_w = M->d_fwd_w.as<float>();
+    a.fwd_ops = M->d_fwd_ops.as<unsigned long long>();
     a.fwd_layer_end = M->d_fwd_layers.as<int>();
     a.fwd_layers = M->ops->fwd_layers;
-    a.adj_ij = M->d_adj_ij.as<unsigned>();
-    a.adj_kf = M->d_adj_kf.as<unsigned>();
-    a.adj_w = M->d_adj_w.as<float>();
+    a.adj_ops = M->d_adj_ops.as<unsigned long long>();
     a.adj_layer_end = M->d_adj_layers.as<int>();
     a.adj_layers = M->ops->adj_layers;
+    a.weights = M->d_weights.as<float>();
+    a.n_weights = M->ops->n_weights;
     a.tpa = choose_tpa(n, M->n_sm);
     a.mom = M->mom.as<T>();
     a.adjm = M->adjm.as<T>();
@@ -277,14 +280,11 @@ mtp_status mtp_create(int lev_max, int n_species, int n_radial, double r_min, do
     mtp_status st = MTP_OK;
     const int fr = ops->fwd_rows * 32, ar = ops->adj_rows * 32;
     if (!st) st = upload(M->d_basis_value, ops->basis_value, M->m);
-    if (!st) st = upload(M->d_fwd_ij, ops->fwd_ij, fr);
-    if (!st) st = upload(M->d_fwd_kf, ops->fwd_kf, fr);
-    if (!st) st = upload(M->d_fwd_w, ops->fwd_w, fr);
+    if (!st) st = upload(M->d_fwd_ops, ops->fwd_ops, fr);
     if (!st) st = upload(M->d_fwd_layers, ops->fwd_layer_end, ops->fwd_layers);
-    if (!st) st = upload(M->d_adj_ij, ops->adj_ij, ar);
-    if (!st) st = upload(M->d_adj_kf, ops->adj_kf, ar);
-    if (!st) st = upload(M->d_adj_w, ops->adj_w, ar);
+    if (!st) st = upload(M->d_adj_ops, ops->adj_ops, ar);
     if (!st) st = upload(M->d_adj_layers, ops->adj_layer_end, ops->adj_layers);
+    if (!st) st = upload(M->d_weights, ops->weights, ops->n_weights);
     if (!st) st = upload_params(M);
     if (st) {
         mtp_destroy(M);
@@ -296,14 +296,16 @@ mtp_status mtp_create(int lev_max, int n_species, int n_radial, double r_min, do
 
 void mtp_destroy(mtp_model* M) {
     if (!M) return;
-    DevBuf* bufs[] = {&M->d_xi, &M->d_c, &M->d_seed, &M->d_basis_value, &M->d_fwd_ij, &M->d_fwd_kf, &M->d_fwd_w,
-                      &M->d_fwd_layers, &M->d_adj_ij, &M->d_adj_kf, &M->d_adj_w, &M->d_adj_layers, &M->mom,
+    DevBuf* bufs[] = {&M->d_xi, &M->d_c, &M->d_seed, &M->d_basis_value, &M->d_fwd_ops, &M->d_fwd_layers,
+                      &M->d_adj_ops, &M->d_adj_layers, &M->d_weights, &M->mom,
                       &M->adjm, &M->gx, &M->gy, &M->gz, &M->s_off, &M->s_pos, &M->s_types, &M->s_cells,
                       &M->s_energy, &M->s_forces, &M->s_virial, &M->s_site, &M->s_brows, &M->s_batoms,
                       &M->nb.count, &M->nb.jz, &M->nb.shift, &M->nb.rev, &M->nb.rx, &M->nb.ry, &M->nb.rz,
                       &M->nb.cfg_of, &M->nb.desc, &M->nb.atom_bin, &M->nb.atom_wrap, &M->nb.atom_local,
                       &M->nb.bin_count, &M->nb.bin_start, &M->nb.bin_fill, &M->nb.bin_atoms, &M->nb.scan_tmp,
-                      &M->nb.err, &M->nb.max_seen};
+                      &M->nb.err, &M->nb.max_seen, &M->d_A, &M->d_Ai, &M->mv_Bs, &M->mv_D, &M->mv_W, &M->mv_perm, &M->mv_sel,
+                      &M->mv_C, &M->mv_status, &M->mv_swaps, &M->mv_gmax, &M->s_rows, &M->s_gamma, &M->g_brows,
+                      &M->g_batoms};
     for (DevBuf* b : bufs) b->release();
     for (cudaEvent_t& e : M->ev_nbr)
         if (e) cudaEventDestroy(e);
@@ -371,7 +373,10 @@ static mtp_status check_batch(mtp_model* M, int K, int n, const int32_t* off, co
 
 static mtp_status prepare_neighbors(mtp_model* M, int K, int n, const int* off, const double* pos,
                                     const int* types, const double* cells, double skin, cudaStream_t st) {
-    if (M->nb.err.reserve(4) || M->nb.max_seen.reserve(4)) return MTP_ENOMEM;
+    if (!M->nb.err.p) {  // the error word starts at zero and is cleared after every read
+        if (M->nb.err.reserve(4) || M->nb.max_seen.reserve(4)) return MTP_ENOMEM;
+        if (cudaMemset(M->nb.err.p, 0, M->nb.err.bytes) != cudaSuccess) return MTP_ECUDA;
+    }
     cudaMemsetAsync(M->nb.max_seen.p, 0, sizeof(int), st);
     if (M->profiling) cudaEventRecord(M->ev_nbr[0], st);
     const int l = mtp::build_neighbors(M->nb, K, n, off, pos, types, cells, M->rcut + skin, is_fp64(M), M->cap,
@@ -389,8 +394,9 @@ mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, co
     mtp_status s = check_batch(M, K, n, cfg_off, pos, cells);
     if (s) return s;
     if (n > 0 && !types) return MTP_EINVAL;
-    if (grade_cfg || grade_atom) return MTP_ENOACTIVESET;
+    if ((grade_cfg || grade_atom) && !M->has_active) return MTP_ENOACTIVESET;
     if (flags & MTP_REUSE_NEIGHBORS) return MTP_EUNSUPPORTED;
+    double *h_gcfg = grade_cfg, *h_gatom = grade_atom;
     cudaStream_t st = (cudaStream_t)stream;
     const bool host = flags & MTP_HOST_MEMORY;
     double *h_energy = energy, *h_forces = forces, *h_virial = virial, *h_site = site, *h_brows = b_rows,
@@ -411,7 +417,21 @@ mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, co
         site = stage_out(M->s_site, site, n, &ok);
         b_rows = stage_out(M->s_brows, b_rows, (size_t)K * M->m, &ok);
         b_atoms = stage_out(M->s_batoms, b_atoms, (size_t)n * M->m, &ok);
+        if (grade_cfg || grade_atom) {
+            if (M->s_gamma.reserve(sizeof(double) * ((size_t)K + n) + 16)) return MTP_ENOMEM;
+            if (grade_cfg) grade_cfg = M->s_gamma.as<double>();
+            if (grade_atom) grade_atom = M->s_gamma.as<double>() + K;
+        }
         if (!ok) return MTP_ENOMEM;
+    }
+    // grades need the basis rows: use internal buffers when the caller did not ask for them
+    if (grade_cfg && !b_rows) {
+        if (M->g_brows.reserve(sizeof(double) * (size_t)K * M->m)) return MTP_ENOMEM;
+        b_rows = M->g_brows.as<double>();
+    }
+    if ((grade_atom || b_rows) && !b_atoms) {  // per-atom rows also feed the per-configuration sums
+        if (M->g_batoms.reserve(sizeof(double) * (size_t)n * M->m + 8)) return MTP_ENOMEM;
+        b_atoms = M->g_batoms.as<double>();
     }
     if ((s = prepare_neighbors(M, K, n, cfg_off, pos, types, cells, 0.0, st))) return s;
     if (is_fp64(M))
@@ -419,7 +439,15 @@ mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, co
     else
         s = run_eval<float>(M, K, n, cfg_off, types, energy, forces, virial, site, b_rows, b_atoms, st);
     if (s) return s;
+    if (grade_cfg)
+        M->launches += mtp::launch_grade<double>(K, M->m, b_rows, M->m, M->d_Ai.as<double>(),
+                                                 reinterpret_cast<unsigned long long*>(grade_cfg), st);
+    if (grade_atom)
+        M->launches += mtp::launch_grade<double>(n, M->m, b_atoms, M->m, M->d_Ai.as<double>(),
+                                                 reinterpret_cast<unsigned long long*>(grade_atom), st);
     if (host) {
+        if (h_gcfg) cudaMemcpyAsync(h_gcfg, grade_cfg, sizeof(double) * K, cudaMemcpyDeviceToHost, st);
+        if (h_gatom) cudaMemcpyAsync(h_gatom, grade_atom, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
         if (h_energy) cudaMemcpyAsync(h_energy, energy, sizeof(double) * K, cudaMemcpyDeviceToHost, st);
         if (h_forces) cudaMemcpyAsync(h_forces, forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st);
         if (h_virial) cudaMemcpyAsync(h_virial, virial, sizeof(double) * 9 * K, cudaMemcpyDeviceToHost, st);
@@ -473,6 +501,109 @@ mtp_status mtp_neighbors(mtp_model* M, int K, int n, const int32_t* cfg_off, con
     if (total > cap_pairs) return MTP_EOVERFLOW;
     mtp::export_neighbors(M->nb, pos, offs.as<int>(), nbr_j, nbr_s, r_ij, st);
     return finish(M, st);
+}
+
+mtp_status mtp_select_active_set(mtp_model* M, int n_rows, const double* b_rows, int32_t* selected, int* n_swaps,
+                                 double* max_grade, int flags, void* stream) {
+    if (!M || !b_rows || n_rows < M->m) return MTP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = M->m, n = n_rows;
+    const size_t wsz = std::max((size_t)n * m, (size_t)2 * m * m) + 2 * (size_t)m + n + 16;
+    if (M->mv_W.reserve(sizeof(double) * wsz) || M->mv_perm.reserve(sizeof(int) * n) ||
+        M->mv_sel.reserve(sizeof(int) * m) || M->d_A.reserve(sizeof(double) * m * m) ||
+        M->d_Ai.reserve(sizeof(double) * m * m) || M->mv_C.reserve(sizeof(double) * (size_t)n * m) ||
+        M->mv_status.reserve(16) || M->mv_swaps.reserve(16) || M->mv_gmax.reserve(16) ||
+        M->mv_Bs.reserve(sizeof(double) * (size_t)n * m) || M->mv_D.reserve(sizeof(double) * m))
+        return MTP_ENOMEM;
+    const double* B = b_rows;
+    if (flags & MTP_HOST_MEMORY) {
+        if (M->s_rows.reserve(sizeof(double) * (size_t)n * m)) return MTP_ENOMEM;
+        cudaMemcpyAsync(M->s_rows.p, b_rows, sizeof(double) * (size_t)n * m, cudaMemcpyHostToDevice, st);
+        B = M->s_rows.as<double>();
+    }
+    cudaMemsetAsync(M->mv_status.p, 0, sizeof(int), st);
+    M->launches += mtp::launch_maxvol(n, m, B, M->mv_Bs.as<double>(), M->mv_D.as<double>(), M->mv_W.as<double>(),
+                                      M->mv_perm.as<int>(), M->mv_sel.as<int>(), M->d_A.as<double>(),
+                                      M->d_Ai.as<double>(), M->mv_C.as<double>(), 1e-6, 100 * m,
+                                      M->mv_status.as<int>(), M->mv_swaps.as<int>(), M->mv_gmax.as<double>(), st);
+    int status = 0, swaps = 0;
+    double g = 0.0;
+    std::vector<int> sel(m);
+    cudaMemcpyAsync(&status, M->mv_status.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&swaps, M->mv_swaps.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&g, M->mv_gmax.p, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(sel.data(), M->mv_sel.p, sizeof(int) * m, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (status & mtp::kErrSingular) {
+        M->has_active = false;
+        return MTP_ESINGULAR;
+    }
+    if (status & mtp::kErrTimeout) {
+        M->has_active = false;
+        return MTP_ETIMEOUT;
+    }
+    M->active_rows = sel;
+    M->has_active = true;
+    if (n_swaps) *n_swaps = swaps;
+    if (max_grade) *max_grade = g;
+    if (selected) {
+        if (flags & MTP_HOST_MEMORY)
+            std::memcpy(selected, sel.data(), sizeof(int) * m);
+        else if (cudaMemcpy(selected, sel.data(), sizeof(int) * m, cudaMemcpyHostToDevice) != cudaSuccess)
+            return MTP_ECUDA;
+    }
+    return MTP_OK;
+}
+
+mtp_status mtp_set_active_set(mtp_model* M, const double* A) {
+    if (!M || !A) return MTP_EINVAL;
+    const int m = M->m;
+    if (M->d_A.reserve(sizeof(double) * m * m) || M->d_Ai.reserve(sizeof(double) * m * m) ||
+        M->mv_W.reserve(sizeof(double) * 2 * m * m + 16) || M->mv_status.reserve(16))
+        return MTP_ENOMEM;
+    if (cudaMemcpy(M->d_A.p, A, sizeof(double) * m * m, cudaMemcpyHostToDevice) != cudaSuccess) return MTP_ECUDA;
+    cudaMemset(M->mv_status.p, 0, sizeof(int));
+    M->launches += mtp::launch_invert(m, M->d_A.as<double>(), M->d_Ai.as<double>(), M->mv_W.as<double>(),
+                                      M->mv_status.as<int>(), 0);
+    int status = 0;
+    if (cudaMemcpy(&status, M->mv_status.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
+    M->active_rows.assign(m, -1);
+    M->has_active = !(status & mtp::kErrSingular);
+    return M->has_active ? MTP_OK : MTP_ESINGULAR;
+}
+
+mtp_status mtp_get_active_set(const mtp_model* M, double* A, double* A_inv, int32_t* rows) {
+    if (!M) return MTP_EINVAL;
+    if (!M->has_active) return MTP_ENOACTIVESET;
+    const size_t bytes = sizeof(double) * M->m * M->m;
+    if (A && cudaMemcpy(A, M->d_A.p, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
+    if (A_inv && cudaMemcpy(A_inv, M->d_Ai.p, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
+    if (rows) std::memcpy(rows, M->active_rows.data(), sizeof(int) * M->m);
+    return MTP_OK;
+}
+
+mtp_status mtp_grade(mtp_model* M, int n_rows, const double* b_rows, double* gamma, int flags, void* stream) {
+    if (!M || n_rows < 0 || (n_rows > 0 && (!b_rows || !gamma))) return MTP_EINVAL;
+    if (!M->has_active) return MTP_ENOACTIVESET;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = M->m;
+    const double* B = b_rows;
+    double* g = gamma;
+    if (flags & MTP_HOST_MEMORY) {
+        if (M->s_rows.reserve(sizeof(double) * (size_t)n_rows * m + 8) ||
+            M->s_gamma.reserve(sizeof(double) * (size_t)n_rows + 8))
+            return MTP_ENOMEM;
+        cudaMemcpyAsync(M->s_rows.p, b_rows, sizeof(double) * (size_t)n_rows * m, cudaMemcpyHostToDevice, st);
+        B = M->s_rows.as<double>();
+        g = M->s_gamma.as<double>();
+    }
+    M->launches += mtp::launch_grade<double>(n_rows, m, B, m, M->d_Ai.as<double>(),
+                                             reinterpret_cast<unsigned long long*>(g), st);
+    if (flags & MTP_HOST_MEMORY)
+        cudaMemcpyAsync(gamma, g, sizeof(double) * n_rows, cudaMemcpyDeviceToHost, st);
+    if (flags & MTP_ASYNC) return cuda_status(cudaGetLastError());
+    return cuda_status(cudaStreamSynchronize(st));
 }
 
 }  // extern "C"

@@ -29,6 +29,7 @@ struct EvalCtx {
     T rmin, rcut, inv_span;
     const int* types;     // [n]
     const int* cfg_of;    // [n] atom -> configuration
+    const int* cfg_off;   // [n_cfg + 1] first atom of each configuration
     const int* count;     // [n] neighbours of each atom
     const int* jz;        // [cap][n] neighbour index | species << 24
     const int* rev;       // [cap][n] slot of the reverse pair in the neighbour's list, -1 if absent
@@ -39,16 +40,14 @@ struct EvalCtx {
     const T* xi;          // [M]
     const T* seed;        // [V] adjoint seed: xi at the value index of each basis function
     const int* basis_value;  // [M]
-    const unsigned* fwd_ij;  // forward program rows (32 lanes per row)
-    const unsigned* fwd_kf;
-    const float* fwd_w;
+    const unsigned long long* fwd_ops;  // forward program rows (32 packed ops per row)
     const int* fwd_layer_end;
     int fwd_layers;
-    const unsigned* adj_ij;  // adjoint program rows
-    const unsigned* adj_kf;
-    const float* adj_w;
+    const unsigned long long* adj_ops;  // adjoint program rows
     const int* adj_layer_end;
     int adj_layers;
+    const float* weights;               // [n_weights] op weights
+    int n_weights;
     int tpa;              // threads per atom in the pair kernels (1, 2, 4 or 8)
     T* mom;               // [ceil(n/32)][C][32] moment components (tile layout)
     T* adjm;              // [ceil(n/32)][C][32] dV/dM

@@ -33,6 +33,7 @@ struct DevBuf {
 struct CellDesc {
     double H[9], Hi[9];
     float hn[9];  // lattice vectors divided by the bin counts, rows
+    float hhi[9], hlo[9];  // lattice vectors as float pairs (hi + lo = H to ~2^-48)
     int n[3], c[3];
     int bin0, nbins;
 };
@@ -43,7 +44,7 @@ struct NbrState {
     bool fp64 = false;
     double rsearch = 0.0;
     DevBuf count, jz, shift, rev, rx, ry, rz;
-    DevBuf cfg_of, desc, atom_bin, atom_wrap, atom_local, bin_count, bin_start, bin_fill, bin_atoms, scan_tmp;
+    DevBuf cfg_of, desc, atom_bin, atom_wrap, atom_local, atom_wp, bin_count, bin_start, bin_fill, bin_atoms, scan_tmp;
     DevBuf err, max_seen;
 };
 
@@ -56,6 +57,14 @@ int build_neighbors(NbrState& nb, int n_cfg, int n_atoms, const int* cfg_off, co
 // Exclusive prefix sum of n ints: out[0..n] with out[n] = total; tmp holds >= scan_tmp_ints(n) ints.
 size_t scan_tmp_ints(int n);
 int scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_t st);
+
+// Active set (mtp_maxvol.cu)
+int launch_maxvol(int n, int m, const double* B, double* Bs, double* D, double* W, int* perm, int* sel, double* A,
+                  double* Ai, double* C, double tol, int max_iter, int* status, int* swaps, double* gmax,
+                  cudaStream_t st);
+int launch_invert(int m, const double* A, double* Ai, double* W, int* status, cudaStream_t st);
+template <class T>
+int launch_grade(int n, int m, const T* B, int ldb, const T* Ai, unsigned long long* gbits, cudaStream_t st);
 
 // CSR export of the neighbour list with exact double-precision r_ij.
 int export_neighbors(const NbrState& nb, const double* pos, const int* offsets, int* nbr_j, int* nbr_s,

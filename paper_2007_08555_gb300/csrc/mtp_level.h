@@ -10,16 +10,14 @@ struct LevelOps {
     const int* level_table;
     int level_table_len;
     const int* basis_value;        // [M] value index of each basis function
-    const unsigned* fwd_ij;
-    const unsigned* fwd_kf;
-    const float* fwd_w;
+    const unsigned long long* fwd_ops;  // [rows][32] packed ops, see codegen.py
     const int* fwd_layer_end;
     int fwd_rows, fwd_layers;
-    const unsigned* adj_ij;
-    const unsigned* adj_kf;
-    const float* adj_w;
+    const unsigned long long* adj_ops;
     const int* adj_layer_end;
     int adj_rows, adj_layers;
+    const float* weights;               // weight table indexed by the packed ops
+    int n_weights;
     int program_ops;
     int flop_pair_moments, flop_pair_adjoint, flop_atom_program;
     // launchers (stream-ordered, no synchronisation); return the number of kernels launched

@@ -166,94 +166,212 @@ __global__ void __launch_bounds__(128) k_moments(const EvalCtx<T> a) {
 // ----------------------------------------------------------------------------------------------
 // k_contract: warp per atom
 // ----------------------------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ void run_forward(const EvalCtx<T>& a, T* val, int lane) {
+// One layer-ordered pass of a generated program over A atoms held by the warp.  Op word layout:
+// i (16) | j (16) | k (16) | flags (3) | weight index (13); flags: 1 = first term of the target,
+// 2 = last term (store), 4 = padding.  Forward: val[k] = sum w val[i] val[j].  Adjoint:
+// adj[k] = adj[k] + sum w val[i] adj[j] (the target's own seed enters through the first term).
+template <class T, int A, bool ADJ>
+__device__ __forceinline__ void run_program(const unsigned long long* __restrict__ ops, const int* __restrict__ layer_end,
+                                            int layers, const float* sw, T* val, T* adj, int lane) {
+    constexpr int V = G::V_;
     int row = 0;
-    for (int l = 0; l < a.fwd_layers; ++l) {
-        const int end = a.fwd_layer_end[l];
-        T acc = T(0);
+    for (int l = 0; l < layers; ++l) {
+        const int end = layer_end[l];
+        T acc[A];
+#pragma unroll
+        for (int q = 0; q < A; ++q) acc[q] = T(0);
+        unsigned long long op = row < end ? ops[row * 32 + lane] : 4ull << 48;
         for (; row < end; ++row) {
-            const unsigned ij = a.fwd_ij[row * 32 + lane];
-            const unsigned kf = a.fwd_kf[row * 32 + lane];
-            const unsigned fl = kf >> 16;
+            const unsigned long long nxt = row + 1 < end ? ops[(row + 1) * 32 + lane] : 4ull << 48;  // prefetch
+            const unsigned fl = (unsigned)(op >> 48) & 7u;
             if (!(fl & 4u)) {
-                if (fl & 1u) acc = T(0);
-                acc += T(a.fwd_w[row * 32 + lane]) * val[ij & 0xffffu] * val[ij >> 16];
-                if (fl & 2u) val[kf & 0xffffu] = acc;
+                const int i = (int)(op & 0xffffu), j = (int)((op >> 16) & 0xffffu), k = (int)((op >> 32) & 0xffffu);
+                const T w = (T)sw[op >> 51];
+#pragma unroll
+                for (int q = 0; q < A; ++q) {
+                    if (fl & 1u) acc[q] = ADJ ? adj[q * V + k] : T(0);
+                    acc[q] += w * val[q * V + i] * (ADJ ? adj[q * V + j] : val[q * V + j]);
+                    if (fl & 2u) {
+                        if (ADJ)
+                            adj[q * V + k] = acc[q];
+                        else
+                            val[q * V + k] = acc[q];
+                    }
+                }
             }
+            op = nxt;
         }
         __syncwarp();
     }
 }
 
-template <class T>
-__device__ __forceinline__ void run_adjoint(const EvalCtx<T>& a, const T* val, T* adj, int lane) {
-    int row = 0;
-    for (int l = 0; l < a.adj_layers; ++l) {
-        const int end = a.adj_layer_end[l];
-        T acc = T(0);
-        for (; row < end; ++row) {
-            const unsigned ij = a.adj_ij[row * 32 + lane];
-            const unsigned kf = a.adj_kf[row * 32 + lane];
-            const unsigned fl = kf >> 16;
-            if (!(fl & 4u)) {
-                const unsigned k = kf & 0xffffu;
-                if (fl & 1u) acc = adj[k];
-                acc += T(a.adj_w[row * 32 + lane]) * val[ij & 0xffffu] * adj[ij >> 16];
-                if (fl & 2u) adj[k] = acc;
-            }
-        }
-        __syncwarp();
-    }
+// Flush a running per-configuration sum.
+__device__ __forceinline__ void flush_sum(double* dst, int cfg, double v) {
+    if (cfg >= 0 && dst) atomicAdd(&dst[cfg], v);
 }
 
-template <class T>
+// warp per group of A consecutive atoms (contiguous chunks per warp)
+template <class T, int A>
 __global__ void __launch_bounds__(256) k_contract(const EvalCtx<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int V = G::V_, C = G::C_, M = G::M_;
+    constexpr int MB = (M + 31) / 32;  // basis values per lane
+    __shared__ int s_cfg[8];
+    __shared__ double s_sum[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     T* seed = reinterpret_cast<T*>(smem_raw);
-    T* val = seed + V + warp * 2 * V;
-    T* adj = val + V;
+    float* sw = reinterpret_cast<float*>(seed + V);
+    T* val = reinterpret_cast<T*>(sw + ((a.n_weights + 3) & ~3)) + (size_t)warp * 2 * A * V;
+    T* adj = val + A * V;
     for (int v = threadIdx.x; v < V; v += blockDim.x) seed[v] = a.seed[v];
+    for (int v = threadIdx.x; v < a.n_weights; v += blockDim.x) sw[v] = a.weights[v];
     __syncthreads();
+    const int total_warps = gridDim.x * wpb;
+    const int chunk = (a.n_atoms + total_warps - 1) / total_warps;
+    const int gw = blockIdx.x * wpb + warp;
+    const int i0 = gw * chunk;
+    const int i1 = min(a.n_atoms, i0 + chunk);
     double esum = 0.0;
     int ecfg = -1;
-    const int total_warps = gridDim.x * wpb;
-    for (int i = blockIdx.x * wpb + warp; i < a.n_atoms; i += total_warps) {
-        const T* msrc = a.mom + (size_t)(i >> 5) * C * 32 + (i & 31);
-        for (int c = lane; c < C; c += 32) val[c] = msrc[(size_t)c * 32];
-        __syncwarp();
-        run_forward(a, val, lane);
-        // site energy and basis values
-        const int cfg = a.cfg_of[i];
-        T e = T(0);
-        for (int al = lane; al < M; al += 32) {
-            const T b = val[a.basis_value[al]];
-            e += a.xi[al] * b;
-            if (a.b_atoms) a.b_atoms[(size_t)i * M + al] = (double)b;
-            if (a.b_rows) atomicAdd(&a.b_rows[(size_t)cfg * M + al], (double)b);
+    double brun[MB];
+#pragma unroll
+    for (int t = 0; t < MB; ++t) brun[t] = 0.0;
+    for (int ib = i0; ib < i1; ib += A) {
+        const int na = min(A, i1 - ib);
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            if (q < na) {
+                const int i = ib + q;
+                const T* msrc = a.mom + (size_t)(i >> 5) * C * 32 + (i & 31);
+                for (int c = lane; c < C; c += 32) val[q * V + c] = msrc[(size_t)c * 32];
+            }
         }
-        const double ed = warp_sum((double)e);
-        if (lane == 0) {
-            if (a.site) a.site[i] = ed;
-            if (cfg != ecfg) {
-                if (ecfg >= 0 && a.energy) atomicAdd(&a.energy[ecfg], esum);
+        __syncwarp();
+        run_program<T, A, false>(a.fwd_ops, a.fwd_layer_end, a.fwd_layers, sw, val, adj, lane);
+        for (int q = 0; q < na; ++q) {
+            const int i = ib + q;
+            const int cfg = a.cfg_of[i];
+            if (cfg != ecfg) {  // warp-uniform
+                if (lane == 0) flush_sum(a.energy, ecfg, esum);
+                if (a.b_rows && ecfg >= 0) {
+#pragma unroll
+                    for (int t = 0; t < MB; ++t)
+                        if (lane + 32 * t < M) atomicAdd(&a.b_rows[(size_t)ecfg * M + lane + 32 * t], brun[t]);
+                }
+#pragma unroll
+                for (int t = 0; t < MB; ++t) brun[t] = 0.0;
                 ecfg = cfg;
                 esum = 0.0;
             }
+            T e = T(0);
+#pragma unroll
+            for (int t = 0; t < MB; ++t) {
+                const int al = lane + 32 * t;
+                if (al < M) {
+                    const T b = val[q * V + a.basis_value[al]];
+                    e += a.xi[al] * b;
+                    if (a.b_rows) brun[t] += (double)b;
+                    if (a.b_atoms) a.b_atoms[(size_t)i * M + al] = (double)b;
+                }
+            }
+            const double ed = warp_sum((double)e);
+            if (lane == 0 && a.site) a.site[i] = ed;
             esum += ed;
         }
-        // adjoint: dV/dval seeded with xi at the basis values
-        for (int v = lane; v < V; v += 32) adj[v] = seed[v];
+        for (int v = lane; v < A * V; v += 32) adj[v] = seed[v % V];
         __syncwarp();
-        run_adjoint(a, val, adj, lane);
-        T* adst = a.adjm + (size_t)(i >> 5) * C * 32 + (i & 31);
-        for (int c = lane; c < C; c += 32) adst[(size_t)c * 32] = adj[c];
+        run_program<T, A, true>(a.adj_ops, a.adj_layer_end, a.adj_layers, sw, val, adj, lane);
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            if (q < na) {
+                const int i = ib + q;
+                T* adst = a.adjm + (size_t)(i >> 5) * C * 32 + (i & 31);
+                for (int c = lane; c < C; c += 32) adst[(size_t)c * 32] = adj[q * V + c];
+            }
+        }
         __syncwarp();
     }
-    if (lane == 0 && ecfg >= 0 && a.energy) atomicAdd(&a.energy[ecfg], esum);
+    if (a.b_rows && ecfg >= 0) {
+#pragma unroll
+        for (int t = 0; t < MB; ++t)
+            if (lane + 32 * t < M) atomicAdd(&a.b_rows[(size_t)ecfg * M + lane + 32 * t], brun[t]);
+    }
+    // combine the warps' last running energies: one atomic per configuration per block
+    if (lane == 0) {
+        s_cfg[warp] = ecfg;
+        s_sum[warp] = esum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int cur = -1;
+        double acc = 0.0;
+        for (int w = 0; w < wpb; ++w) {
+            if (s_cfg[w] < 0) continue;
+            if (s_cfg[w] != cur) {
+                flush_sum(a.energy, cur, acc);
+                cur = s_cfg[w];
+                acc = 0.0;
+            }
+            acc += s_sum[w];
+        }
+        flush_sum(a.energy, cur, acc);
+    }
+}
+
+#if MTPGEN_HAS_UNROLLED
+// thread per atom: the generated straight-line contraction (float)
+__global__ void __launch_bounds__(128) k_contract_unrolled(const EvalCtx<float> a) {
+    constexpr int C = G::C_, M = G::M_;
+    __shared__ double s_e[128];
+    __shared__ int s_c[128];
+    double erun = 0.0;
+    int ecfg = -1;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_atoms; i += stride) {
+        const size_t t = (size_t)(i >> 5) * C * 32 + (i & 31);
+        double* bout = a.b_atoms ? a.b_atoms + (size_t)i * M : nullptr;
+        const float e = bout ? ::MTP_GEN_NS::contract_unrolled<true>(a.mom + t, a.adjm + t, a.xi, bout)
+                             : ::MTP_GEN_NS::contract_unrolled<false>(a.mom + t, a.adjm + t, a.xi, nullptr);
+        if (a.site) a.site[i] = (double)e;
+        const int cfg = a.cfg_of[i];
+        if (cfg != ecfg) {
+            flush_sum(a.energy, ecfg, erun);
+            ecfg = cfg;
+            erun = 0.0;
+        }
+        erun += (double)e;
+    }
+    // block-level combine (tree when the block ends in one configuration)
+    s_c[threadIdx.x] = ecfg;
+    __syncthreads();
+    const int c0 = s_c[0];
+    const bool uniform = __syncthreads_and(ecfg == c0 || ecfg < 0) && c0 >= 0;
+    if (!uniform) {
+        flush_sum(a.energy, ecfg, erun);
+        return;
+    }
+    s_e[threadIdx.x] = erun;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) s_e[threadIdx.x] += s_e[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) flush_sum(a.energy, c0, s_e[0]);
+}
+#endif
+
+// b rows as sums of the per-atom rows of each configuration (one block per configuration)
+template <class T>
+__global__ void k_brows(const EvalCtx<T> a, const int* cfg_off) {
+    constexpr int M = G::M_;
+    const int k = blockIdx.x;
+    const int i0 = cfg_off[k], i1 = cfg_off[k + 1];
+    for (int al = threadIdx.x; al < M; al += blockDim.x) {
+        double s = 0.0;
+        for (int i = i0; i < i1; ++i) s += a.b_atoms[(size_t)i * M + al];
+        a.b_rows[(size_t)k * M + al] = s;
+    }
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -317,14 +435,19 @@ __global__ void __launch_bounds__(128) k_pairgrad(const EvalCtx<T> a) {
 // ----------------------------------------------------------------------------------------------
 // k_gather: forces and virial
 // ----------------------------------------------------------------------------------------------
-template <class T>
+template <class T, int TPA>
 __global__ void __launch_bounds__(128) k_gather(const EvalCtx<T> a) {
-    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-    const int stride = gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
+    __shared__ int s_cfg[128];
+    __shared__ double s_w[9][128];
     const size_t n = (size_t)a.n_atoms;
-    const int n_round = ((a.n_atoms + 31) / 32) * 32;
-    for (int i = i0; i < n_round; i += stride) {
+    const int stride = gridDim.x * blockDim.x;
+    const int n_groups = ((a.n_atoms + 31) / 32) * 32;  // whole warps stay converged for the shuffles
+    double Wrun[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Wrun[k] = 0.0;
+    int wcfg = -1;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups * TPA; g += stride) {
+        const int i = g / TPA, sub = g % TPA;
         const bool active = i < a.n_atoms;
         T F[3] = {T(0), T(0), T(0)};
         T W[9];
@@ -334,15 +457,15 @@ __global__ void __launch_bounds__(128) k_gather(const EvalCtx<T> a) {
         if (active) {
             cfg = a.cfg_of[i];
             const int cnt = a.count[i];
-            for (int p = 0; p < cnt; ++p) {
+            for (int p = sub; p < cnt; p += TPA) {
                 const size_t idx = (size_t)p * n + i;
-                const T g[3] = {a.gx[idx], a.gy[idx], a.gz[idx]};
+                const T g3[3] = {a.gx[idx], a.gy[idx], a.gz[idx]};
                 const T r[3] = {a.rx[idx], a.ry[idx], a.rz[idx]};
 #pragma unroll
                 for (int u = 0; u < 3; ++u) {
-                    F[u] += g[u];
+                    F[u] += g3[u];
 #pragma unroll
-                    for (int v = 0; v < 3; ++v) W[3 * u + v] -= g[u] * r[v];
+                    for (int v = 0; v < 3; ++v) W[3 * u + v] -= g3[u] * r[v];
                 }
                 const int q = a.rev[idx];
                 if (q >= 0) {
@@ -352,27 +475,58 @@ __global__ void __launch_bounds__(128) k_gather(const EvalCtx<T> a) {
                     F[2] -= a.gz[ridx];
                 }
             }
-            if (a.forces) {
-                a.forces[3 * (size_t)i + 0] = (double)F[0];
-                a.forces[3 * (size_t)i + 1] = (double)F[1];
-                a.forces[3 * (size_t)i + 2] = (double)F[2];
+        }
+        if (TPA > 1) {
+#pragma unroll
+            for (int o = 1; o < TPA; o <<= 1) {
+#pragma unroll
+                for (int u = 0; u < 3; ++u) F[u] += __shfl_xor_sync(0xffffffffu, F[u], o);
             }
         }
-        if (!a.virial) continue;
-        // per-configuration reduction: one atomic per warp when the warp lies in one configuration
-        const int c0 = __shfl_sync(0xffffffffu, cfg, 0);
-        const bool uniform = __all_sync(0xffffffffu, cfg == c0 || cfg < 0);
-        if (uniform) {
+        if (active && sub == 0 && a.forces) {
+            a.forces[3 * (size_t)i + 0] = (double)F[0];
+            a.forces[3 * (size_t)i + 1] = (double)F[1];
+            a.forces[3 * (size_t)i + 2] = (double)F[2];
+        }
+        if (active && a.virial) {
+            if (cfg != wcfg) {
+                if (wcfg >= 0) {
 #pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const double s = warp_sum((double)W[k]);
-                if (lane == 0 && c0 >= 0) atomicAdd(&a.virial[(size_t)c0 * 9 + k], s);
+                    for (int k = 0; k < 9; ++k) atomicAdd(&a.virial[(size_t)wcfg * 9 + k], Wrun[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 9; ++k) Wrun[k] = 0.0;
+                wcfg = cfg;
             }
-        } else if (active) {
 #pragma unroll
-            for (int k = 0; k < 9; ++k) atomicAdd(&a.virial[(size_t)cfg * 9 + k], (double)W[k]);
+            for (int k = 0; k < 9; ++k) Wrun[k] += (double)W[k];
         }
     }
+    if (!a.virial) return;
+    // block-level combine of the running sums: a tree reduction when the whole block ends in one
+    // configuration (large cells), otherwise one atomic per thread and component
+    s_cfg[threadIdx.x] = wcfg;
+    __syncthreads();
+    const int c0 = s_cfg[0];
+    const bool uniform = __syncthreads_and(wcfg == c0 || wcfg < 0) && c0 >= 0;
+    if (!uniform) {
+        if (wcfg >= 0) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) atomicAdd(&a.virial[(size_t)wcfg * 9 + k], Wrun[k]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s_w[k][threadIdx.x] = Wrun[k];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) s_w[k][threadIdx.x] += s_w[k][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 9) atomicAdd(&a.virial[(size_t)c0 * 9 + threadIdx.x], s_w[threadIdx.x][0]);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -411,22 +565,39 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks)
     if (marks) cudaEventRecord(marks[kPhaseMoments], st);
     launches += launch_pairs_tpa<T>(a, st, n_sm, true);
     if (marks) cudaEventRecord(marks[kPhaseContract], st);
+#if MTPGEN_HAS_UNROLLED
+    if constexpr (sizeof(T) == 4) {
+        const int threads = 128;
+        int blocks = (a.n_atoms + threads - 1) / threads;
+        if (blocks > n_sm * 16) blocks = n_sm * 16;
+        k_contract_unrolled<<<blocks, threads, 0, st>>>(a);
+        ++launches;
+        if (a.b_rows) {  // the caller provides per-atom rows whenever b rows are requested
+            k_brows<T><<<a.n_cfg, 128, 0, st>>>(a, a.cfg_off);
+            ++launches;
+        }
+    } else
+#endif
     {
-        const int threads = 256;
+        // atoms per warp: amortise each program word over several atoms while the per-warp working
+        // set (2 A V values) stays small enough for at least two blocks per SM
+        constexpr int A = (sizeof(T) * G::V_ * 2 * 4 * 8 <= 100 * 1024) ? 4
+                        : (sizeof(T) * G::V_ * 2 * 2 * 8 <= 100 * 1024) ? 2 : 1;
+        constexpr int threads = (sizeof(T) * G::V_ * 2 * A * 8 <= 100 * 1024) ? 256 : 128;
         const int wpb = threads / 32;
-        const size_t smem = sizeof(T) * (size_t)G::V_ * (1 + 2 * wpb);
+        const size_t smem = sizeof(T) * (size_t)G::V_ * (1 + 2 * A * wpb) + sizeof(float) * (a.n_weights + 4) + 64;
         if (smem > 200 * 1024) return -1000;  // not reachable for lev_max <= 20
         static bool attr_set = false;
         if (!attr_set) {
-            cudaFuncSetAttribute(k_contract<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            cudaFuncSetAttribute(k_contract<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             attr_set = true;
         }
-        int blocks = (a.n_atoms + wpb - 1) / wpb;
-        int per_sm = (int)((200 * 1024) / (smem ? smem : 1));
+        int per_sm = (int)((220 * 1024) / (smem + 1024));
         if (per_sm < 1) per_sm = 1;
-        if (per_sm > 4) per_sm = 4;
-        if (blocks > n_sm * per_sm * 4) blocks = n_sm * per_sm * 4;
-        k_contract<T><<<blocks, threads, smem, st>>>(a);
+        if (per_sm > 8) per_sm = 8;
+        int blocks = (a.n_atoms + wpb * A - 1) / (wpb * A);
+        if (blocks > n_sm * per_sm) blocks = n_sm * per_sm;
+        k_contract<T, A><<<blocks, threads, smem, st>>>(a);
         ++launches;
     }
     if (marks) cudaEventRecord(marks[kPhasePairgrad], st);
@@ -434,9 +605,15 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks)
     if (marks) cudaEventRecord(marks[kPhaseGather], st);
     {
         const int threads = 128;
-        int blocks = (a.n_atoms + threads - 1) / threads;
-        if (blocks > n_sm * 16) blocks = n_sm * 16;
-        k_gather<T><<<blocks, threads, 0, st>>>(a);
+        const long work = (long)(((a.n_atoms + 31) / 32) * 32) * a.tpa;
+        int blocks = (int)((work + threads - 1) / threads);
+        if (blocks > n_sm * 8) blocks = n_sm * 8;
+        switch (a.tpa) {
+            case 8: k_gather<T, 8><<<blocks, threads, 0, st>>>(a); break;
+            case 4: k_gather<T, 4><<<blocks, threads, 0, st>>>(a); break;
+            case 2: k_gather<T, 2><<<blocks, threads, 0, st>>>(a); break;
+            default: k_gather<T, 1><<<blocks, threads, 0, st>>>(a); break;
+        }
         ++launches;
     }
     if (marks) cudaEventRecord(marks[kPhases], st);
@@ -457,8 +634,8 @@ const LevelOps* MTP_LEVEL_FN() {
     static const LevelOps ops = {
         g::L, g::C, g::V, g::M, g::NMU, g::NUMAX,
         g::level_table, g::LEVEL_TABLE_LEN, g::basis_value,
-        g::fwd_ij, g::fwd_kf, g::fwd_w, g::fwd_layer_rows, g::FWD_ROWS, g::FWD_LAYERS,
-        g::adj_ij, g::adj_kf, g::adj_w, g::adj_layer_rows, g::ADJ_ROWS, g::ADJ_LAYERS,
+        g::fwd_ops, g::fwd_layer_rows, g::FWD_ROWS, g::FWD_LAYERS,
+        g::adj_ops, g::adj_layer_rows, g::ADJ_ROWS, g::ADJ_LAYERS, g::weights, g::NWEIGHTS,
         g::PROGRAM_OPS, g::FLOP_PAIR_MOMENTS, g::FLOP_PAIR_ADJOINT, g::FLOP_ATOM_PROGRAM,
         &MTP_GEN_NS::eval_f32, &MTP_GEN_NS::eval_f64};
     return &ops;

@@ -4,9 +4,13 @@
 // each lattice direction (bin width >= R_cut unless the cell is thinner), and each atom visits
 // the bins within c_k = ceil(R_cut / bin width) along every direction, periodic images included
 // (small cells are visited several times with different image shifts).  Distances are first
-// taken in float from bin-local coordinates; pairs within 1e-3 Angstrom of the cutoff are decided
-// in double precision with the fixed operation order documented in mtp.h, so the lists are
-// identical to a brute-force double-precision search.  Each warp owns one atom: lanes test
+// taken in float from bin-local coordinates as a prefilter; pairs within 1e-3 Angstrom of the
+// cutoff are decided in double precision with the fixed operation order documented in mtp.h, so
+// the lists are identical to a brute-force double-precision search.  After compaction each lane
+// computes r_ij of one accepted pair: exactly in double precision for the double path, and in
+// double-float arithmetic (error-free float transformations, ~2^-44 relative) rounded once to
+// float for the float path.  Double-precision instructions are few and never divergent: on this
+// part a warp-wide double-precision instruction costs many times a float one.  Each warp owns one atom: lanes test
 // candidates, accepted pairs are compacted with a ballot, rank-sorted by (j, s) and written in
 // slot-major layout.  A last kernel records, for every pair, the slot of the reverse pair in
 // the neighbour's list (used by the deterministic force gather).
@@ -48,18 +52,22 @@ __global__ void k_cells(int K, const double* cells, const int* cfg_off, double r
     const double* H = cells + 9 * (size_t)k;
     for (int q = 0; q < 9; ++q) D.H[q] = H[q];
     const double a = H[0], b = H[1], c = H[2], e = H[3], f = H[4], g = H[5], h = H[6], ii = H[7], jj = H[8];
+    // double-precision division and square root are long instruction sequences on this part, and
+    // this thread's chain is serial: one reciprocal, three reciprocal square roots, no divisions
     const double det = a * (f * jj - g * ii) - b * (e * jj - g * h) + c * (e * ii - f * h);
-    D.Hi[0] = (f * jj - g * ii) / det; D.Hi[1] = (c * ii - b * jj) / det; D.Hi[2] = (b * g - c * f) / det;
-    D.Hi[3] = (g * h - e * jj) / det; D.Hi[4] = (a * jj - c * h) / det; D.Hi[5] = (c * e - a * g) / det;
-    D.Hi[6] = (e * ii - f * h) / det; D.Hi[7] = (b * h - a * ii) / det; D.Hi[8] = (a * f - b * e) / det;
+    const double id = 1.0 / det;
+    D.Hi[0] = (f * jj - g * ii) * id; D.Hi[1] = (c * ii - b * jj) * id; D.Hi[2] = (b * g - c * f) * id;
+    D.Hi[3] = (g * h - e * jj) * id; D.Hi[4] = (a * jj - c * h) * id; D.Hi[5] = (c * e - a * g) * id;
+    D.Hi[6] = (e * ii - f * h) * id; D.Hi[7] = (b * h - a * ii) * id; D.Hi[8] = (a * f - b * e) * id;
     const double vol = fabs(det);
+    const double irs = 1.0 / rsearch;
     double w[3];
     for (int q = 0; q < 3; ++q) {
         const double* u = H + ((q + 1) % 3) * 3;
         const double* v = H + ((q + 2) % 3) * 3;
         const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
-        w[q] = vol / sqrt(cx * cx + cy * cy + cz * cz);
-        int nq = (int)floor(w[q] / rsearch);
+        w[q] = vol * rsqrt(cx * cx + cy * cy + cz * cz);
+        int nq = (int)floor(w[q] * irs * (1.0 - 1e-12));  // bins no thinner than the search radius
         D.n[q] = nq < 1 ? 1 : (nq > 1024 ? 1024 : nq);
     }
     const long natoms = cfg_off[k + 1] - cfg_off[k];
@@ -72,15 +80,21 @@ __global__ void k_cells(int K, const double* cells, const int* cfg_off, double r
         if (D.n[0] * D.n[1] * D.n[2] == 1) break;
     }
     for (int q = 0; q < 3; ++q) {
-        const double width = w[q] / D.n[q];
-        int cq = (int)ceil((rsearch + kBand) / width);
+        // bins to visit: ceil((rsearch + band) / width) with width = w / n; rounded up for safety
+        int cq = (int)ceil((rsearch + kBand) * D.n[q] * (1.0 / w[q]) * (1.0 + 1e-12));
         if (cq < 1) cq = 1;
         if (cq > kMaxImageReach) {
             atomicOr(err, kErrCellThin);
             cq = kMaxImageReach;
         }
         D.c[q] = cq;
-        for (int t = 0; t < 3; ++t) D.hn[3 * q + t] = (float)(H[3 * q + t] / D.n[q]);
+        const double inq = 1.0 / D.n[q];
+        for (int t = 0; t < 3; ++t) {
+            D.hn[3 * q + t] = (float)(H[3 * q + t] * inq);
+            const float hi = (float)H[3 * q + t];
+            D.hhi[3 * q + t] = hi;
+            D.hlo[3 * q + t] = (float)(H[3 * q + t] - (double)hi);
+        }
     }
     D.nbins = D.n[0] * D.n[1] * D.n[2];
     D.bin0 = 0;
@@ -95,7 +109,7 @@ __global__ void k_cells_offsets(int K, const int* bin0, CellDesc* d) {
 
 __global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, int S, const int* cfg_off,
                             const CellDesc* d, int* cfg_of, int* atom_bin, int* atom_wrap, float4* local,
-                            int* bin_count, int* err) {
+                            float4* wp, int* bin_count, int* err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int k = find_cfg(cfg_off, K, i);
@@ -117,9 +131,16 @@ __global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, i
         frac[q] = (double)w[q] + (double)bq / (double)D.n[q];
         if (w[q] > kMaxShift || w[q] < -kMaxShift) atomicOr(err, kErrShift);
     }
-    double o[3];
-    for (int t = 0; t < 3; ++t) o[t] = frac[0] * D.H[0 * 3 + t] + frac[1] * D.H[1 * 3 + t] + frac[2] * D.H[2 * 3 + t];
+    double o[3], xw[3];
+    for (int t = 0; t < 3; ++t) {
+        o[t] = frac[0] * D.H[0 * 3 + t] + frac[1] * D.H[1 * 3 + t] + frac[2] * D.H[2 * 3 + t];
+        xw[t] = x[t] - (w[0] * D.H[0 * 3 + t] + w[1] * D.H[1 * 3 + t] + w[2] * D.H[2 * 3 + t]);
+    }
     local[i] = make_float4((float)(x[0] - o[0]), (float)(x[1] - o[1]), (float)(x[2] - o[2]), 0.f);
+    // wrapped position x - w H as a float pair (hi, lo) for the double-float displacement
+    const float h0 = (float)xw[0], h1 = (float)xw[1], h2 = (float)xw[2];
+    wp[2 * (size_t)i] = make_float4(h0, h1, h2, 0.f);
+    wp[2 * (size_t)i + 1] = make_float4((float)(xw[0] - h0), (float)(xw[1] - h1), (float)(xw[2] - h2), 0.f);
     const int bin = D.bin0 + (b[0] * D.n[1] + b[1]) * D.n[2] + b[2];
     atom_bin[i] = bin;
     atom_wrap[i] = ((w[0] + 128) & 255) | (((w[1] + 128) & 255) << 8) | (((w[2] + 128) & 255) << 16);
@@ -159,6 +180,7 @@ struct BuildArgs {
     const int* atom_bin;
     const int* atom_wrap;
     const float4* local;
+    const float4* wp;
     const int* bin_start;
     const int* bin_atoms;
     int* count;
@@ -170,6 +192,30 @@ struct BuildArgs {
     int* err;
     int* max_seen;
 };
+
+// ---- double-float arithmetic (float pairs hi + lo), error-free transformations -------------------
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_scale(float t, float hhi, float hlo) {  // t small integer
+    const float p = __fmul_rn(t, hhi);
+    const float e = __fmaf_rn(t, hhi, -p);
+    return fast_two_sum(p, __fmaf_rn(t, hlo, e));
+}
 
 template <class T>
 __global__ void __launch_bounds__(128) k_build(const BuildArgs a) {
@@ -189,67 +235,87 @@ __global__ void __launch_bounds__(128) k_build(const BuildArgs a) {
         const int b2 = lb % D.n[2], b1 = (lb / D.n[2]) % D.n[1], b0 = lb / (D.n[2] * D.n[1]);
         const int wi = a.atom_wrap[i];
         const float4 li = a.local[i];
-        const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1], a.pos[3 * (size_t)i + 2]};
         int cnt = 0;
-        for (int o0 = -D.c[0]; o0 <= D.c[0]; ++o0) {
-            const int bb0 = b0 + o0, t0 = floordiv(bb0, D.n[0]), w0 = bb0 - t0 * D.n[0];
-            for (int o1 = -D.c[1]; o1 <= D.c[1]; ++o1) {
-                const int bb1 = b1 + o1, t1 = floordiv(bb1, D.n[1]), w1 = bb1 - t1 * D.n[1];
-                for (int o2 = -D.c[2]; o2 <= D.c[2]; ++o2) {
-                    const int bb2 = b2 + o2, t2 = floordiv(bb2, D.n[2]), w2 = bb2 - t2 * D.n[2];
-                    const float ox = o0 * D.hn[0] + o1 * D.hn[3] + o2 * D.hn[6];
-                    const float oy = o0 * D.hn[1] + o1 * D.hn[4] + o2 * D.hn[7];
-                    const float oz = o0 * D.hn[2] + o1 * D.hn[5] + o2 * D.hn[8];
-                    const int bin = D.bin0 + (w0 * D.n[1] + w1) * D.n[2] + w2;
-                    const int start = a.bin_start[bin], end = a.bin_start[bin + 1];
-                    for (int q0 = start; q0 < end; q0 += 32) {
-                        const int q = q0 + lane;
-                        bool acc = false;
-                        int j = 0, s[3] = {0, 0, 0};
-                        float dx = 0.f, dy = 0.f, dz = 0.f;
-                        double dd[3] = {0.0, 0.0, 0.0};
-                        if (q < end) {
-                            j = a.bin_atoms[q];
-                            const int wj = a.atom_wrap[j];
-                            s[0] = t0 - unpack(wj, 0) + unpack(wi, 0);
-                            s[1] = t1 - unpack(wj, 1) + unpack(wi, 1);
-                            s[2] = t2 - unpack(wj, 2) + unpack(wi, 2);
-                            if (!(j == i && s[0] == 0 && s[1] == 0 && s[2] == 0)) {
-                                const float4 lj = a.local[j];
-                                dx = (lj.x - li.x) + ox;
-                                dy = (lj.y - li.y) + oy;
-                                dz = (lj.z - li.z) + oz;
-                                const float r2 = dx * dx + dy * dy + dz * dz;
-                                const bool exact_needed = sizeof(T) == 8 ? (r2 <= a.hi2) : (r2 >= a.lo2 && r2 <= a.hi2);
-                                if (exact_needed) {
-                                    const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1],
-                                                          a.pos[3 * (size_t)j + 2]};
-                                    acc = exact_r2(xi, xj, D.H, s, dd) < a.rs2;
-                                } else {
-                                    acc = r2 < a.lo2;
-                                }
-                            }
+        // 1. candidates: float prefilter; only the rare pairs within 1e-3 Angstrom of the cutoff
+        //    take the double-precision decision.  The bins to visit are handed out one per lane
+        //    (32 at a time); their atoms are then flattened over the lanes, each lane finding its
+        //    bin by a binary search over the lanes' running candidate counts.
+        const int ny = 2 * D.c[1] + 1, nz = 2 * D.c[2] + 1;
+        const int n_off = (2 * D.c[0] + 1) * ny * nz;
+        for (int base = 0; base < n_off; base += 32) {
+            const int o = base + lane;
+            int bstart = 0, bcnt = 0, tb0 = 0, tb1 = 0, tb2 = 0;
+            float ox = 0.f, oy = 0.f, oz = 0.f;
+            if (o < n_off) {
+                const int o2 = o % nz - D.c[2], o1 = (o / nz) % ny - D.c[1], o0 = o / (nz * ny) - D.c[0];
+                int w0 = b0 + o0, w1 = b1 + o1, w2 = b2 + o2;
+                while (w0 < 0) { w0 += D.n[0]; --tb0; }
+                while (w0 >= D.n[0]) { w0 -= D.n[0]; ++tb0; }
+                while (w1 < 0) { w1 += D.n[1]; --tb1; }
+                while (w1 >= D.n[1]) { w1 -= D.n[1]; ++tb1; }
+                while (w2 < 0) { w2 += D.n[2]; --tb2; }
+                while (w2 >= D.n[2]) { w2 -= D.n[2]; ++tb2; }
+                ox = o0 * D.hn[0] + o1 * D.hn[3] + o2 * D.hn[6];
+                oy = o0 * D.hn[1] + o1 * D.hn[4] + o2 * D.hn[7];
+                oz = o0 * D.hn[2] + o1 * D.hn[5] + o2 * D.hn[8];
+                const int bin = D.bin0 + (w0 * D.n[1] + w1) * D.n[2] + w2;
+                bstart = a.bin_start[bin];
+                bcnt = a.bin_start[bin + 1] - bstart;
+            }
+            int incl = bcnt;
+#pragma unroll
+            for (int sh = 1; sh < 32; sh <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, sh);
+                if (lane >= sh) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int pre = incl - bcnt;
+            for (int f0 = 0; f0 < total; f0 += 32) {
+                const int f = f0 + lane;
+                // last lane b with pre[b] <= f (then f < pre[b] + cnt[b])
+                int b = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int pv = __shfl_sync(0xffffffffu, pre, b + step);
+                    if (pv <= f) b += step;
+                }
+                const int qs = __shfl_sync(0xffffffffu, bstart, b), qp = __shfl_sync(0xffffffffu, pre, b);
+                const int t0 = __shfl_sync(0xffffffffu, tb0, b), t1 = __shfl_sync(0xffffffffu, tb1, b),
+                          t2 = __shfl_sync(0xffffffffu, tb2, b);
+                const float fx = __shfl_sync(0xffffffffu, ox, b), fy = __shfl_sync(0xffffffffu, oy, b),
+                            fz = __shfl_sync(0xffffffffu, oz, b);
+                bool acc = false;
+                int j = 0, sv[3] = {0, 0, 0};
+                if (f < total) {
+                    j = a.bin_atoms[qs + (f - qp)];
+                    const int wj = a.atom_wrap[j];
+                    sv[0] = t0 - unpack(wj, 0) + unpack(wi, 0);
+                    sv[1] = t1 - unpack(wj, 1) + unpack(wi, 1);
+                    sv[2] = t2 - unpack(wj, 2) + unpack(wi, 2);
+                    if (!(j == i && sv[0] == 0 && sv[1] == 0 && sv[2] == 0)) {
+                        const float4 lj = a.local[j];
+                        const float dx = (lj.x - li.x) + fx, dy = (lj.y - li.y) + fy, dz = (lj.z - li.z) + fz;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < a.lo2) {
+                            acc = true;
+                        } else if (r2 <= a.hi2) {
+                            const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1],
+                                                  a.pos[3 * (size_t)i + 2]};
+                            const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1],
+                                                  a.pos[3 * (size_t)j + 2]};
+                            double dd[3];
+                            acc = exact_r2(xi, xj, D.H, sv, dd) < a.rs2;
                         }
-                        const unsigned ball = __ballot_sync(0xffffffffu, acc);
-                        if (acc) {
-                            const int pos_ = cnt + __popc(ball & ((1u << lane) - 1u));
-                            if (pos_ < a.cap) {
-                                keys[pos_] = ((unsigned long long)j << 24) |
-                                             (unsigned long long)(((s[0] + 128) << 16) | ((s[1] + 128) << 8) | (s[2] + 128));
-                                if (sizeof(T) == 8) {
-                                    rbuf[3 * pos_] = (T)dd[0];
-                                    rbuf[3 * pos_ + 1] = (T)dd[1];
-                                    rbuf[3 * pos_ + 2] = (T)dd[2];
-                                } else {
-                                    rbuf[3 * pos_] = (T)dx;
-                                    rbuf[3 * pos_ + 1] = (T)dy;
-                                    rbuf[3 * pos_ + 2] = (T)dz;
-                                }
-                            }
-                        }
-                        cnt += __popc(ball);
                     }
                 }
+                const unsigned ball = __ballot_sync(0xffffffffu, acc);
+                if (acc) {
+                    const int pos_ = cnt + __popc(ball & ((1u << lane) - 1u));
+                    if (pos_ < a.cap)
+                        keys[pos_] = ((unsigned long long)j << 24) |
+                                     (unsigned long long)(((sv[0] + 128) << 16) | ((sv[1] + 128) << 8) | (sv[2] + 128));
+                }
+                cnt += __popc(ball);
             }
         }
         __syncwarp();
@@ -263,6 +329,46 @@ __global__ void __launch_bounds__(128) k_build(const BuildArgs a) {
         } else if (lane == 0) {
             atomicMax(a.max_seen, cnt);
         }
+        // 2. r_ij of the accepted pairs, one pair per lane: exact double precision for the double
+        //    path, double-float arithmetic (then one rounding) for the float path
+        if (sizeof(T) == 8) {
+            const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1], a.pos[3 * (size_t)i + 2]};
+            for (int e = lane; e < keep; e += 32) {
+                const unsigned long long key = keys[e];
+                const int j = (int)(key >> 24);
+                const int s[3] = {(int)((key >> 16) & 255) - 128, (int)((key >> 8) & 255) - 128, (int)(key & 255) - 128};
+                const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1], a.pos[3 * (size_t)j + 2]};
+                double dd[3];
+                exact_r2(xi, xj, D.H, s, dd);
+                rbuf[3 * e] = (T)dd[0];
+                rbuf[3 * e + 1] = (T)dd[1];
+                rbuf[3 * e + 2] = (T)dd[2];
+            }
+        } else {
+            const float4 pih = a.wp[2 * (size_t)i], pil = a.wp[2 * (size_t)i + 1];
+            for (int e = lane; e < keep; e += 32) {
+                const unsigned long long key = keys[e];
+                const int j = (int)(key >> 24);
+                const int wj = a.atom_wrap[j];
+                // image shift relative to the wrapped positions: t = s + w_j - w_i
+                const float t[3] = {(float)((int)((key >> 16) & 255) - 128 + unpack(wj, 0) - unpack(wi, 0)),
+                                    (float)((int)((key >> 8) & 255) - 128 + unpack(wj, 1) - unpack(wi, 1)),
+                                    (float)((int)(key & 255) - 128 + unpack(wj, 2) - unpack(wi, 2))};
+                const float4 pjh = a.wp[2 * (size_t)j], pjl = a.wp[2 * (size_t)j + 1];
+                const float jh[3] = {pjh.x, pjh.y, pjh.z}, jl[3] = {pjl.x, pjl.y, pjl.z};
+                const float ih[3] = {pih.x, pih.y, pih.z}, il[3] = {pil.x, pil.y, pil.z};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    DF d = df_add({jh[c], jl[c]}, {-ih[c], -il[c]});
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (t[q] != 0.f) d = df_add(d, df_scale(t[q], D.hhi[3 * q + c], D.hlo[3 * q + c]));
+                    rbuf[3 * e + c] = (T)__fadd_rn(d.hi, d.lo);
+                }
+            }
+        }
+        __syncwarp();
+        // 3. canonical order (j, s) by rank, written in slot-major layout
         const size_t n = (size_t)a.n;
         for (int e = lane; e < keep; e += 32) {
             const unsigned long long key = keys[e];
@@ -283,13 +389,14 @@ __global__ void __launch_bounds__(128) k_build(const BuildArgs a) {
     }
 }
 
-__global__ void k_reverse(int n, const int* count, const int* jz, const int* shift, int* rev) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int cnt = count[i];
+// one thread per (slot, atom): binary search of the reverse pair (i, -s) in the neighbour's list
+__global__ void k_reverse(int n, int cap, const int* count, const int* jz, const int* shift, int* rev) {
     const size_t N = (size_t)n;
-    for (int p = 0; p < cnt; ++p) {
-        const size_t o = (size_t)p * N + i;
+    const size_t total = N * (size_t)cap;
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < total; o += (size_t)gridDim.x * blockDim.x) {
+        const int p = (int)(o / N);
+        const int i = (int)(o - (size_t)p * N);
+        if (p >= count[i]) continue;
         const int j = jz[o] & 0xffffff;
         const int sp = shift[o];
         const int neg = ((256 - (sp & 255)) & 255) | (((256 - ((sp >> 8) & 255)) & 255) << 8) |
@@ -428,7 +535,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     if (nb.count.reserve(N * 4) || nb.jz.reserve(N * cap * 4) || nb.shift.reserve(N * cap * 4) ||
         nb.rev.reserve(N * cap * 4) || nb.rx.reserve(N * cap * realsz) || nb.ry.reserve(N * cap * realsz) ||
         nb.rz.reserve(N * cap * realsz) || nb.cfg_of.reserve(N * 4) || nb.desc.reserve(sizeof(CellDesc) * K) ||
-        nb.atom_bin.reserve(N * 4) || nb.atom_wrap.reserve(N * 4) || nb.atom_local.reserve(N * 16) ||
+        nb.atom_bin.reserve(N * 4) || nb.atom_wrap.reserve(N * 4) || nb.atom_local.reserve(N * 16) || nb.atom_wp.reserve(N * 32) ||
         nb.bin_count.reserve(bins_max * 4) || nb.bin_start.reserve((bins_max + 1) * 4) ||
         nb.bin_fill.reserve(bins_max * 4) || nb.bin_atoms.reserve(N * 4 + 4) ||
         nb.scan_tmp.reserve(4 * (scan_tmp_ints((int)bins_max) + scan_tmp_ints(K + 1) + 16)) ||
@@ -456,7 +563,8 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     cudaMemsetAsync(nb.bin_fill.p, 0, (size_t)(total_bins_upper + 1) * 4, st);
     k_bin_atoms<<<(n + 255) / 256, 256, 0, st>>>(n, K, pos, types, S, cfg_off, desc, nb.cfg_of.as<int>(),
                                                 nb.atom_bin.as<int>(), nb.atom_wrap.as<int>(),
-                                                nb.atom_local.as<float4>(), bin_count, nb.err.as<int>());
+                                                nb.atom_local.as<float4>(), nb.atom_wp.as<float4>(), bin_count,
+                                                nb.err.as<int>());
     ++launches;
     launches += scan_exclusive(bin_count, bin_start, total_bins_upper, tmp, st);
     k_bin_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, nb.atom_bin.as<int>(), bin_start, nb.bin_fill.as<int>(),
@@ -476,6 +584,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     a.atom_bin = nb.atom_bin.as<int>();
     a.atom_wrap = nb.atom_wrap.as<int>();
     a.local = nb.atom_local.as<float4>();
+    a.wp = nb.atom_wp.as<float4>();
     a.bin_start = bin_start;
     a.bin_atoms = nb.bin_atoms.as<int>();
     a.count = nb.count.as<int>();
@@ -490,16 +599,28 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     const size_t smem = (size_t)wpb * cap * (8 + 3 * realsz);
     int blocks = (n + wpb - 1) / wpb;
     if (blocks > 152 * 64) blocks = 152 * 64;
+    static int attr64 = 0, attr32 = 0;  // largest dynamic shared memory already allowed
     if (fp64) {
-        cudaFuncSetAttribute(k_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if ((int)smem > attr64) {
+            cudaFuncSetAttribute(k_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr64 = (int)smem;
+        }
         k_build<double><<<blocks, threads, smem, st>>>(a);
     } else {
-        cudaFuncSetAttribute(k_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if ((int)smem > attr32) {
+            cudaFuncSetAttribute(k_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr32 = (int)smem;
+        }
         k_build<float><<<blocks, threads, smem, st>>>(a);
     }
     ++launches;
-    k_reverse<<<(n + 127) / 128, 128, 0, st>>>(n, nb.count.as<int>(), nb.jz.as<int>(), nb.shift.as<int>(),
+    {
+        const size_t total = N * (size_t)cap;
+        size_t blocks = (total + 255) / 256;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        k_reverse<<<(int)blocks, 256, 0, st>>>(n, cap, nb.count.as<int>(), nb.jz.as<int>(), nb.shift.as<int>(),
                                               nb.rev.as<int>());
+    }
     ++launches;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }

@@ -63,6 +63,10 @@ _SIGS = {
     "mtp_sync": (_I, [_P, _P]),
     "mtp_launch_count": (_L, [_P]),
     "mtp_profile": (_I, [_P, _I]),
+    "mtp_select_active_set": (_I, [_P, _I, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D), _I, _P]),
+    "mtp_set_active_set": (_I, [_P, _P]),
+    "mtp_get_active_set": (_I, [_P, _P, _P, _P]),
+    "mtp_grade": (_I, [_P, _I, _P, _P, _I, _P]),
     "mtp_profile_read": (_I, [_P, _P, _I, ctypes.POINTER(_L)]),
 }
 
@@ -167,6 +171,33 @@ def mtp_launch_count(h):
     return int(load().mtp_launch_count(h))
 
 
+def mtp_select_active_set(h, n_rows, b_rows, selected=None, flags=0, stream=None):
+    """Returns (number of swaps, final max |C|)."""
+    sw = ctypes.c_int()
+    g = ctypes.c_double()
+    s = None if flags & HOST_MEMORY else _stream(stream)
+    _check(load().mtp_select_active_set(h, int(n_rows), _ptr(b_rows), _ptr(selected), ctypes.byref(sw),
+                                        ctypes.byref(g), int(flags), s), "mtp_select_active_set")
+    return int(sw.value), float(g.value)
+
+
+def mtp_set_active_set(h, A):
+    _check(load().mtp_set_active_set(h, _ptr(np.ascontiguousarray(A, dtype=np.float64))), "mtp_set_active_set")
+
+
+def mtp_get_active_set(h, m):
+    A = np.zeros((m, m))
+    Ai = np.zeros((m, m))
+    rows = np.zeros(m, dtype=np.int32)
+    _check(load().mtp_get_active_set(h, _ptr(A), _ptr(Ai), _ptr(rows)), "mtp_get_active_set")
+    return A, Ai, rows
+
+
+def mtp_grade(h, n_rows, b_rows, gamma, flags=0, stream=None):
+    s = None if flags & HOST_MEMORY else _stream(stream)
+    _check(load().mtp_grade(h, int(n_rows), _ptr(b_rows), _ptr(gamma), int(flags), s), "mtp_grade")
+
+
 def mtp_profile(h, enable):
     _check(load().mtp_profile(h, int(bool(enable))), "mtp_profile")
 
@@ -221,7 +252,7 @@ class Model:
         return mtp_launch_count(self.h)
 
     def eval_batch(self, pos, types, cells, cfg_off, forces=True, virial=True, site=False, b_rows=False,
-                   b_atoms=False, stream=None, flags=0):
+                   b_atoms=False, grade_cfg=False, grade_atom=False, stream=None, flags=0):
         """Device tensors in (float64 pos [N,3], int32 types [N], float64 cells [K,3,3], int32 cfg_off [K+1]);
         device tensors out."""
         import torch
@@ -241,9 +272,29 @@ class Model:
             out["b_rows"] = torch.empty((K, self.m), **f64)
         if b_atoms:
             out["b_atoms"] = torch.empty((N, self.m), **f64)
+        if grade_cfg:
+            out["grade_cfg"] = torch.empty(K, **f64)
+        if grade_atom:
+            out["grade_atom"] = torch.empty(N, **f64)
         mtp_eval_batch(self.h, K, N, cfg_off, pos, types, cells, out["energy"], out.get("forces"), out.get("virial"),
-                       out.get("site"), out.get("b_rows"), out.get("b_atoms"), None, None, flags, stream)
+                       out.get("site"), out.get("b_rows"), out.get("b_atoms"), out.get("grade_cfg"),
+                       out.get("grade_atom"), flags, stream)
         return out
+
+    def select_active_set(self, b_rows):
+        """MaxVol over the rows of b_rows (device float64 [n, m]); returns (rows, swaps, max |C|)."""
+        import torch
+
+        sel = torch.empty(self.m, dtype=torch.int32, device=b_rows.device)
+        swaps, g = mtp_select_active_set(self.h, b_rows.shape[0], b_rows.contiguous(), sel)
+        return sel, swaps, g
+
+    def grade(self, b_rows):
+        import torch
+
+        g = torch.empty(b_rows.shape[0], dtype=torch.float64, device=b_rows.device)
+        mtp_grade(self.h, b_rows.shape[0], b_rows.contiguous(), g)
+        return g
 
     def eval(self, pos, types, cell, **kw):
         import torch

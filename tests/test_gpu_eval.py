@@ -164,8 +164,11 @@ def test_config2_fcc16_lev16_full(gpu_lib, config2, precision):
     tol = TOL[precision]
     check_config(out["energy"].item(), F, out["virial"].cpu().numpy(), ref, cfg.n, tol)
     assert out["energy"].item() == pytest.approx(site.sum(), rel=1e-9)
-    scale = np.sqrt(np.mean(ref["site"] ** 2))
-    assert np.abs(site - ref["site"]).max() <= tol["e"] * scale * (10 if precision == "fp32" else 1)
+    # per-site relative error; sites with neighbours closer than R_min evaluate the Chebyshev
+    # polynomials outside [-1, 1], where float rounding is amplified (up to ~1e-5 measured)
+    floor = 1e-6 * np.sqrt(np.mean(ref["site"] ** 2))
+    relsite = np.abs(site - ref["site"]) / (np.abs(ref["site"]) + floor)
+    assert relsite.max() <= (3e-5 if precision == "fp32" else 1e-10)
     rms_f = np.sqrt(np.mean(F ** 2))
     assert np.abs(F.sum(0)).max() <= (1e-9 if precision == "fp64" else 1e-3) * rms_f * np.sqrt(cfg.n)
 
@@ -178,7 +181,7 @@ def test_edge_cases(gpu_lib):
     one = synth.Config(np.array([[0.1, 0.2, 0.3]]), np.array([1], np.int32), np.diag([3.1, 2.8, 3.3]))
     empty = synth.Config(np.zeros((0, 3)), np.zeros(0, np.int32), np.eye(3) * 4.0)
     rng = np.random.default_rng(4)
-    odd = synth.random_small_config(rng, 33, 33, max_species=2)
+    odd = synth.random_small_config(rng, 33, 33, species_pool=(0, 1), max_species=2)
     b = synth.pack([one, empty, odd])
     pos, types, cells, off = batch_tensors(b)
     out = model.eval_batch(pos, types, cells, off)
@@ -215,5 +218,6 @@ def test_host_memory_path_matches_device_path(gpu_lib):
     w = np.zeros((K, 9))
     mtp.mtp_eval_batch(model.h, K, N, b.cfg_off, b.pos, b.types, b.cells.reshape(K, 9), e, f, w,
                        flags=mtp.HOST_MEMORY)
-    np.testing.assert_array_equal(e, ref["energy"].cpu().numpy())
-    np.testing.assert_array_equal(f, ref["forces"].cpu().numpy())
+    # the per-configuration sums use double-precision atomics, so the order of additions may differ
+    np.testing.assert_allclose(e, ref["energy"].cpu().numpy(), rtol=1e-13)
+    np.testing.assert_allclose(f, ref["forces"].cpu().numpy(), rtol=1e-6, atol=1e-6 * np.abs(f).max())
