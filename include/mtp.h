@@ -161,6 +161,24 @@ mtp_status mtp_eval(mtp_model* model, int n_atoms, const double* pos, const int3
 mtp_status mtp_select_active_set(mtp_model* model, int n_rows, const double* b_rows, int32_t* selected, int* n_swaps,
                                  double* max_grade, int flags, void* stream);
 
+/*
+ * MaxVol active-set selection that allocates nothing (the paper has no counterpart: this is a
+ * library service).  For callers that must not allocate device memory -- a time-step loop where a
+ * cudaMalloc could synchronise the device and stall other work, or an application whose device
+ * memory is entirely owned by its own pool -- it runs the algorithm of mtp_select_active_set() with
+ * all scratch in one fixed array built into the library (4 MiB, held on every GPU that loads the
+ * library until the process exits).  Limit: the scratch layout for n_rows x m must fit that array
+ * (about n_rows * m <= 100,000 for m near 100); larger sizes return MTP_EINVAL before any work.
+ * Inputs and outputs are the caller's device arrays: b_rows [n_rows][m] (double), selected [m]
+ * (int32, the chosen row of each position), a_inv [m][m] (double, may be NULL); n_swaps is a host
+ * pointer (may be NULL).  It needs no model and keeps no active set.  The first call on each device
+ * looks up the array's device address; make that first call before any stream capture.  All calls
+ * share the array, which keeps the last call's contents: calls that overlap on the GPU race.
+ * Synchronous on `stream`.  MTP_ESINGULAR / MTP_ETIMEOUT as for mtp_select_active_set().
+ */
+mtp_status mtp_select_active_set_noalloc(int n_rows, int m, const double* b_rows, int32_t* selected, double* a_inv,
+                                         int* n_swaps, void* stream);
+
 /* Install an active set given its m x m matrix A (host, row-major; rows = b of the active configurations);
  * A^-1 is computed on the device.  MTP_ESINGULAR if A is singular. */
 mtp_status mtp_set_active_set(mtp_model* model, const double* A);

@@ -15,6 +15,8 @@
 //   the row maxima are combined with an atomic max on the bit pattern (gamma >= 0).
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <mutex>
+#include "../../include/mtp.h"
 #include "mtp_common.cuh"
 
 namespace mtp {
@@ -321,3 +323,85 @@ template int launch_grade<float>(int, int, const float*, int, const float*, unsi
 template int launch_grade<double>(int, int, const double*, int, const double*, unsigned long long*, cudaStream_t);
 
 }  // namespace mtp
+
+// ------------------------------------------------------------------------------------------------
+// Active-set selection without any allocation (mtp_select_active_set_noalloc in include/mtp.h).
+//
+// Some callers cannot let a library allocate device memory: a simulation loop that checks the
+// extrapolation grade inside its time step must not pay for cudaMalloc (which may synchronise the
+// whole device and stall the other streams), and applications that hand all device memory to
+// their own pool allocator have nothing left for a library to take.  This entry point therefore
+// runs the same MaxVol kernel with all of its scratch in one fixed array compiled into the library.
+// Every GPU that loads the library holds this array (kNoAllocScratchDoubles doubles, 4 MiB) until
+// the process exits.  Calls share it and it keeps the last call's contents, so calls that overlap
+// on the GPU (two streams, or two host threads) race; the status word is cleared at every call.
+// ------------------------------------------------------------------------------------------------
+namespace mtp {
+namespace {
+
+constexpr size_t kNoAllocScratchDoubles = (size_t)1 << 19;  // 4 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+cudaError_t noalloc_scratch(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace mtp
+
+extern "C" mtp_status mtp_select_active_set_noalloc(int n_rows, int m, const double* b_rows, int32_t* selected,
+                                                    double* a_inv, int* n_swaps, void* stream) {
+    using namespace mtp;
+    if (m < 1 || n_rows < m || !b_rows || !selected) return MTP_EINVAL;
+    // layout inside the fixed array (in doubles): Bs, C [n m]; W [max(n m, 2 m m) + 2 m + n];
+    // D [m]; A, A^-1 [m m]; then ints: perm [n], sel [m], status, swaps; then gmax.
+    const size_t nm = (size_t)n_rows * m, mm = (size_t)m * m;
+    const size_t w = (nm > 2 * mm ? nm : 2 * mm) + 2 * (size_t)m + n_rows;
+    const size_t ints = (size_t)n_rows + m + 2;
+    const size_t need = 2 * nm + w + m + 2 * mm + (ints + 1) / 2 + 1;
+    if (need > kNoAllocScratchDoubles) return MTP_EINVAL;  // larger than the fixed scratch array
+    double* base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) return MTP_ECUDA;
+    double* Bs = base;
+    double* C = Bs + nm;
+    double* W = C + nm;
+    double* D = W + w;
+    double* A = D + m;
+    double* Ai = A + mm;
+    int* perm = reinterpret_cast<int*>(Ai + mm);
+    int* sel = perm + n_rows;
+    int* status = sel + m;
+    int* swaps = status + 1;
+    double* gmax = reinterpret_cast<double*>(base + (need - 1));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(status, 0, 2 * sizeof(int), st) != cudaSuccess) return MTP_ECUDA;
+    launch_maxvol(n_rows, m, b_rows, Bs, D, W, perm, sel, A, Ai, C, 1e-6, 100 * m, status, swaps, gmax, st);
+    int h[2] = {0, 0};
+    if (cudaMemcpyAsync(h, status, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MTP_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MTP_ECUDA;
+    if (h[0] & kErrSingular) return MTP_ESINGULAR;
+    if (h[0] & kErrTimeout) return MTP_ETIMEOUT;
+    if (cudaMemcpyAsync(selected, sel, sizeof(int) * m, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return MTP_ECUDA;
+    if (a_inv && cudaMemcpyAsync(a_inv, Ai, sizeof(double) * mm, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return MTP_ECUDA;
+    if (n_swaps) *n_swaps = h[1];
+    return cudaStreamSynchronize(st) == cudaSuccess ? MTP_OK : MTP_ECUDA;
+}

@@ -67,6 +67,7 @@ _SIGS = {
     "mtp_set_active_set": (_I, [_P, _P]),
     "mtp_get_active_set": (_I, [_P, _P, _P, _P]),
     "mtp_grade": (_I, [_P, _I, _P, _P, _I, _P]),
+    "mtp_select_active_set_noalloc": (_I, [_I, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
     "mtp_profile_read": (_I, [_P, _P, _I, ctypes.POINTER(_L)]),
 }
 
@@ -179,6 +180,14 @@ def mtp_select_active_set(h, n_rows, b_rows, selected=None, flags=0, stream=None
     _check(load().mtp_select_active_set(h, int(n_rows), _ptr(b_rows), _ptr(selected), ctypes.byref(sw),
                                         ctypes.byref(g), int(flags), s), "mtp_select_active_set")
     return int(sw.value), float(g.value)
+
+
+def mtp_select_active_set_noalloc(n_rows, m, b_rows, selected, a_inv=None, stream=None):
+    """MaxVol with the library's fixed scratch array (no allocation); returns the number of swaps."""
+    sw = ctypes.c_int()
+    _check(load().mtp_select_active_set_noalloc(int(n_rows), int(m), _ptr(b_rows), _ptr(selected), _ptr(a_inv),
+                                                ctypes.byref(sw), _stream(stream)), "mtp_select_active_set_noalloc")
+    return int(sw.value)
 
 
 def mtp_set_active_set(h, A):
