@@ -151,7 +151,7 @@ mtp_status mtp_eval(mtp_model* model, int n_atoms, const double* pos, const int3
  * Active set by MaxVol (Sec. 2.3, Eq. 13; Goreinov et al. 2010).  Chooses m of the n_rows >= m rows of
  * the tall matrix b_rows [n_rows][m] (double) so that |det A| of the m x m submatrix cannot grow by
  * exchanging one row: start from the pivot rows of Gaussian elimination with partial pivoting, then
- * repeatedly let the row and column of the largest |c| of C = B A^-1 swap in, while it exceeds 1 + 1e-6
+ * repeatedly let the row and column of the largest |c| of C = B A^-1 swap in, while it exceeds 1 + 1e-3
  * (ties: smallest row, then smallest column), at most 100 m swaps.  Columns are first scaled by
  * 1 / max |column|, which changes neither C nor the selection but conditions the arithmetic.  A and A^-1 (double) stay in the
  * model for grades.  selected[m] receives the chosen row indices (position j = row of A), n_swaps the

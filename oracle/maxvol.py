@@ -15,8 +15,8 @@ Readings where the paper is silent (each stated in the design notes):
   * start: the m pivot rows of Gaussian elimination with partial pivoting on B;
   * a sweep computes C = B A^{-1} for every row, takes the largest |C_kj| (ties: the first in
     row-major order, i.e. smallest row k, then smallest column j) and swaps while it exceeds
-    1 + tol (tol = 1e-6: rounding noise of C on ill-conditioned rows exceeds 1e-9 and would
-    make the swaps cycle);
+    1 + tol (tol = 1e-3: on real b rows, whose condition number reaches 1e13 even after column
+    scaling, the rounding noise of C exceeds 1e-6 and smaller thresholds make the swaps cycle);
   * at most max_iter = 100 m swaps;
   * the columns of B are first scaled by 1 / max |column|: C = B A^{-1} is unchanged by B -> B D
     (it becomes B D (A D)^{-1}), so this only conditions the arithmetic.
@@ -55,7 +55,7 @@ def pivot_rows(B):
     return np.asarray([int(np.argmax(P[:, k])) for k in range(m)], dtype=np.int64)
 
 
-def maxvol(B, tol=1e-6, max_iter=None):
+def maxvol(B, tol=1e-3, max_iter=None):
     """Active set of m rows of the tall matrix B.  Returns (rows [m], swaps, final max |C|)."""
     B, _ = equilibrate(B)
     K, m = B.shape

@@ -524,7 +524,7 @@ mtp_status mtp_select_active_set(mtp_model* M, int n_rows, const double* b_rows,
     cudaMemsetAsync(M->mv_status.p, 0, sizeof(int), st);
     M->launches += mtp::launch_maxvol(n, m, B, M->mv_Bs.as<double>(), M->mv_D.as<double>(), M->mv_W.as<double>(),
                                       M->mv_perm.as<int>(), M->mv_sel.as<int>(), M->d_A.as<double>(),
-                                      M->d_Ai.as<double>(), M->mv_C.as<double>(), 1e-6, 100 * m,
+                                      M->d_Ai.as<double>(), M->mv_C.as<double>(), 1e-3, 100 * m,
                                       M->mv_status.as<int>(), M->mv_swaps.as<int>(), M->mv_gmax.as<double>(), st);
     int status = 0, swaps = 0;
     double g = 0.0;

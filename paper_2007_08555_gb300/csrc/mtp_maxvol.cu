@@ -8,7 +8,7 @@
 //   2. A^-1 of A = B[sel] by Gauss-Jordan elimination with partial pivoting;
 //   3. C = B A^-1 for every row;
 //   4. repeat at most max_iter times: (k, j) = argmax |C_kj| (ties: smallest k, then smallest j);
-//      stop when |C_kj| <= 1 + tol (tol = 1e-6); otherwise row k replaces active row j, and A^-1 and C follow
+//      stop when |C_kj| <= 1 + tol (tol = 1e-3); otherwise row k replaces active row j, and A^-1 and C follow
 //      by the rank-one (Sherman-Morrison) update  C <- C - C[:,j] (C[k,:] - e_j) / C_kj.
 //   A^-1 is recomputed from scratch at the end.
 // k_grade: gamma_r = max_j |(b_r A^-1)_j| for many rows; 64x64 output tiles through shared memory,
@@ -393,7 +393,7 @@ extern "C" mtp_status mtp_select_active_set_noalloc(int n_rows, int m, const dou
     double* gmax = reinterpret_cast<double*>(base + (need - 1));
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(status, 0, 2 * sizeof(int), st) != cudaSuccess) return MTP_ECUDA;
-    launch_maxvol(n_rows, m, b_rows, Bs, D, W, perm, sel, A, Ai, C, 1e-6, 100 * m, status, swaps, gmax, st);
+    launch_maxvol(n_rows, m, b_rows, Bs, D, W, perm, sel, A, Ai, C, 1e-3, 100 * m, status, swaps, gmax, st);
     int h[2] = {0, 0};
     if (cudaMemcpyAsync(h, status, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MTP_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return MTP_ECUDA;
