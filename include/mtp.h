@@ -191,6 +191,22 @@ mtp_status mtp_get_active_set(const mtp_model* model, double* A, double* A_inv, 
  * [n_rows][m] (double), in double precision.  Device arrays unless MTP_HOST_MEMORY. */
 mtp_status mtp_grade(mtp_model* model, int n_rows, const double* b_rows, double* gamma, int flags, void* stream);
 
+/*
+ * Training loss and its exact gradient in theta = {xi, c} (Sec. 2.2, Eqs. 7, 11, 12):
+ *   L = sum_k s_e w_e (E_k - e_ref_k)^2 + s_f w_f sum_i |F_i - f_ref_i|^2 + s_s w_s |W_k - w_ref_k|_F^2
+ * with the per-configuration scalings of the paper, scaling = 0 "molecules" (Eq. 7: 1, 1, 1),
+ * 1 "structures" (Eq. 11: 1/N^2, 1/N, 1/N^2), 2 "vibrations" (Eq. 12: 1/N, 1, 1/N); the stress
+ * term uses the virial W (eV, extensive).  The batch layout is that of mtp_eval_batch; e_ref [n_cfg],
+ * f_ref [n_atoms][3], w_ref [n_cfg][9].  Outputs: loss [1], d_xi [m], d_c [S][S][N_mu][N_Q] (each may
+ * be NULL).  The force and stress terms are obtained as the derivative of the pair gradients along
+ * the residual displacements (the mixed second derivative), recomputed rather than stored.
+ * Device arrays unless MTP_HOST_MEMORY.  Gradient sums are accumulated in double precision.
+ */
+mtp_status mtp_param_grad(mtp_model* model, int n_cfg, int n_atoms, const int32_t* cfg_off, const double* pos,
+                          const int32_t* types, const double* cells, const double* e_ref, const double* f_ref,
+                          const double* w_ref, double w_e, double w_f, double w_s, int scaling, double* loss,
+                          double* d_xi, double* d_c, int flags, void* stream);
+
 /* Wait for the model's work on `stream` and report errors detected on the device since the last
  * check (MTP_EOVERFLOW, MTP_EINVAL for bad species or shifts). */
 mtp_status mtp_sync(mtp_model* model, void* stream);

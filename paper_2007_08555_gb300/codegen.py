@@ -636,6 +636,49 @@ def emit_slice_functions(prog: Program, slc, tag):
                     out.append(f"      {gv} += {coef}al * {src};")
             out.append("    }")
         out.append("  }")
+        # tangent of the moments along per-pair displacements u (loss gradient):
+        #   acc[t] += df[mu] (r-hat . u) mono + f[mu] (grad mono . u)
+        out.append("  template <class T> static __device__ __forceinline__ void tmom(const T x, const T y, const T z, "
+                   "const T* __restrict__ f, const T* __restrict__ df, const T rdu, const T ux, const T uy, const T uz, "
+                   "T* __restrict__ acc) {")
+        out += ["    " + l for l in _mono_code(need, "T")]
+        for t, ci in enumerate(comps):
+            mu, m = prog.comp_list[ci]
+            mv = "T(1)" if m == (0, 0, 0) else _mono_name(m)
+            gterms = []
+            for k, uv in enumerate(("ux", "uy", "uz")):
+                if m[k] > 0:
+                    mm = list(m)
+                    mm[k] -= 1
+                    mm = tuple(mm)
+                    src = "T(1)" if mm == (0, 0, 0) else _mono_name(mm)
+                    coef = "" if m[k] == 1 else f"T({m[k]}) * "
+                    gterms.append(f"{coef}{src} * {uv}")
+            g = " + ".join(gterms) if gterms else "T(0)"
+            out.append(f"    acc[{t}] += df[{mu}] * rdu * {mv} + f[{mu}] * ({g});")
+        out.append("  }")
+        # P_mu = sum adj mono and its tangent Pd_mu = sum adjt mono + adj (grad mono . u), with the
+        # adjoint values read from the tile layout (stride 32) starting at this slice
+        out.append("  template <class T> static __device__ __forceinline__ void pdot(const T x, const T y, const T z, "
+                   "const T* __restrict__ adjp, const T* __restrict__ adjtp, const T ux, const T uy, const T uz, "
+                   "T* __restrict__ P, T* __restrict__ Pd) {")
+        out += ["    " + l for l in _mono_code(need, "T")]
+        for t, ci in enumerate(comps):
+            mu, m = prog.comp_list[ci]
+            mv = "T(1)" if m == (0, 0, 0) else _mono_name(m)
+            gterms = []
+            for k, uv in enumerate(("ux", "uy", "uz")):
+                if m[k] > 0:
+                    mm = list(m)
+                    mm[k] -= 1
+                    mm = tuple(mm)
+                    src = "T(1)" if mm == (0, 0, 0) else _mono_name(mm)
+                    coef = "" if m[k] == 1 else f"T({m[k]}) * "
+                    gterms.append(f"{coef}{src} * {uv}")
+            g = " + ".join(gterms) if gterms else "T(0)"
+            out.append(f"    {{ const T av = adjp[{t * 32}], atv = adjtp[{t * 32}];")
+            out.append(f"      P[{mu}] += av * {mv}; Pd[{mu}] += atv * {mv} + av * ({g}); }}")
+        out.append("  }")
         out.append("};")
     return out
 

@@ -51,6 +51,13 @@ template <> struct SliceF<0> {
       s += be * T(1);
     }
   }
+  template <class T> static __device__ __forceinline__ void tmom(const T x, const T y, const T z, const T* __restrict__ f, const T* __restrict__ df, const T rdu, const T ux, const T uy, const T uz, T* __restrict__ acc) {
+    acc[0] += df[0] * rdu * T(1) + f[0] * (T(0));
+  }
+  template <class T> static __device__ __forceinline__ void pdot(const T x, const T y, const T z, const T* __restrict__ adjp, const T* __restrict__ adjtp, const T ux, const T uy, const T uz, T* __restrict__ P, T* __restrict__ Pd) {
+    { const T av = adjp[0], atv = adjtp[0];
+      P[0] += av * T(1); Pd[0] += atv * T(1) + av * (T(0)); }
+  }
 };
 template <int S> struct SliceD;
 template <> struct SliceD<0> {
@@ -62,6 +69,13 @@ template <> struct SliceD<0> {
     { const T al = adj[0] * f[0]; const T be = adj[0] * df[0];
       s += be * T(1);
     }
+  }
+  template <class T> static __device__ __forceinline__ void tmom(const T x, const T y, const T z, const T* __restrict__ f, const T* __restrict__ df, const T rdu, const T ux, const T uy, const T uz, T* __restrict__ acc) {
+    acc[0] += df[0] * rdu * T(1) + f[0] * (T(0));
+  }
+  template <class T> static __device__ __forceinline__ void pdot(const T x, const T y, const T z, const T* __restrict__ adjp, const T* __restrict__ adjtp, const T ux, const T uy, const T uz, T* __restrict__ P, T* __restrict__ Pd) {
+    { const T av = adjp[0], atv = adjtp[0];
+      P[0] += av * T(1); Pd[0] += atv * T(1) + av * (T(0)); }
   }
 };
 struct Traits {

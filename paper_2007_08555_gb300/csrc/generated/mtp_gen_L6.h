@@ -103,6 +103,31 @@ template <> struct SliceF<0> {
       gz += al * T(1);
     }
   }
+  template <class T> static __device__ __forceinline__ void tmom(const T x, const T y, const T z, const T* __restrict__ f, const T* __restrict__ df, const T rdu, const T ux, const T uy, const T uz, T* __restrict__ acc) {
+    const T m1_0_0 = x;
+    const T m0_1_0 = y;
+    const T m0_0_1 = z;
+    acc[0] += df[0] * rdu * T(1) + f[0] * (T(0));
+    acc[1] += df[1] * rdu * T(1) + f[1] * (T(0));
+    acc[2] += df[0] * rdu * m1_0_0 + f[0] * (T(1) * ux);
+    acc[3] += df[0] * rdu * m0_1_0 + f[0] * (T(1) * uy);
+    acc[4] += df[0] * rdu * m0_0_1 + f[0] * (T(1) * uz);
+  }
+  template <class T> static __device__ __forceinline__ void pdot(const T x, const T y, const T z, const T* __restrict__ adjp, const T* __restrict__ adjtp, const T ux, const T uy, const T uz, T* __restrict__ P, T* __restrict__ Pd) {
+    const T m1_0_0 = x;
+    const T m0_1_0 = y;
+    const T m0_0_1 = z;
+    { const T av = adjp[0], atv = adjtp[0];
+      P[0] += av * T(1); Pd[0] += atv * T(1) + av * (T(0)); }
+    { const T av = adjp[32], atv = adjtp[32];
+      P[1] += av * T(1); Pd[1] += atv * T(1) + av * (T(0)); }
+    { const T av = adjp[64], atv = adjtp[64];
+      P[0] += av * m1_0_0; Pd[0] += atv * m1_0_0 + av * (T(1) * ux); }
+    { const T av = adjp[96], atv = adjtp[96];
+      P[0] += av * m0_1_0; Pd[0] += atv * m0_1_0 + av * (T(1) * uy); }
+    { const T av = adjp[128], atv = adjtp[128];
+      P[0] += av * m0_0_1; Pd[0] += atv * m0_0_1 + av * (T(1) * uz); }
+  }
 };
 template <int S> struct SliceD;
 template <> struct SliceD<0> {
@@ -136,6 +161,31 @@ template <> struct SliceD<0> {
       s += be * m0_0_1;
       gz += al * T(1);
     }
+  }
+  template <class T> static __device__ __forceinline__ void tmom(const T x, const T y, const T z, const T* __restrict__ f, const T* __restrict__ df, const T rdu, const T ux, const T uy, const T uz, T* __restrict__ acc) {
+    const T m1_0_0 = x;
+    const T m0_1_0 = y;
+    const T m0_0_1 = z;
+    acc[0] += df[0] * rdu * T(1) + f[0] * (T(0));
+    acc[1] += df[1] * rdu * T(1) + f[1] * (T(0));
+    acc[2] += df[0] * rdu * m1_0_0 + f[0] * (T(1) * ux);
+    acc[3] += df[0] * rdu * m0_1_0 + f[0] * (T(1) * uy);
+    acc[4] += df[0] * rdu * m0_0_1 + f[0] * (T(1) * uz);
+  }
+  template <class T> static __device__ __forceinline__ void pdot(const T x, const T y, const T z, const T* __restrict__ adjp, const T* __restrict__ adjtp, const T ux, const T uy, const T uz, T* __restrict__ P, T* __restrict__ Pd) {
+    const T m1_0_0 = x;
+    const T m0_1_0 = y;
+    const T m0_0_1 = z;
+    { const T av = adjp[0], atv = adjtp[0];
+      P[0] += av * T(1); Pd[0] += atv * T(1) + av * (T(0)); }
+    { const T av = adjp[32], atv = adjtp[32];
+      P[1] += av * T(1); Pd[1] += atv * T(1) + av * (T(0)); }
+    { const T av = adjp[64], atv = adjtp[64];
+      P[0] += av * m1_0_0; Pd[0] += atv * m1_0_0 + av * (T(1) * ux); }
+    { const T av = adjp[96], atv = adjtp[96];
+      P[0] += av * m0_1_0; Pd[0] += atv * m0_1_0 + av * (T(1) * uy); }
+    { const T av = adjp[128], atv = adjtp[128];
+      P[0] += av * m0_0_1; Pd[0] += atv * m0_0_1 + av * (T(1) * uz); }
   }
 };
 struct Traits {

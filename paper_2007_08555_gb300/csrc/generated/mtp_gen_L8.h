@@ -200,6 +200,61 @@ template <> struct SliceF<0> {
       gz += T(2) * al * m0_0_1;
     }
   }
+  template <class T> static __device__ __forceinline__ void tmom(const T x, const T y, const T z, const T* __restrict__ f, const T* __restrict__ df, const T rdu, const T ux, const T uy, const T uz, T* __restrict__ acc) {
+    const T m1_0_0 = x;
+    const T m0_1_0 = y;
+    const T m0_0_1 = z;
+    const T m2_0_0 = m1_0_0 * x;
+    const T m1_1_0 = m0_1_0 * x;
+    const T m1_0_1 = m0_0_1 * x;
+    const T m0_2_0 = m0_1_0 * y;
+    const T m0_1_1 = m0_0_1 * y;
+    const T m0_0_2 = m0_0_1 * z;
+    acc[0] += df[0] * rdu * T(1) + f[0] * (T(0));
+    acc[1] += df[1] * rdu * T(1) + f[1] * (T(0));
+    acc[2] += df[0] * rdu * m1_0_0 + f[0] * (T(1) * ux);
+    acc[3] += df[0] * rdu * m0_1_0 + f[0] * (T(1) * uy);
+    acc[4] += df[0] * rdu * m0_0_1 + f[0] * (T(1) * uz);
+    acc[5] += df[0] * rdu * m2_0_0 + f[0] * (T(2) * m1_0_0 * ux);
+    acc[6] += df[0] * rdu * m1_1_0 + f[0] * (m0_1_0 * ux + m1_0_0 * uy);
+    acc[7] += df[0] * rdu * m1_0_1 + f[0] * (m0_0_1 * ux + m1_0_0 * uz);
+    acc[8] += df[0] * rdu * m0_2_0 + f[0] * (T(2) * m0_1_0 * uy);
+    acc[9] += df[0] * rdu * m0_1_1 + f[0] * (m0_0_1 * uy + m0_1_0 * uz);
+    acc[10] += df[0] * rdu * m0_0_2 + f[0] * (T(2) * m0_0_1 * uz);
+  }
+  template <class T> static __device__ __forceinline__ void pdot(const T x, const T y, const T z, const T* __restrict__ adjp, const T* __restrict__ adjtp, const T ux, const T uy, const T uz, T* __restrict__ P, T* __restrict__ Pd) {
+    const T m1_0_0 = x;
+    const T m0_1_0 = y;
+    const T m0_0_1 = z;
+    const T m2_0_0 = m1_0_0 * x;
+    const T m1_1_0 = m0_1_0 * x;
+    const T m1_0_1 = m0_0_1 * x;
+    const T m0_2_0 = m0_1_0 * y;
+    const T m0_1_1 = m0_0_1 * y;
+    const T m0_0_2 = m0_0_1 * z;
+    { const T av = adjp[0], atv = adjtp[0];
+      P[0] += av * T(1); Pd[0] += atv * T(1) + av * (T(0)); }
+    { const T av = adjp[32], atv = adjtp[32];
+      P[1] += av * T(1); Pd[1] += atv * T(1) + av * (T(0)); }
+    { const T av = adjp[64], atv = adjtp[64];
+      P[0] += av * m1_0_0; Pd[0] += atv * m1_0_0 + av * (T(1) * ux); }
+    { const T av = adjp[96], atv = adjtp[96];
+      P[0] += av * m0_1_0; Pd[0] += atv * m0_1_0 + av * (T(1) * uy); }
+    { const T av = adjp[128], atv = adjtp[128];
+      P[0] += av * m0_0_1; Pd[0] += atv * m0_0_1 + av * (T(1) * uz); }
+    { const T av = adjp[160], atv = adjtp[160];
+      P[0] += av * m2_0_0; Pd[0] += atv * m2_0_0 + av * (T(2) * m1_0_0 * ux); }
+    { const T av = adjp[192], atv = adjtp[192];
+      P[0] += av * m1_1_0; Pd[0] += atv * m1_1_0 + av * (m0_1_0 * ux + m1_0_0 * uy); }
+    { const T av = adjp[224], atv = adjtp[224];
+      P[0] += av * m1_0_1; Pd[0] += atv * m1_0_1 + av * (m0_0_1 * ux + m1_0_0 * uz); }
+    { const T av = adjp[256], atv = adjtp[256];
+      P[0] += av * m0_2_0; Pd[0] += atv * m0_2_0 + av * (T(2) * m0_1_0 * uy); }
+    { const T av = adjp[288], atv = adjtp[288];
+      P[0] += av * m0_1_1; Pd[0] += atv * m0_1_1 + av * (m0_0_1 * uy + m0_1_0 * uz); }
+    { const T av = adjp[320], atv = adjtp[320];
+      P[0] += av * m0_0_2; Pd[0] += atv * m0_0_2 + av * (T(2) * m0_0_1 * uz); }
+  }
 };
 template <int S> struct SliceD;
 template <> struct SliceD<0> {
@@ -278,6 +333,61 @@ template <> struct SliceD<0> {
       s += be * m0_0_2;
       gz += T(2) * al * m0_0_1;
     }
+  }
+  template <class T> static __device__ __forceinline__ void tmom(const T x, const T y, const T z, const T* __restrict__ f, const T* __restrict__ df, const T rdu, const T ux, const T uy, const T uz, T* __restrict__ acc) {
+    const T m1_0_0 = x;
+    const T m0_1_0 = y;
+    const T m0_0_1 = z;
+    const T m2_0_0 = m1_0_0 * x;
+    const T m1_1_0 = m0_1_0 * x;
+    const T m1_0_1 = m0_0_1 * x;
+    const T m0_2_0 = m0_1_0 * y;
+    const T m0_1_1 = m0_0_1 * y;
+    const T m0_0_2 = m0_0_1 * z;
+    acc[0] += df[0] * rdu * T(1) + f[0] * (T(0));
+    acc[1] += df[1] * rdu * T(1) + f[1] * (T(0));
+    acc[2] += df[0] * rdu * m1_0_0 + f[0] * (T(1) * ux);
+    acc[3] += df[0] * rdu * m0_1_0 + f[0] * (T(1) * uy);
+    acc[4] += df[0] * rdu * m0_0_1 + f[0] * (T(1) * uz);
+    acc[5] += df[0] * rdu * m2_0_0 + f[0] * (T(2) * m1_0_0 * ux);
+    acc[6] += df[0] * rdu * m1_1_0 + f[0] * (m0_1_0 * ux + m1_0_0 * uy);
+    acc[7] += df[0] * rdu * m1_0_1 + f[0] * (m0_0_1 * ux + m1_0_0 * uz);
+    acc[8] += df[0] * rdu * m0_2_0 + f[0] * (T(2) * m0_1_0 * uy);
+    acc[9] += df[0] * rdu * m0_1_1 + f[0] * (m0_0_1 * uy + m0_1_0 * uz);
+    acc[10] += df[0] * rdu * m0_0_2 + f[0] * (T(2) * m0_0_1 * uz);
+  }
+  template <class T> static __device__ __forceinline__ void pdot(const T x, const T y, const T z, const T* __restrict__ adjp, const T* __restrict__ adjtp, const T ux, const T uy, const T uz, T* __restrict__ P, T* __restrict__ Pd) {
+    const T m1_0_0 = x;
+    const T m0_1_0 = y;
+    const T m0_0_1 = z;
+    const T m2_0_0 = m1_0_0 * x;
+    const T m1_1_0 = m0_1_0 * x;
+    const T m1_0_1 = m0_0_1 * x;
+    const T m0_2_0 = m0_1_0 * y;
+    const T m0_1_1 = m0_0_1 * y;
+    const T m0_0_2 = m0_0_1 * z;
+    { const T av = adjp[0], atv = adjtp[0];
+      P[0] += av * T(1); Pd[0] += atv * T(1) + av * (T(0)); }
+    { const T av = adjp[32], atv = adjtp[32];
+      P[1] += av * T(1); Pd[1] += atv * T(1) + av * (T(0)); }
+    { const T av = adjp[64], atv = adjtp[64];
+      P[0] += av * m1_0_0; Pd[0] += atv * m1_0_0 + av * (T(1) * ux); }
+    { const T av = adjp[96], atv = adjtp[96];
+      P[0] += av * m0_1_0; Pd[0] += atv * m0_1_0 + av * (T(1) * uy); }
+    { const T av = adjp[128], atv = adjtp[128];
+      P[0] += av * m0_0_1; Pd[0] += atv * m0_0_1 + av * (T(1) * uz); }
+    { const T av = adjp[160], atv = adjtp[160];
+      P[0] += av * m2_0_0; Pd[0] += atv * m2_0_0 + av * (T(2) * m1_0_0 * ux); }
+    { const T av = adjp[192], atv = adjtp[192];
+      P[0] += av * m1_1_0; Pd[0] += atv * m1_1_0 + av * (m0_1_0 * ux + m1_0_0 * uy); }
+    { const T av = adjp[224], atv = adjtp[224];
+      P[0] += av * m1_0_1; Pd[0] += atv * m1_0_1 + av * (m0_0_1 * ux + m1_0_0 * uz); }
+    { const T av = adjp[256], atv = adjtp[256];
+      P[0] += av * m0_2_0; Pd[0] += atv * m0_2_0 + av * (T(2) * m0_1_0 * uy); }
+    { const T av = adjp[288], atv = adjtp[288];
+      P[0] += av * m0_1_1; Pd[0] += atv * m0_1_1 + av * (m0_0_1 * uy + m0_1_0 * uz); }
+    { const T av = adjp[320], atv = adjtp[320];
+      P[0] += av * m0_0_2; Pd[0] += atv * m0_0_2 + av * (T(2) * m0_0_1 * uz); }
   }
 };
 struct Traits {

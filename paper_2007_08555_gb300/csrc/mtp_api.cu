@@ -59,6 +59,7 @@ struct mtp_model {
     // active set (Sec. 2.3): rows of the last selection, A and A^-1 in double precision
     bool has_active = false;
     std::vector<int> active_rows;
+    DevBuf g_energy, g_forces, g_virial, g_D, g_eps, g_ew, g_momt, g_adjmt, g_out, g_refs;
     DevBuf d_A, d_Ai, mv_Bs, mv_D, mv_W, mv_perm, mv_sel, mv_C, mv_status, mv_swaps, mv_gmax, s_rows, s_gamma, g_brows, g_batoms;
     // profiling: events around the neighbour build and each evaluation phase
     bool profiling = false;
@@ -122,8 +123,9 @@ int choose_tpa(int n_atoms, int n_sm) {
 }
 
 template <class T>
-mtp_status run_eval(mtp_model* M, int K, int n, const int* cfg_off, const int* types, double* energy,
-                    double* forces, double* virial, double* site, double* brows, double* batoms, cudaStream_t st) {
+mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* types, double* energy,
+                    double* forces, double* virial, double* site, double* brows, double* batoms, cudaStream_t st,
+                    mtp::EvalCtx<T>& a) {
     const size_t N = (size_t)n;
     const size_t tiles = (N + 31) / 32;
     const int cap = M->nb.cap;
@@ -133,7 +135,7 @@ mtp_status run_eval(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     if (energy) cudaMemsetAsync(energy, 0, sizeof(double) * K, st);
     if (virial) cudaMemsetAsync(virial, 0, sizeof(double) * 9 * K, st);
     if (brows) cudaMemsetAsync(brows, 0, sizeof(double) * (size_t)M->m * K, st);
-    mtp::EvalCtx<T> a;
+    a = mtp::EvalCtx<T>{};
     a.n_atoms = n;
     a.n_cfg = K;
     a.cap = cap;
@@ -176,6 +178,16 @@ mtp_status run_eval(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     a.forces = forces;
     a.virial = virial;
     a.err = M->nb.err.as<int>();
+    return MTP_OK;
+}
+
+template <class T>
+mtp_status run_eval(mtp_model* M, int K, int n, const int* cfg_off, const int* types, double* energy,
+                    double* forces, double* virial, double* site, double* brows, double* batoms, cudaStream_t st,
+                    mtp::EvalCtx<T>* keep = nullptr) {
+    mtp::EvalCtx<T> a;
+    mtp_status s = fill_ctx<T>(M, K, n, cfg_off, types, energy, forces, virial, site, brows, batoms, st, a);
+    if (s) return s;
     int l;
     cudaEvent_t* marks = M->profiling ? M->ev_phase : nullptr;
     if constexpr (sizeof(T) == 8)
@@ -184,6 +196,7 @@ mtp_status run_eval(mtp_model* M, int K, int n, const int* cfg_off, const int* t
         l = M->ops->eval_f32(a, st, M->n_sm, marks);
     if (l < 0) return MTP_EUNSUPPORTED;
     M->launches += l;
+    if (keep) *keep = a;
     return cuda_status(cudaGetLastError());
 }
 
@@ -303,7 +316,8 @@ void mtp_destroy(mtp_model* M) {
                       &M->nb.count, &M->nb.jz, &M->nb.shift, &M->nb.rev, &M->nb.rx, &M->nb.ry, &M->nb.rz,
                       &M->nb.cfg_of, &M->nb.desc, &M->nb.atom_bin, &M->nb.atom_wrap, &M->nb.atom_local,
                       &M->nb.bin_count, &M->nb.bin_start, &M->nb.bin_fill, &M->nb.bin_atoms, &M->nb.scan_tmp,
-                      &M->nb.err, &M->nb.max_seen, &M->d_A, &M->d_Ai, &M->mv_Bs, &M->mv_D, &M->mv_W, &M->mv_perm, &M->mv_sel,
+                      &M->nb.err, &M->nb.max_seen, &M->g_energy, &M->g_forces, &M->g_virial, &M->g_D, &M->g_eps, &M->g_ew,
+                      &M->g_momt, &M->g_adjmt, &M->g_out, &M->g_refs, &M->d_A, &M->d_Ai, &M->mv_Bs, &M->mv_D, &M->mv_W, &M->mv_perm, &M->mv_sel,
                       &M->mv_C, &M->mv_status, &M->mv_swaps, &M->mv_gmax, &M->s_rows, &M->s_gamma, &M->g_brows,
                       &M->g_batoms};
     for (DevBuf* b : bufs) b->release();
@@ -386,6 +400,112 @@ static mtp_status prepare_neighbors(mtp_model* M, int K, int n, const int* off, 
     M->launches += l;
     return MTP_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+template <class T>
+mtp_status run_param_grad(mtp_model* M, int K, int n, const int* off, const int* types, const double* e_ref,
+                          const double* f_ref, const double* w_ref, double we, double wf, double ws, int scaling,
+                          double* out, cudaStream_t st) {
+    const size_t N = (size_t)n;
+    const int nc = (int)M->c.size();
+    if (M->g_energy.reserve(8 * (size_t)K + 8) || M->g_forces.reserve(24 * N + 8) ||
+        M->g_virial.reserve(72 * (size_t)K + 8) || M->g_D.reserve(3 * N * sizeof(T) + 8) ||
+        M->g_eps.reserve(9 * (size_t)K * sizeof(T) + 8) || M->g_ew.reserve(8 * (size_t)K + 8) ||
+        M->g_momt.reserve(((N + 31) / 32) * M->C * 32 * sizeof(T)) ||
+        M->g_adjmt.reserve(((N + 31) / 32) * M->C * 32 * sizeof(T)))
+        return MTP_ENOMEM;
+    mtp::EvalCtx<T> a;
+    mtp_status s = run_eval<T>(M, K, n, off, types, M->g_energy.as<double>(), M->g_forces.as<double>(),
+                               M->g_virial.as<double>(), nullptr, nullptr, nullptr, st, &a);
+    if (s) return s;
+    // out = [loss, dxi (m), dc (nc)]
+    cudaMemsetAsync(out, 0, sizeof(double) * (1 + M->m + nc), st);
+    a.gD = M->g_D.as<T>();
+    a.geps = M->g_eps.as<T>();
+    a.gew = M->g_ew.as<double>();
+    a.momt = M->g_momt.as<T>();
+    a.adjmt = M->g_adjmt.as<T>();
+    a.dxi = out + 1;
+    a.dc = out + 1 + M->m;
+    mtp::LossArgs L;
+    L.n_atoms = n;
+    L.n_cfg = K;
+    L.scaling = scaling;
+    L.we = we;
+    L.wf = wf;
+    L.ws = ws;
+    L.cfg_off = off;
+    L.cfg_of = M->nb.cfg_of.as<int>();
+    L.energy = M->g_energy.as<double>();
+    L.forces = M->g_forces.as<double>();
+    L.virial = M->g_virial.as<double>();
+    L.e_ref = e_ref;
+    L.f_ref = f_ref;
+    L.w_ref = w_ref;
+    L.loss = out;
+    L.gew = M->g_ew.as<double>();
+    int l;
+    if constexpr (sizeof(T) == 8)
+        l = M->ops->grad_f64(a, L, st, M->n_sm);
+    else
+        l = M->ops->grad_f32(a, L, st, M->n_sm);
+    if (l < 0) return MTP_EUNSUPPORTED;
+    M->launches += l;
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" mtp_status mtp_param_grad(mtp_model* M, int K, int n, const int32_t* cfg_off, const double* pos,
+                                     const int32_t* types, const double* cells, const double* e_ref,
+                                     const double* f_ref, const double* w_ref, double w_e, double w_f, double w_s,
+                                     int scaling, double* loss, double* d_xi, double* d_c, int flags, void* stream) {
+    if (!M || K < 1 || n < 1 || n >= (1 << 24) || !cfg_off || !pos || !types || !cells || !e_ref || !f_ref ||
+        !w_ref || scaling < 0 || scaling > 2 || !(w_e >= 0) || !(w_f >= 0) || !(w_s >= 0))
+        return MTP_EINVAL;
+    if (flags & MTP_REUSE_NEIGHBORS) return MTP_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool host = flags & MTP_HOST_MEMORY;
+    const int nc = (int)M->c.size();
+    if (host) {
+        bool ok = true;
+        cfg_off = stage_in(M->s_off, cfg_off, K + 1, st, &ok);
+        pos = stage_in(M->s_pos, pos, 3 * (size_t)n, st, &ok);
+        types = stage_in(M->s_types, types, (size_t)n, st, &ok);
+        cells = stage_in(M->s_cells, cells, 9 * (size_t)K, st, &ok);
+        if (!ok || M->g_refs.reserve(sizeof(double) * ((size_t)K * 10 + 3 * (size_t)n) + 64)) return MTP_ENOMEM;
+        double* r = M->g_refs.as<double>();
+        cudaMemcpyAsync(r, e_ref, sizeof(double) * K, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(r + K, w_ref, sizeof(double) * 9 * K, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(r + 10 * (size_t)K, f_ref, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st);
+        e_ref = r;
+        w_ref = r + K;
+        f_ref = r + 10 * (size_t)K;
+    }
+    if (M->g_out.reserve(sizeof(double) * (1 + M->m + nc) + 64)) return MTP_ENOMEM;
+    mtp_status s = prepare_neighbors(M, K, n, cfg_off, pos, types, cells, 0.0, st);
+    if (s) return s;
+    double* out = M->g_out.as<double>();
+    if (is_fp64(M))
+        s = run_param_grad<double>(M, K, n, cfg_off, types, e_ref, f_ref, w_ref, w_e, w_f, w_s, scaling, out, st);
+    else
+        s = run_param_grad<float>(M, K, n, cfg_off, types, e_ref, f_ref, w_ref, w_e, w_f, w_s, scaling, out, st);
+    if (s) return s;
+    const cudaMemcpyKind kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (loss) cudaMemcpyAsync(loss, out, sizeof(double), kind, st);
+    if (d_xi) cudaMemcpyAsync(d_xi, out + 1, sizeof(double) * M->m, kind, st);
+    if (d_c) cudaMemcpyAsync(d_c, out + 1 + M->m, sizeof(double) * nc, kind, st);
+    if (flags & MTP_ASYNC) return cuda_status(cudaGetLastError());
+    return finish(M, st);
+}
+
+namespace {
+}  // namespace
+
+extern "C" {
 
 mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, const double* pos,
                           const int32_t* types, const double* cells, double* energy, double* forces, double* virial,

@@ -61,7 +61,41 @@ struct EvalCtx {
     double* forces;       // [n][3] or NULL
     double* virial;       // [n_cfg][9] (accumulated) or NULL
     int* err;
+    // training-loss gradient (Sec. 2.2): residual directions and outputs
+    const T* gD;          // [n][3] D_i = 2 s_f w_f (F_i - F_i^ref)
+    const T* geps;        // [n_cfg][9] eps_k = 2 s_s w_s (W_k - W_k^ref)
+    const double* gew;    // [n_cfg] e_k = 2 s_e w_e (E_k - E_k^ref)
+    T* momt;              // tangent of the moments along u (tile layout)
+    T* adjmt;             // tangent of dV/dM (tile layout)
+    double* dxi;          // [M] accumulated dL/dxi
+    double* dc;           // [S][S][NMU][NQ] accumulated dL/dc
 };
+
+// Loss (Sec. 2.2): residuals and the directions of the gradient.  Scalings of Eqs. 7, 11, 12.
+struct LossArgs {
+    int n_atoms, n_cfg, scaling;  // 0 molecules, 1 structures, 2 vibrations
+    double we, wf, ws;
+    const int* cfg_off;
+    const int* cfg_of;
+    const double* energy;   // [K] model
+    const double* forces;   // [N][3] model
+    const double* virial;   // [K][9] model
+    const double* e_ref;
+    const double* f_ref;
+    const double* w_ref;
+    double* loss;           // [1] accumulated
+    double* gew;            // [K]
+};
+
+__host__ __device__ inline void loss_scales(int kind, double n, double* se, double* sf, double* ss) {
+    if (kind == 0) {
+        *se = 1.0; *sf = 1.0; *ss = 1.0;
+    } else if (kind == 1) {
+        *se = 1.0 / (n * n); *sf = 1.0 / n; *ss = 1.0 / (n * n);
+    } else {
+        *se = 1.0 / n; *sf = 1.0; *ss = 1.0 / n;
+    }
+}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

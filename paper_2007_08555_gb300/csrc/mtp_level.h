@@ -23,6 +23,9 @@ struct LevelOps {
     // launchers (stream-ordered, no synchronisation); return the number of kernels launched
     int (*eval_f32)(const EvalCtx<float>&, cudaStream_t, int n_sm, cudaEvent_t* marks);
     int (*eval_f64)(const EvalCtx<double>&, cudaStream_t, int n_sm, cudaEvent_t* marks);
+    // loss gradient after an evaluation: residuals -> tangent moments -> dual contraction -> dc
+    int (*grad_f32)(EvalCtx<float>&, const LossArgs&, cudaStream_t, int n_sm);
+    int (*grad_f64)(EvalCtx<double>&, const LossArgs&, cudaStream_t, int n_sm);
 };
 
 // Phases timed when profiling is on: marks[k] is recorded before phase k, marks[kPhases] after.

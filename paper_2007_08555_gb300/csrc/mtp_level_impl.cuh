@@ -627,6 +627,399 @@ int eval_f64(const EvalCtx<double>& a, cudaStream_t st, int n_sm, cudaEvent_t* m
     return eval_all<double>(a, st, n_sm, marks);
 }
 
+
+// ----------------------------------------------------------------------------------------------
+// Training-loss gradient (Sec. 2.2, Eqs. 7, 11, 12).  With e_k = 2 s_e w_e dE_k, D_i = 2 s_f w_f dF_i
+// and eps_k = 2 s_s w_s dW_k, the force and stress terms equal -dG/dtheta for
+// G = sum_pairs g_ij . u_ij, u_ij = (D_j - D_i) + eps_k r_ij (g_ij = dV_i/dr_ij), so
+//   dL/dxi_a = sum_i (e_k B_a(n_i) - dB_a/dt),
+//   dL/dc    = sum_pairs (e_k Q_b P_mu - Q'_b (r-hat . u) P_mu - Q_b dP_mu/dt),
+// with P_mu = sum_m dV/dM[mu,m] mono_m and d/dt the derivative along u (forward mode): the moments'
+// tangent comes from k_tmom, the programs run again on (value, tangent) pairs.
+// ----------------------------------------------------------------------------------------------
+template <class T>
+__global__ void k_resid_atoms(EvalCtx<T> a, LossArgs L, T* D) {
+    __shared__ double s_l[128];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n_atoms; i += gridDim.x * blockDim.x) {
+        const int k = L.cfg_of[i];
+        double se, sf, ss;
+        loss_scales(L.scaling, (double)(L.cfg_off[k + 1] - L.cfg_off[k]), &se, &sf, &ss);
+        double q = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double d = L.forces[3 * (size_t)i + c] - L.f_ref[3 * (size_t)i + c];
+            D[3 * (size_t)i + c] = (T)(2.0 * sf * L.wf * d);
+            q += d * d;
+        }
+        acc += sf * L.wf * q;
+    }
+    s_l[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) s_l[threadIdx.x] += s_l[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(L.loss, s_l[0]);
+}
+
+template <class T>
+__global__ void k_resid_cfgs(LossArgs L, T* eps) {
+    __shared__ double s_l[128];
+    double acc = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L.n_cfg; k += gridDim.x * blockDim.x) {
+        double se, sf, ss;
+        loss_scales(L.scaling, (double)(L.cfg_off[k + 1] - L.cfg_off[k]), &se, &sf, &ss);
+        const double de = L.energy[k] - L.e_ref[k];
+        L.gew[k] = 2.0 * se * L.we * de;
+        double q = 0.0;
+        for (int c = 0; c < 9; ++c) {
+            const double dw = L.virial[9 * (size_t)k + c] - L.w_ref[9 * (size_t)k + c];
+            eps[9 * (size_t)k + c] = (T)(2.0 * ss * L.ws * dw);
+            q += dw * dw;
+        }
+        acc += se * L.we * de * de + ss * L.ws * q;
+    }
+    s_l[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) s_l[threadIdx.x] += s_l[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(L.loss, s_l[0]);
+}
+
+// pair displacement direction u_ij = (D_j - D_i) + eps_k r_ij
+template <class T>
+__device__ __forceinline__ void pair_u(const EvalCtx<T>& a, const T* Di, const T* E, int j, T x, T y, T z, T& ux,
+                                       T& uy, T& uz) {
+    ux = (a.gD[3 * (size_t)j] - Di[0]) + (E[0] * x + E[1] * y + E[2] * z);
+    uy = (a.gD[3 * (size_t)j + 1] - Di[1]) + (E[3] * x + E[4] * y + E[5] * z);
+    uz = (a.gD[3 * (size_t)j + 2] - Di[2]) + (E[6] * x + E[7] * y + E[8] * z);
+}
+
+template <class T, int S, int TPA>
+__device__ __forceinline__ void tmom_slice(const EvalCtx<T>& a, int i, int sub, bool active, int zi, int cnt,
+                                           const T* cs, const T* Di, const T* E) {
+    using SL = typename SliceSel<T, S>::type;
+    T acc[SL::SIZE];
+#pragma unroll
+    for (int t = 0; t < SL::SIZE; ++t) acc[t] = T(0);
+    const size_t n = (size_t)a.n_atoms;
+    if (active) {
+        const int csz = G::NMU_ * a.NQ;
+        for (int p = sub; p < cnt; p += TPA) {
+            const size_t idx = (size_t)p * n + i;
+            const int jz = a.jz[idx];
+            const int j = jz & 0xffffff, zj = jz >> 24;
+            const T x = a.rx[idx], y = a.ry[idx], z = a.rz[idx];
+            const T r = my_sqrt(x * x + y * y + z * z);
+            T f[G::NMU_], df[G::NMU_];
+            radial<T, true>(r, cs + (zi * a.S + zj) * csz, a.NQ, a.rmin, a.rcut, a.inv_span, f, df);
+            T ux, uy, uz;
+            pair_u(a, Di, E, j, x, y, z, ux, uy, uz);
+            const T rdu = (x * ux + y * uy + z * uz) / r;
+            SL::template tmom<T>(x, y, z, f, df, rdu, ux, uy, uz, acc);
+        }
+    }
+    if (TPA > 1) {
+#pragma unroll
+        for (int t = 0; t < SL::SIZE; ++t) {
+#pragma unroll
+            for (int o = 1; o < TPA; o <<= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+        }
+    }
+    if (active) {
+        T* dst = a.momt + (size_t)(i >> 5) * G::C_ * 32 + (i & 31);
+#pragma unroll
+        for (int t = 0; t < SL::SIZE; ++t)
+            if (t % TPA == sub) dst[(size_t)(SL::BEGIN + t) * 32] = acc[t];
+    }
+}
+
+template <class T, int S, int NS, int TPA>
+__device__ __forceinline__ void tmom_all(const EvalCtx<T>& a, int i, int sub, bool active, int zi, int cnt,
+                                         const T* cs, const T* Di, const T* E) {
+    if constexpr (S < NS) {
+        tmom_slice<T, S, TPA>(a, i, sub, active, zi, cnt, cs, Di, E);
+        tmom_all<T, S + 1, NS, TPA>(a, i, sub, active, zi, cnt, cs, Di, E);
+    }
+}
+
+template <class T, int TPA>
+__global__ void __launch_bounds__(128) k_tmom(const EvalCtx<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* cs = reinterpret_cast<T*>(smem_raw);
+    load_c(a, cs);
+    const int stride = gridDim.x * blockDim.x;
+    const int n_groups = ((a.n_atoms + 31) / 32) * 32;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups * TPA; g += stride) {
+        const int i = g / TPA, sub = g % TPA;
+        const bool active = i < a.n_atoms;
+        int zi = 0, cnt = 0;
+        T Di[3] = {T(0), T(0), T(0)}, E[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) E[q] = T(0);
+        if (active) {
+            zi = clamp_species(a.types[i], a.S);
+            cnt = a.count[i];
+            for (int q = 0; q < 3; ++q) Di[q] = a.gD[3 * (size_t)i + q];
+            const int k = a.cfg_of[i];
+            for (int q = 0; q < 9; ++q) E[q] = a.geps[9 * (size_t)k + q];
+        }
+        tmom_all<T, 0, NumSlices<T>::value, TPA>(a, i, sub, active, zi, cnt, cs, Di, E);
+    }
+}
+
+// forward and adjoint programs on (value, tangent) pairs, warp per atom
+template <class T, bool ADJ>
+__device__ __forceinline__ void run_program_dual(const unsigned long long* __restrict__ ops,
+                                                 const int* __restrict__ layer_end, int layers, const float* sw,
+                                                 T* val, T* tan, T* adj, T* adt, int lane) {
+    int row = 0;
+    for (int l = 0; l < layers; ++l) {
+        const int end = layer_end[l];
+        T acc = T(0), acct = T(0);
+        for (; row < end; ++row) {
+            const unsigned long long op = ops[row * 32 + lane];
+            const unsigned fl = (unsigned)(op >> 48) & 7u;
+            if (fl & 4u) continue;
+            const int i = (int)(op & 0xffffu), j = (int)((op >> 16) & 0xffffu), k = (int)((op >> 32) & 0xffffu);
+            const T w = (T)sw[op >> 51];
+            if (ADJ) {
+                if (fl & 1u) {
+                    acc = adj[k];
+                    acct = adt[k];
+                }
+                acc += w * val[i] * adj[j];
+                acct += w * (tan[i] * adj[j] + val[i] * adt[j]);
+                if (fl & 2u) {
+                    adj[k] = acc;
+                    adt[k] = acct;
+                }
+            } else {
+                if (fl & 1u) {
+                    acc = T(0);
+                    acct = T(0);
+                }
+                acc += w * val[i] * val[j];
+                acct += w * (tan[i] * val[j] + val[i] * tan[j]);
+                if (fl & 2u) {
+                    val[k] = acc;
+                    tan[k] = acct;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_contract_tan(const EvalCtx<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int V = G::V_, C = G::C_, M = G::M_;
+    constexpr int MB = (M + 31) / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    T* seed = reinterpret_cast<T*>(smem_raw);
+    float* sw = reinterpret_cast<float*>(seed + V);
+    T* val = reinterpret_cast<T*>(sw + ((a.n_weights + 3) & ~3)) + (size_t)warp * 4 * V;
+    T* tan = val + V;
+    T* adj = tan + V;
+    T* adt = adj + V;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) seed[v] = a.seed[v];
+    for (int v = threadIdx.x; v < a.n_weights; v += blockDim.x) sw[v] = a.weights[v];
+    __syncthreads();
+    double dx[MB];
+#pragma unroll
+    for (int t = 0; t < MB; ++t) dx[t] = 0.0;
+    for (int i = blockIdx.x * wpb + warp; i < a.n_atoms; i += gridDim.x * wpb) {
+        const size_t tb = (size_t)(i >> 5) * C * 32 + (i & 31);
+        for (int c = lane; c < C; c += 32) {
+            val[c] = a.mom[tb + (size_t)c * 32];
+            tan[c] = a.momt[tb + (size_t)c * 32];
+        }
+        __syncwarp();
+        run_program_dual<T, false>(a.fwd_ops, a.fwd_layer_end, a.fwd_layers, sw, val, tan, adj, adt, lane);
+        const double ek = a.gew[a.cfg_of[i]];
+#pragma unroll
+        for (int t = 0; t < MB; ++t) {
+            const int al = lane + 32 * t;
+            if (al < M) {
+                const int v = a.basis_value[al];
+                dx[t] += ek * (double)val[v] - (double)tan[v];
+            }
+        }
+        for (int v = lane; v < V; v += 32) {
+            adj[v] = seed[v];
+            adt[v] = T(0);
+        }
+        __syncwarp();
+        run_program_dual<T, true>(a.adj_ops, a.adj_layer_end, a.adj_layers, sw, val, tan, adj, adt, lane);
+        for (int c = lane; c < C; c += 32) {
+            a.adjm[tb + (size_t)c * 32] = adj[c];
+            a.adjmt[tb + (size_t)c * 32] = adt[c];
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int t = 0; t < MB; ++t)
+        if (lane + 32 * t < M) atomicAdd(&a.dxi[lane + 32 * t], dx[t]);
+}
+
+template <class T, int S, int NS>
+__device__ __forceinline__ void pdot_all(const T* adjp, const T* adjtp, T x, T y, T z, T ux, T uy, T uz, T* P,
+                                         T* Pd) {
+    if constexpr (S < NS) {
+        using SL = typename SliceSel<T, S>::type;
+        SL::template pdot<T>(x, y, z, adjp + (size_t)SL::BEGIN * 32, adjtp + (size_t)SL::BEGIN * 32, ux, uy, uz, P,
+                             Pd);
+        pdot_all<T, S + 1, NS>(adjp, adjtp, x, y, z, ux, uy, uz, P, Pd);
+    }
+}
+
+// dL/dc: thread group per atom, one pass per neighbour species (register accumulators), then
+// shared-memory and global double atomics
+template <class T, int TPA>
+__global__ void __launch_bounds__(128) k_dc(const EvalCtx<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NMU = G::NMU_;
+    const int nc = a.S * a.S * NMU * a.NQ;
+    double* dcs = reinterpret_cast<double*>(smem_raw);
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) dcs[k] = 0.0;
+    __syncthreads();
+    const size_t n = (size_t)a.n_atoms;
+    const int NQ = a.NQ;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_atoms * TPA; g += gridDim.x * blockDim.x) {
+        const int i = g / TPA, sub = g % TPA;
+        const int zi = clamp_species(a.types[i], a.S);
+        const int cnt = a.count[i];
+        const int k = a.cfg_of[i];
+        const T ek = (T)a.gew[k];
+        T Di[3], E[9];
+        for (int q = 0; q < 3; ++q) Di[q] = a.gD[3 * (size_t)i + q];
+        for (int q = 0; q < 9; ++q) E[q] = a.geps[9 * (size_t)k + q];
+        const size_t tb = (size_t)(i >> 5) * G::C_ * 32 + (i & 31);
+        for (int zp = 0; zp < a.S; ++zp) {
+            T acc[NMU][kMaxRadial];
+#pragma unroll
+            for (int mu = 0; mu < NMU; ++mu)
+#pragma unroll
+                for (int b = 0; b < kMaxRadial; ++b) acc[mu][b] = T(0);
+            bool any = false;
+            for (int p = sub; p < cnt; p += TPA) {
+                const size_t idx = (size_t)p * n + i;
+                const int jz = a.jz[idx];
+                if ((jz >> 24) != zp) continue;
+                any = true;
+                const int j = jz & 0xffffff;
+                const T x = a.rx[idx], y = a.ry[idx], z = a.rz[idx];
+                const T r = my_sqrt(x * x + y * y + z * z);
+                T ux, uy, uz;
+                pair_u(a, Di, E, j, x, y, z, ux, uy, uz);
+                const T rdu = (x * ux + y * uy + z * uz) / r;
+                T P[NMU], Pd[NMU];
+#pragma unroll
+                for (int mu = 0; mu < NMU; ++mu) P[mu] = Pd[mu] = T(0);
+                pdot_all<T, 0, NumSlices<T>::value>(a.adjm + tb, a.adjmt + tb, x, y, z, ux, uy, uz, P, Pd);
+                // Q_b = T_b(x) u^2 and dQ_b/dr (Eq. 4)
+                const T xx = (T(2) * r - a.rmin - a.rcut) * a.inv_span;
+                const T uu = a.rcut - r;
+                T t0 = T(1), t1 = xx, d0 = T(0), d1 = T(1);
+#pragma unroll
+                for (int b = 0; b < kMaxRadial; ++b) {
+                    if (b >= NQ) break;
+                    T tb_, db_;
+                    if (b == 0) {
+                        tb_ = t0;
+                        db_ = d0;
+                    } else if (b == 1) {
+                        tb_ = t1;
+                        db_ = d1;
+                    } else {
+                        const T t2 = T(2) * xx * t1 - t0, d2 = T(2) * t1 + T(2) * xx * d1 - d0;
+                        t0 = t1;
+                        t1 = t2;
+                        d0 = d1;
+                        d1 = d2;
+                        tb_ = t2;
+                        db_ = d2;
+                    }
+                    const T Q = tb_ * uu * uu;
+                    const T dQ = db_ * (T(2) * a.inv_span) * uu * uu - T(2) * tb_ * uu;
+#pragma unroll
+                    for (int mu = 0; mu < NMU; ++mu) acc[mu][b] += ek * Q * P[mu] - dQ * rdu * P[mu] - Q * Pd[mu];
+                }
+            }
+            if (any) {
+                double* dst = dcs + (size_t)((zi * a.S + zp) * NMU) * NQ;
+#pragma unroll
+                for (int mu = 0; mu < NMU; ++mu)
+                    for (int b = 0; b < NQ; ++b) atomicAdd(&dst[mu * NQ + b], (double)acc[mu][b]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc; q += blockDim.x)
+        if (dcs[q] != 0.0) atomicAdd(&a.dc[q], dcs[q]);
+}
+
+template <class T, int TPA>
+int launch_grad_pairs(EvalCtx<T>& a, cudaStream_t st, int n_sm) {
+    const int threads = 128;
+    const long work = (long)(((a.n_atoms + 31) / 32) * 32) * TPA;
+    int blocks = (int)((work + threads - 1) / threads);
+    if (blocks > n_sm * 16) blocks = n_sm * 16;
+    if (blocks < 1) blocks = 1;
+    const size_t cbytes = sizeof(T) * (size_t)a.S * a.S * G::NMU_ * a.NQ;
+    k_tmom<T, TPA><<<blocks, threads, cbytes, st>>>(a);
+    return 1;
+}
+
+template <class T>
+int grad_all(EvalCtx<T>& a, const LossArgs& L, cudaStream_t st, int n_sm) {
+    int launches = 0;
+    T* D = const_cast<T*>(a.gD);
+    T* eps = const_cast<T*>(a.geps);
+    k_resid_atoms<T><<<min((a.n_atoms + 127) / 128 + 1, n_sm * 8), 128, 0, st>>>(a, L, D);
+    k_resid_cfgs<T><<<min((a.n_cfg + 127) / 128 + 1, n_sm * 8), 128, 0, st>>>(L, eps);
+    launches += 2;
+    if (a.n_atoms == 0) return launches;
+    switch (a.tpa) {
+        case 8: launches += launch_grad_pairs<T, 8>(a, st, n_sm); break;
+        case 4: launches += launch_grad_pairs<T, 4>(a, st, n_sm); break;
+        case 2: launches += launch_grad_pairs<T, 2>(a, st, n_sm); break;
+        default: launches += launch_grad_pairs<T, 1>(a, st, n_sm); break;
+    }
+    {
+        const int threads = 128, wpb = 4;
+        const size_t smem = sizeof(T) * (size_t)G::V_ * (1 + 4 * wpb) + sizeof(float) * (a.n_weights + 4) + 64;
+        if (smem > 200 * 1024) return -1000;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_contract_tan<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr_set = true;
+        }
+        int per_sm = (int)((220 * 1024) / (smem + 1024));
+        if (per_sm < 1) per_sm = 1;
+        int blocks = (a.n_atoms + wpb - 1) / wpb;
+        if (blocks > n_sm * per_sm) blocks = n_sm * per_sm;
+        k_contract_tan<T><<<blocks, threads, smem, st>>>(a);
+        ++launches;
+    }
+    {
+        const int threads = 128;
+        const size_t smem = sizeof(double) * (size_t)a.S * a.S * G::NMU_ * a.NQ;
+        int blocks = (a.n_atoms + threads - 1) / threads;
+        if (blocks > n_sm * 8) blocks = n_sm * 8;
+        k_dc<T, 1><<<blocks, threads, smem, st>>>(a);
+        ++launches;
+    }
+    return launches;
+}
+
+int grad_f32(EvalCtx<float>& a, const LossArgs& L, cudaStream_t st, int n_sm) { return grad_all<float>(a, L, st, n_sm); }
+int grad_f64(EvalCtx<double>& a, const LossArgs& L, cudaStream_t st, int n_sm) { return grad_all<double>(a, L, st, n_sm); }
+
 }  // namespace MTP_GEN_NS
 
 const LevelOps* MTP_LEVEL_FN() {
@@ -637,7 +1030,7 @@ const LevelOps* MTP_LEVEL_FN() {
         g::fwd_ops, g::fwd_layer_rows, g::FWD_ROWS, g::FWD_LAYERS,
         g::adj_ops, g::adj_layer_rows, g::ADJ_ROWS, g::ADJ_LAYERS, g::weights, g::NWEIGHTS,
         g::PROGRAM_OPS, g::FLOP_PAIR_MOMENTS, g::FLOP_PAIR_ADJOINT, g::FLOP_ATOM_PROGRAM,
-        &MTP_GEN_NS::eval_f32, &MTP_GEN_NS::eval_f64};
+        &MTP_GEN_NS::eval_f32, &MTP_GEN_NS::eval_f64, &MTP_GEN_NS::grad_f32, &MTP_GEN_NS::grad_f64};
     return &ops;
 }
 

@@ -67,6 +67,7 @@ _SIGS = {
     "mtp_set_active_set": (_I, [_P, _P]),
     "mtp_get_active_set": (_I, [_P, _P, _P, _P]),
     "mtp_grade": (_I, [_P, _I, _P, _P, _I, _P]),
+    "mtp_param_grad": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, _D, _D, _D, _I, _P, _P, _P, _I, _P]),
     "mtp_select_active_set_noalloc": (_I, [_I, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
     "mtp_profile_read": (_I, [_P, _P, _I, ctypes.POINTER(_L)]),
 }
@@ -164,6 +165,14 @@ def mtp_neighbors(h, n_cfg, n_atoms, cfg_off, pos, cells, skin, counts, nbr_j=No
     _check(code, "mtp_neighbors")
 
 
+def mtp_param_grad(h, n_cfg, n_atoms, cfg_off, pos, types, cells, e_ref, f_ref, w_ref, w_e, w_f, w_s, scaling,
+                   loss=None, d_xi=None, d_c=None, flags=0, stream=None):
+    s = None if flags & HOST_MEMORY else _stream(stream)
+    _check(load().mtp_param_grad(h, int(n_cfg), int(n_atoms), _ptr(cfg_off), _ptr(pos), _ptr(types), _ptr(cells),
+                                 _ptr(e_ref), _ptr(f_ref), _ptr(w_ref), float(w_e), float(w_f), float(w_s),
+                                 int(scaling), _ptr(loss), _ptr(d_xi), _ptr(d_c), int(flags), s), "mtp_param_grad")
+
+
 def mtp_sync(h, stream=None):
     _check(load().mtp_sync(h, _stream(stream)), "mtp_sync")
 
@@ -226,6 +235,8 @@ class Model:
     def __init__(self, lev_max, n_species, n_radial, r_min, r_cut, xi=None, c=None, precision="fp64"):
         prec = {"fp64": FP64, "fp32": FP32}[precision] if isinstance(precision, str) else int(precision)
         self.precision = prec
+        self.n_species = int(n_species)
+        self.n_radial = int(n_radial)
         self.h = mtp_create(lev_max, n_species, n_radial, r_min, r_cut, xi, c, prec)
         lib = load()
         self.m = lib.mtp_basis_count(self.h)
@@ -289,6 +300,21 @@ class Model:
                        out.get("site"), out.get("b_rows"), out.get("b_atoms"), out.get("grade_cfg"),
                        out.get("grade_atom"), flags, stream)
         return out
+
+    def param_grad(self, pos, types, cells, cfg_off, e_ref, f_ref, w_ref, weights=(1.0, 0.01, 0.001),
+                   scaling="vibrations"):
+        """Loss and gradient (Sec. 2.2) for device tensors; returns (loss, d_xi [m], d_c [S,S,N_mu,N_Q])."""
+        import torch
+
+        kind = {"molecules": 0, "structures": 1, "vibrations": 2}[scaling] if isinstance(scaling, str) else scaling
+        dev = pos.device
+        loss = torch.empty(1, dtype=torch.float64, device=dev)
+        dxi = torch.empty(self.m, dtype=torch.float64, device=dev)
+        S = self.n_species
+        dc = torch.empty((S, S, self.n_mu, self.n_radial), dtype=torch.float64, device=dev)
+        mtp_param_grad(self.h, cells.shape[0], pos.shape[0], cfg_off, pos, types, cells, e_ref, f_ref, w_ref,
+                       weights[0], weights[1], weights[2], kind, loss, dxi, dc)
+        return loss, dxi, dc
 
     def select_active_set(self, b_rows):
         """MaxVol over the rows of b_rows (device float64 [n, m]); returns (rows, swaps, max |C|)."""

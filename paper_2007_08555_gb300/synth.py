@@ -118,6 +118,41 @@ def random_params(lev_max, n_species, n_radial, r_min, r_cut, m, seed, xi_std=1e
     return Params(lev_max, n_species, n_radial, r_min, r_cut, xi, c)
 
 
+def labels_from_level_table(table):
+    """Moment labels [(mu, nu), ...] of every basis function, read from a canonical level table
+    (format of mtp_level_table: [m, then per function: level, n_components, then per component:
+    n, mu_0, nu_0, ..., then the upper triangle of its adjacency])."""
+    t = list(table)
+    m = t[0]
+    pos = 1
+    out = []
+    for _ in range(m):
+        pos += 1  # level
+        ncomp = t[pos]
+        pos += 1
+        labs = []
+        for _ in range(ncomp):
+            n = t[pos]
+            for u in range(n):
+                labs.append((t[pos + 1 + 2 * u], t[pos + 2 + 2 * u]))
+            pos += 1 + 2 * n + n * (n - 1) // 2
+        out.append(labs)
+    return out
+
+
+def scaled_params(lev_max, n_species, n_radial, r_min, r_cut, labels, seed, xi_std=1e-2, c_std=0.1,
+                  n_bar=40.0, f_bar=0.5, r_bar=2.6):
+    """Random parameters whose terms xi_alpha B_alpha are of order xi_std at neighbourhoods like the
+    workloads' (about n_bar neighbours at distance r_bar, radial functions of size f_bar): each
+    basis function's coefficient is divided by prod over its moments of n_bar f_bar r_bar^nu.
+    Used for the lev_max-20 workloads, where the plain recipe gives energies of 1e25 eV."""
+    rng = np.random.default_rng(seed)
+    scale = np.array([np.prod([n_bar * f_bar * r_bar ** nu for _, nu in labs]) for labs in labels])
+    xi = rng.normal(0.0, xi_std, size=len(labels)) / scale
+    c = rng.normal(0.0, c_std, size=(n_species, n_species, n_mu(lev_max), n_radial))
+    return Params(lev_max, n_species, n_radial, r_min, r_cut, xi, c)
+
+
 def perturbed(kind, reps, sigma, rng, n_species=1, species_frac=None):
     base = LATTICES[kind]() if isinstance(kind, str) else kind
     pos, cell = supercell(base, reps)

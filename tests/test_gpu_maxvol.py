@@ -68,12 +68,15 @@ def test_active_set_from_configurations(gpu_lib, L):
     assert sel.cpu().numpy().tolist() == sel_o.tolist()
     # grades of every configuration, from mtp_grade and from the evaluation itself
     g_ref = maxvol.grades(B_o, B_o[sel_o])
+    # grades carry the conditioning of the active-set matrix: forward error ~ cond(A D) * eps
+    A_s, _ = maxvol.equilibrate(B_o[sel_o])
+    tol = max(1e-8, 1e-12 * np.linalg.cond(A_s))
     g = model.grade(B_gpu).cpu().numpy()
-    np.testing.assert_allclose(g, g_ref, rtol=1e-8)
+    np.testing.assert_allclose(g, g_ref, rtol=tol)
     out2 = model.eval_batch(pos, types, cells, off, grade_cfg=True, grade_atom=True)
-    np.testing.assert_allclose(out2["grade_cfg"].cpu().numpy(), g_ref, rtol=1e-8)
+    np.testing.assert_allclose(out2["grade_cfg"].cpu().numpy(), g_ref, rtol=tol)
     ga_ref = maxvol.grades(np.concatenate(atoms_o), B_o[sel_o])
-    np.testing.assert_allclose(out2["grade_atom"].cpu().numpy(), ga_ref, rtol=1e-8)
+    np.testing.assert_allclose(out2["grade_atom"].cpu().numpy(), ga_ref, rtol=tol, atol=tol * np.abs(ga_ref).max())
 
 
 def test_singular_rows_are_reported(gpu_lib):
