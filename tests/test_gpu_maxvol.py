@@ -70,7 +70,7 @@ def test_active_set_from_configurations(gpu_lib, L):
     g_ref = maxvol.grades(B_o, B_o[sel_o])
     # grades carry the conditioning of the active-set matrix: forward error ~ cond(A D) * eps
     A_s, _ = maxvol.equilibrate(B_o[sel_o])
-    tol = max(1e-8, 1e-12 * np.linalg.cond(A_s))
+    tol = min(1e-3, max(1e-8, 1e-12 * np.linalg.cond(A_s)))  # observed 1.5e-5 at cond 3.6e13
     g = model.grade(B_gpu).cpu().numpy()
     np.testing.assert_allclose(g, g_ref, rtol=tol)
     out2 = model.eval_batch(pos, types, cells, off, grade_cfg=True, grade_atom=True)
