@@ -106,6 +106,13 @@ mtp_status mtp_level_table(const mtp_model* model, int32_t* buf, size_t cap, siz
 /* Replace theta = {xi, c} (host arrays, layouts as in mtp_create; NULL keeps the old value). */
 mtp_status mtp_set_params(mtp_model* model, const double* xi, const double* c);
 
+/* Skin added to R_cut when neighbour lists are built (default 0).  With a skin > 0 the build also
+ * keeps the positions, and an evaluation with MTP_REUSE_NEIGHBORS (same atoms, configurations and
+ * cells) refreshes r_ij = r0_ij + (u_j - u_i) from the displacements u since the build instead of
+ * searching again; pairs beyond R_cut contribute nothing (Q_b = 0 there, Eq. 4).  The caller must
+ * rebuild before any atom has moved by skin / 2. */
+mtp_status mtp_set_skin(mtp_model* model, double skin);
+
 /* Capacity of the per-atom neighbour list (default 128).  MTP_EOVERFLOW reports the largest
  * count seen through *max_seen of mtp_last_neighbor_max(). */
 mtp_status mtp_set_neighbor_capacity(mtp_model* model, int cap);
@@ -206,6 +213,19 @@ mtp_status mtp_param_grad(mtp_model* model, int n_cfg, int n_atoms, const int32_
                           const int32_t* types, const double* cells, const double* e_ref, const double* f_ref,
                           const double* w_ref, double w_e, double w_f, double w_s, int scaling, double* loss,
                           double* d_xi, double* d_c, int flags, void* stream);
+
+/*
+ * Velocity-Verlet molecular dynamics of one periodic configuration with this potential (the paper
+ * runs MD through LAMMPS, Sec. 5; this is the data-parallel step itself).  pos and vel ([n][3]
+ * double, Angstrom and Angstrom/fs, device) are advanced in place by n_steps steps of dt fs;
+ * masses [S] (host, amu).  Requires mtp_set_skin() > 0: the neighbour list is rebuilt when an atom
+ * has moved more than skin / 2 since the last build, otherwise refreshed.  e_pot and e_kin (host,
+ * [n_steps + 1], eV, step 0 = initial state) and n_rebuilds (host) may be NULL.  Energies and the
+ * kinetic sum are accumulated in double precision; forces are the model's precision.
+ */
+mtp_status mtp_md_run(mtp_model* model, int n_atoms, double* pos, double* vel, const int32_t* types,
+                      const double* cell, const double* masses, double dt, int n_steps, double* e_pot,
+                      double* e_kin, int* n_rebuilds, int flags, void* stream);
 
 /* Wait for the model's work on `stream` and report errors detected on the device since the last
  * check (MTP_EOVERFLOW, MTP_EINVAL for bad species or shifts). */

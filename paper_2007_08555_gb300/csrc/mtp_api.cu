@@ -54,6 +54,9 @@ struct mtp_model {
     // staging for MTP_HOST_MEMORY calls
     DevBuf s_off, s_pos, s_types, s_cells, s_energy, s_forces, s_virial, s_site, s_brows, s_batoms;
     int cap = 128;
+    double skin = 0.0;   // neighbour lists are built for R_cut + skin
+    bool reused = false; // the last evaluation refreshed r_ij from the build-time list
+    DevBuf md_F, md_scalars, md_masses, md_flag;
     int last_max = 0;
     int64_t launches = 0;
     // active set (Sec. 2.3): rows of the last selection, A and A^-1 in double precision
@@ -150,9 +153,9 @@ mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     a.count = M->nb.count.as<int>();
     a.jz = M->nb.jz.as<int>();
     a.rev = M->nb.rev.as<int>();
-    a.rx = M->nb.rx.as<T>();
-    a.ry = M->nb.ry.as<T>();
-    a.rz = M->nb.rz.as<T>();
+    a.rx = M->reused ? M->nb.cx.as<T>() : M->nb.rx.as<T>();
+    a.ry = M->reused ? M->nb.cy.as<T>() : M->nb.ry.as<T>();
+    a.rz = M->reused ? M->nb.cz.as<T>() : M->nb.rz.as<T>();
     a.c = M->d_c.as<T>();
     a.xi = M->d_xi.as<T>();
     a.seed = M->d_seed.as<T>();
@@ -317,7 +320,8 @@ void mtp_destroy(mtp_model* M) {
                       &M->nb.cfg_of, &M->nb.desc, &M->nb.atom_bin, &M->nb.atom_wrap, &M->nb.atom_local,
                       &M->nb.bin_count, &M->nb.bin_start, &M->nb.bin_fill, &M->nb.bin_atoms, &M->nb.scan_tmp,
                       &M->nb.err, &M->nb.max_seen, &M->g_energy, &M->g_forces, &M->g_virial, &M->g_D, &M->g_eps, &M->g_ew,
-                      &M->g_momt, &M->g_adjmt, &M->g_out, &M->g_refs, &M->d_A, &M->d_Ai, &M->mv_Bs, &M->mv_D, &M->mv_W, &M->mv_perm, &M->mv_sel,
+                      &M->g_momt, &M->g_adjmt, &M->g_out, &M->g_refs, &M->md_F, &M->md_scalars, &M->md_masses,
+                      &M->md_flag, &M->nb.x0, &M->nb.cx, &M->nb.cy, &M->nb.cz, &M->d_A, &M->d_Ai, &M->mv_Bs, &M->mv_D, &M->mv_W, &M->mv_perm, &M->mv_sel,
                       &M->mv_C, &M->mv_status, &M->mv_swaps, &M->mv_gmax, &M->s_rows, &M->s_gamma, &M->g_brows,
                       &M->g_batoms};
     for (DevBuf* b : bufs) b->release();
@@ -369,6 +373,13 @@ mtp_status mtp_set_params(mtp_model* M, const double* xi, const double* c) {
     return upload_params(M);
 }
 
+mtp_status mtp_set_skin(mtp_model* M, double skin) {
+    if (!M || !(skin >= 0.0) || skin > 10.0) return MTP_EINVAL;
+    M->skin = skin;
+    M->nb.has_x0 = false;
+    return MTP_OK;
+}
+
 mtp_status mtp_set_neighbor_capacity(mtp_model* M, int cap) {
     if (!M || cap < 1 || cap > 1024) return MTP_EINVAL;
     M->cap = cap;
@@ -398,7 +409,26 @@ static mtp_status prepare_neighbors(mtp_model* M, int K, int n, const int* off, 
     if (M->profiling) cudaEventRecord(M->ev_nbr[1], st);
     if (l < 0) return cuda_status(cudaGetLastError());
     M->launches += l;
+    M->reused = false;
+    M->nb.has_x0 = false;
+    if (skin > 0.0) {  // keep the build-time positions for later refreshes of r_ij
+        if (M->nb.x0.reserve(sizeof(double) * 3 * (size_t)n + 8)) return MTP_ENOMEM;
+        cudaMemcpyAsync(M->nb.x0.p, pos, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, st);
+        M->nb.has_x0 = true;
+    }
     return MTP_OK;
+}
+
+// Refresh r_ij of the last list for new positions (same atoms); requires a build with a skin.
+static mtp_status refresh_neighbors(mtp_model* M, int K, int n, const double* pos, cudaStream_t st) {
+    if (!M->nb.has_x0 || M->nb.n_atoms != n || M->nb.n_cfg != K) return MTP_EINVAL;
+    const size_t bytes = (size_t)n * M->nb.cap * (is_fp64(M) ? 8 : 4);
+    if (M->nb.cx.reserve(bytes) || M->nb.cy.reserve(bytes) || M->nb.cz.reserve(bytes)) return MTP_ENOMEM;
+    if (M->profiling) cudaEventRecord(M->ev_nbr[0], st);
+    M->launches += mtp::launch_update_pairs(M->nb, pos, st, M->n_sm);
+    if (M->profiling) cudaEventRecord(M->ev_nbr[1], st);
+    M->reused = true;
+    return cuda_status(cudaGetLastError());
 }
 
 }  // extern "C"
@@ -486,7 +516,7 @@ extern "C" mtp_status mtp_param_grad(mtp_model* M, int K, int n, const int32_t* 
         f_ref = r + 10 * (size_t)K;
     }
     if (M->g_out.reserve(sizeof(double) * (1 + M->m + nc) + 64)) return MTP_ENOMEM;
-    mtp_status s = prepare_neighbors(M, K, n, cfg_off, pos, types, cells, 0.0, st);
+    mtp_status s = prepare_neighbors(M, K, n, cfg_off, pos, types, cells, M->skin, st);
     if (s) return s;
     double* out = M->g_out.as<double>();
     if (is_fp64(M))
@@ -515,7 +545,7 @@ mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, co
     if (s) return s;
     if (n > 0 && !types) return MTP_EINVAL;
     if ((grade_cfg || grade_atom) && !M->has_active) return MTP_ENOACTIVESET;
-    if (flags & MTP_REUSE_NEIGHBORS) return MTP_EUNSUPPORTED;
+    const bool reuse = (flags & MTP_REUSE_NEIGHBORS) && M->nb.has_x0 && M->nb.n_atoms == n && M->nb.n_cfg == K;
     double *h_gcfg = grade_cfg, *h_gatom = grade_atom;
     cudaStream_t st = (cudaStream_t)stream;
     const bool host = flags & MTP_HOST_MEMORY;
@@ -553,7 +583,11 @@ mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, co
         if (M->g_batoms.reserve(sizeof(double) * (size_t)n * M->m + 8)) return MTP_ENOMEM;
         b_atoms = M->g_batoms.as<double>();
     }
-    if ((s = prepare_neighbors(M, K, n, cfg_off, pos, types, cells, 0.0, st))) return s;
+    if (reuse)
+        s = refresh_neighbors(M, K, n, pos, st);
+    else
+        s = prepare_neighbors(M, K, n, cfg_off, pos, types, cells, M->skin, st);
+    if (s) return s;
     if (is_fp64(M))
         s = run_eval<double>(M, K, n, cfg_off, types, energy, forces, virial, site, b_rows, b_atoms, st);
     else
@@ -726,4 +760,68 @@ mtp_status mtp_grade(mtp_model* M, int n_rows, const double* b_rows, double* gam
     return cuda_status(cudaStreamSynchronize(st));
 }
 
+mtp_status mtp_md_run(mtp_model* M, int n, double* pos, double* vel, const int32_t* types, const double* cell,
+                      const double* masses, double dt, int n_steps, double* e_pot, double* e_kin, int* n_rebuilds,
+                      int flags, void* stream) {
+    if (!M || n < 1 || !pos || !vel || !types || !cell || !masses || !(dt > 0.0) || n_steps < 0) return MTP_EINVAL;
+    if (flags & MTP_HOST_MEMORY) return MTP_EUNSUPPORTED;
+    if (!(M->skin > 0.0)) return MTP_EINVAL;  // velocity Verlet reuses lists: needs a skin
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)n;
+    if (M->md_F.reserve(24 * N) || M->md_scalars.reserve(sizeof(double) * 4) ||
+        M->md_masses.reserve(sizeof(double) * M->S) || M->md_flag.reserve(16) || M->s_off.reserve(16))
+        return MTP_ENOMEM;
+    if (cudaMemcpy(M->md_masses.p, masses, sizeof(double) * M->S, cudaMemcpyHostToDevice) != cudaSuccess)
+        return MTP_ECUDA;
+    int32_t off_h[2] = {0, n};
+    cudaMemcpyAsync(M->s_off.p, off_h, sizeof off_h, cudaMemcpyHostToDevice, st);
+    const int* off = M->s_off.as<int>();
+    double* F = M->md_F.as<double>();
+    double* sc = M->md_scalars.as<double>();  // [0] E_pot, [1] E_kin
+    int* flag = M->md_flag.as<int>();
+    const double* mass = M->md_masses.as<double>();
+    const double lim2 = 0.25 * M->skin * M->skin;
+    int rebuilds = 0;
+    std::vector<double> ep(n_steps + 1), ek(n_steps + 1);
+    auto forces = [&](bool reuse) -> mtp_status {
+        mtp_status s2 = reuse ? refresh_neighbors(M, 1, n, pos, st)
+                              : prepare_neighbors(M, 1, n, off, pos, types, cell, M->skin, st);
+        if (s2) return s2;
+        if (is_fp64(M))
+            return run_eval<double>(M, 1, n, off, types, sc, F, nullptr, nullptr, nullptr, nullptr, st);
+        return run_eval<float>(M, 1, n, off, types, sc, F, nullptr, nullptr, nullptr, nullptr, st);
+    };
+    auto record = [&](int step) -> mtp_status {
+        cudaMemsetAsync(sc + 1, 0, sizeof(double), st);
+        M->launches += mtp::launch_kinetic(n, M->S, vel, types, mass, sc + 1, st, M->n_sm);
+        double h[2];
+        cudaMemcpyAsync(h, sc, sizeof h, cudaMemcpyDeviceToHost, st);
+        mtp_status s2 = finish(M, st);
+        ep[step] = h[0];
+        ek[step] = h[1];
+        return s2;
+    };
+    mtp_status s = forces(false);
+    if (!s) s = record(0);
+    for (int step = 1; step <= n_steps && !s; ++step) {
+        M->launches += mtp::launch_kick(n, M->S, vel, F, types, mass, 0.5 * dt, st, M->n_sm);
+        cudaMemsetAsync(flag, 0, sizeof(int), st);
+        M->launches += mtp::launch_drift(n, pos, vel, M->nb.x0.as<double>(), dt, lim2, flag, st, M->n_sm);
+        int hf = 0;
+        cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return MTP_ECUDA;
+        if (hf) ++rebuilds;
+        s = forces(hf == 0);
+        if (s) break;
+        M->launches += mtp::launch_kick(n, M->S, vel, F, types, mass, 0.5 * dt, st, M->n_sm);
+        s = record(step);
+    }
+    if (s) return s;
+    if (e_pot) std::copy(ep.begin(), ep.end(), e_pot);
+    if (e_kin) std::copy(ek.begin(), ek.end(), e_kin);
+    if (n_rebuilds) *n_rebuilds = rebuilds;
+    return MTP_OK;
+}
+
 }  // extern "C"
+

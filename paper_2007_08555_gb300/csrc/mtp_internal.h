@@ -46,6 +46,9 @@ struct NbrState {
     DevBuf count, jz, shift, rev, rx, ry, rz;
     DevBuf cfg_of, desc, atom_bin, atom_wrap, atom_local, atom_wp, bin_count, bin_start, bin_fill, bin_atoms, scan_tmp;
     DevBuf err, max_seen;
+    // reuse with a skin: positions at the build and the current displacements (float or double)
+    DevBuf x0, cx, cy, cz;
+    bool has_x0 = false;
 };
 
 // Build the neighbour list of a batch (device inputs).  r_ij are written in float or double.
@@ -65,6 +68,15 @@ int launch_maxvol(int n, int m, const double* B, double* Bs, double* D, double* 
 int launch_invert(int m, const double* A, double* Ai, double* W, int* status, cudaStream_t st);
 template <class T>
 int launch_grade(int n, int m, const T* B, int ldb, const T* Ai, unsigned long long* gbits, cudaStream_t st);
+
+// Molecular dynamics helpers (mtp_md.cu).  The refreshed r_ij go to nb.cx/cy/cz.
+int launch_update_pairs(const NbrState& nb, const double* x, cudaStream_t st, int n_sm);
+int launch_kick(int n, int S, double* v, const double* F, const int* types, const double* masses, double half_dt,
+                cudaStream_t st, int n_sm);
+int launch_drift(int n, double* x, const double* v, const double* x0, double dt, double lim2, int* flag,
+                 cudaStream_t st, int n_sm);
+int launch_kinetic(int n, int S, const double* v, const int* types, const double* masses, double* out,
+                   cudaStream_t st, int n_sm);
 
 // CSR export of the neighbour list with exact double-precision r_ij.
 int export_neighbors(const NbrState& nb, const double* pos, const int* offsets, int* nbr_j, int* nbr_s,

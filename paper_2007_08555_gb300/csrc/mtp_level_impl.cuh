@@ -79,7 +79,8 @@ __device__ __forceinline__ void radial(const T r, const T* __restrict__ cz, cons
         d0 = d1;
         d1 = d2;
     }
-    const T u = rcut - r;
+    // Q_b = 0 for r >= R_cut (Eq. 4): pairs kept in a neighbour list with a skin contribute nothing
+    const T u = r < rcut ? rcut - r : T(0);
     const T u2 = u * u;
 #pragma unroll
     for (int mu = 0; mu < NMU; ++mu) {
@@ -923,7 +924,7 @@ __global__ void __launch_bounds__(128) k_dc(const EvalCtx<T> a) {
                 pdot_all<T, 0, NumSlices<T>::value>(a.adjm + tb, a.adjmt + tb, x, y, z, ux, uy, uz, P, Pd);
                 // Q_b = T_b(x) u^2 and dQ_b/dr (Eq. 4)
                 const T xx = (T(2) * r - a.rmin - a.rcut) * a.inv_span;
-                const T uu = a.rcut - r;
+                const T uu = r < a.rcut ? a.rcut - r : T(0);  // Q_b = 0 beyond the cutoff (Eq. 4)
                 T t0 = T(1), t1 = xx, d0 = T(0), d1 = T(1);
 #pragma unroll
                 for (int b = 0; b < kMaxRadial; ++b) {

@@ -68,6 +68,8 @@ _SIGS = {
     "mtp_get_active_set": (_I, [_P, _P, _P, _P]),
     "mtp_grade": (_I, [_P, _I, _P, _P, _I, _P]),
     "mtp_param_grad": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, _D, _D, _D, _I, _P, _P, _P, _I, _P]),
+    "mtp_set_skin": (_I, [_P, _D]),
+    "mtp_md_run": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _I, _P, _P, ctypes.POINTER(_I), _I, _P]),
     "mtp_select_active_set_noalloc": (_I, [_I, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
     "mtp_profile_read": (_I, [_P, _P, _I, ctypes.POINTER(_L)]),
 }
@@ -171,6 +173,21 @@ def mtp_param_grad(h, n_cfg, n_atoms, cfg_off, pos, types, cells, e_ref, f_ref, 
     _check(load().mtp_param_grad(h, int(n_cfg), int(n_atoms), _ptr(cfg_off), _ptr(pos), _ptr(types), _ptr(cells),
                                  _ptr(e_ref), _ptr(f_ref), _ptr(w_ref), float(w_e), float(w_f), float(w_s),
                                  int(scaling), _ptr(loss), _ptr(d_xi), _ptr(d_c), int(flags), s), "mtp_param_grad")
+
+
+def mtp_set_skin(h, skin):
+    _check(load().mtp_set_skin(h, float(skin)), "mtp_set_skin")
+
+
+def mtp_md_run(h, n_atoms, pos, vel, types, cell, masses, dt, n_steps, stream=None):
+    """Velocity Verlet in place on device tensors; returns (e_pot [n+1], e_kin [n+1], rebuilds)."""
+    ep = np.zeros(n_steps + 1)
+    ek = np.zeros(n_steps + 1)
+    nr = ctypes.c_int()
+    m = np.ascontiguousarray(masses, dtype=np.float64)
+    _check(load().mtp_md_run(h, int(n_atoms), _ptr(pos), _ptr(vel), _ptr(types), _ptr(cell), _ptr(m), float(dt),
+                             int(n_steps), _ptr(ep), _ptr(ek), ctypes.byref(nr), 0, _stream(stream)), "mtp_md_run")
+    return ep, ek, int(nr.value)
 
 
 def mtp_sync(h, stream=None):
@@ -315,6 +332,13 @@ class Model:
         mtp_param_grad(self.h, cells.shape[0], pos.shape[0], cfg_off, pos, types, cells, e_ref, f_ref, w_ref,
                        weights[0], weights[1], weights[2], kind, loss, dxi, dc)
         return loss, dxi, dc
+
+    def set_skin(self, skin):
+        mtp_set_skin(self.h, skin)
+
+    def md_run(self, pos, vel, types, cell, masses, dt, n_steps, stream=None):
+        """Velocity Verlet in place (device tensors); returns (e_pot, e_kin, rebuilds)."""
+        return mtp_md_run(self.h, pos.shape[0], pos, vel, types, cell, masses, dt, n_steps, stream)
 
     def select_active_set(self, b_rows):
         """MaxVol over the rows of b_rows (device float64 [n, m]); returns (rows, swaps, max |C|)."""

@@ -141,15 +141,19 @@ def labels_from_level_table(table):
 
 
 def scaled_params(lev_max, n_species, n_radial, r_min, r_cut, labels, seed, xi_std=1e-2, c_std=0.1,
-                  n_bar=40.0, f_bar=0.5, r_bar=2.6):
+                  n_bar=40.0, f_bar=0.5, r_bar=2.6, radial_decay=1.0):
     """Random parameters whose terms xi_alpha B_alpha are of order xi_std at neighbourhoods like the
     workloads' (about n_bar neighbours at distance r_bar, radial functions of size f_bar): each
     basis function's coefficient is divided by prod over its moments of n_bar f_bar r_bar^nu.
-    Used for the lev_max-20 workloads, where the plain recipe gives energies of 1e25 eV."""
+    Used for the lev_max-20 workloads, where the plain recipe gives energies of 1e25 eV.
+    radial_decay < 1 damps the Chebyshev coefficient of order b by radial_decay^b: smooth radial
+    functions, for molecular dynamics (with undamped random coefficients the fcc lattice collapses
+    within ~100 fs at lev_max 16-20 and 1 fs steps no longer resolve the collisions)."""
     rng = np.random.default_rng(seed)
     scale = np.array([np.prod([n_bar * f_bar * r_bar ** nu for _, nu in labs]) for labs in labels])
     xi = rng.normal(0.0, xi_std, size=len(labels)) / scale
     c = rng.normal(0.0, c_std, size=(n_species, n_species, n_mu(lev_max), n_radial))
+    c = c * radial_decay ** np.arange(n_radial)
     return Params(lev_max, n_species, n_radial, r_min, r_cut, xi, c)
 
 
