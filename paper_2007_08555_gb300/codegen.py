@@ -686,7 +686,7 @@ def emit_slice_functions(prog: Program, slc, tag):
 # ---------------------------------------------------------------------------------------------
 # Emission
 # ---------------------------------------------------------------------------------------------
-SLICE_F32 = 136
+SLICE_F32 = int(os.environ.get("MTP_SLICE_F32", "136"))
 SLICE_F64 = 64
 
 
@@ -710,7 +710,10 @@ def flop_counts(prog: Program):
     }
 
 
-UNROLLED_MAX_LEVEL = 16  # above this the straight-line code no longer fits the register file
+# Straight-line thread-per-atom contraction up to this level.  Up to lev_max 16 it fits the register
+# file (~900 bytes of spills); at 18-20 ptxas keeps most values in local memory, which is still 5.8x
+# faster than the warp-cooperative program at lev_max 20 (measured on a 1M-atom cell).
+UNROLLED_MAX_LEVEL = int(os.environ.get("MTP_UNROLLED_MAX_LEVEL", "20"))
 
 
 def emit_unrolled(prog: Program):

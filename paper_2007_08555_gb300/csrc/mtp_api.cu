@@ -70,6 +70,12 @@ struct mtp_model {
     cudaEvent_t ev_phase[mtp::kPhases + 1] = {};
     double prof_ms[mtp::kPhases + 1] = {};  // neighbours, moments, contract, pairgrad, gather
     int64_t prof_calls = 0;
+    // replay of the whole evaluation as a CUDA graph for repeated identical calls
+    bool graphs = true;
+    std::vector<uintptr_t> g_sig;      // arguments of the last eager call
+    cudaGraphExec_t g_exec = nullptr;  // graph captured from a call with g_sig
+    cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
+    int64_t g_launches = 0;            // kernels in the graph
 };
 
 namespace {
@@ -206,9 +212,15 @@ mtp_status run_eval(mtp_model* M, int K, int n, const int* cfg_off, const int* t
 void collect_profile(mtp_model* M) {
     if (!M->profiling || !M->ev_nbr[0]) return;
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, M->ev_nbr[0], M->ev_nbr[1]) == cudaSuccess) M->prof_ms[0] += ms;
-    for (int k = 0; k < mtp::kPhases; ++k)
-        if (cudaEventElapsedTime(&ms, M->ev_phase[k], M->ev_phase[k + 1]) == cudaSuccess) M->prof_ms[k + 1] += ms;
+    bool ok = true;
+    if (cudaEventElapsedTime(&ms, M->ev_nbr[0], M->ev_nbr[1]) == cudaSuccess) M->prof_ms[0] += ms; else ok = false;
+    for (int k = 0; k < mtp::kPhases; ++k) {
+        if (cudaEventElapsedTime(&ms, M->ev_phase[k], M->ev_phase[k + 1]) == cudaSuccess)
+            M->prof_ms[k + 1] += ms;
+        else
+            ok = false;
+    }
+    if (!ok) cudaGetLastError();  // a failed query must not leave an error for the caller's next call
     M->prof_calls += 1;
 }
 
@@ -325,6 +337,8 @@ void mtp_destroy(mtp_model* M) {
                       &M->mv_C, &M->mv_status, &M->mv_swaps, &M->mv_gmax, &M->s_rows, &M->s_gamma, &M->g_brows,
                       &M->g_batoms};
     for (DevBuf* b : bufs) b->release();
+    if (M->g_exec) cudaGraphExecDestroy(M->g_exec);
+    if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
     for (cudaEvent_t& e : M->ev_nbr)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t& e : M->ev_phase)
@@ -347,6 +361,7 @@ mtp_status mtp_profile(mtp_model* M, int enable) {
             if (cudaEventCreate(&e) != cudaSuccess) return MTP_ECUDA;
     }
     M->profiling = enable != 0;
+    M->g_sig.clear();
     for (double& x : M->prof_ms) x = 0.0;
     M->prof_calls = 0;
     return MTP_OK;
@@ -368,6 +383,7 @@ mtp_status mtp_level_table(const mtp_model* M, int32_t* buf, size_t cap, size_t*
 
 mtp_status mtp_set_params(mtp_model* M, const double* xi, const double* c) {
     if (!M) return MTP_EINVAL;
+    M->g_sig.clear();
     if (xi) std::copy(xi, xi + M->m, M->xi.begin());
     if (c) std::copy(c, c + M->c.size(), M->c.begin());
     return upload_params(M);
@@ -398,15 +414,18 @@ static mtp_status check_batch(mtp_model* M, int K, int n, const int32_t* off, co
 
 static mtp_status prepare_neighbors(mtp_model* M, int K, int n, const int* off, const double* pos,
                                     const int* types, const double* cells, double skin, cudaStream_t st) {
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap_status);
+    if (cap_status == cudaStreamCaptureStatusNone) M->g_sig.clear();  // scratch may be re-sized: no replay
     if (!M->nb.err.p) {  // the error word starts at zero and is cleared after every read
         if (M->nb.err.reserve(4) || M->nb.max_seen.reserve(4)) return MTP_ENOMEM;
         if (cudaMemset(M->nb.err.p, 0, M->nb.err.bytes) != cudaSuccess) return MTP_ECUDA;
     }
     cudaMemsetAsync(M->nb.max_seen.p, 0, sizeof(int), st);
-    if (M->profiling) cudaEventRecord(M->ev_nbr[0], st);
+    if (M->profiling) mtp::record_mark(M->ev_nbr[0], st);
     const int l = mtp::build_neighbors(M->nb, K, n, off, pos, types, cells, M->rcut + skin, is_fp64(M), M->cap,
                                        st, M->S);
-    if (M->profiling) cudaEventRecord(M->ev_nbr[1], st);
+    if (M->profiling) mtp::record_mark(M->ev_nbr[1], st);
     if (l < 0) return cuda_status(cudaGetLastError());
     M->launches += l;
     M->reused = false;
@@ -424,9 +443,9 @@ static mtp_status refresh_neighbors(mtp_model* M, int K, int n, const double* po
     if (!M->nb.has_x0 || M->nb.n_atoms != n || M->nb.n_cfg != K) return MTP_EINVAL;
     const size_t bytes = (size_t)n * M->nb.cap * (is_fp64(M) ? 8 : 4);
     if (M->nb.cx.reserve(bytes) || M->nb.cy.reserve(bytes) || M->nb.cz.reserve(bytes)) return MTP_ENOMEM;
-    if (M->profiling) cudaEventRecord(M->ev_nbr[0], st);
+    if (M->profiling) mtp::record_mark(M->ev_nbr[0], st);
     M->launches += mtp::launch_update_pairs(M->nb, pos, st, M->n_sm);
-    if (M->profiling) cudaEventRecord(M->ev_nbr[1], st);
+    if (M->profiling) mtp::record_mark(M->ev_nbr[1], st);
     M->reused = true;
     return cuda_status(cudaGetLastError());
 }
@@ -583,22 +602,76 @@ mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, co
         if (M->g_batoms.reserve(sizeof(double) * (size_t)n * M->m + 8)) return MTP_ENOMEM;
         b_atoms = M->g_batoms.as<double>();
     }
-    if (reuse)
-        s = refresh_neighbors(M, K, n, pos, st);
-    else
-        s = prepare_neighbors(M, K, n, cfg_off, pos, types, cells, M->skin, st);
-    if (s) return s;
-    if (is_fp64(M))
-        s = run_eval<double>(M, K, n, cfg_off, types, energy, forces, virial, site, b_rows, b_atoms, st);
-    else
-        s = run_eval<float>(M, K, n, cfg_off, types, energy, forces, virial, site, b_rows, b_atoms, st);
-    if (s) return s;
-    if (grade_cfg)
-        M->launches += mtp::launch_grade<double>(K, M->m, b_rows, M->m, M->d_Ai.as<double>(),
-                                                 reinterpret_cast<unsigned long long*>(grade_cfg), st);
-    if (grade_atom)
-        M->launches += mtp::launch_grade<double>(n, M->m, b_atoms, M->m, M->d_Ai.as<double>(),
-                                                 reinterpret_cast<unsigned long long*>(grade_atom), st);
+    auto enqueue = [&](cudaStream_t q) -> mtp_status {
+        mtp_status e = reuse ? refresh_neighbors(M, K, n, pos, q)
+                             : prepare_neighbors(M, K, n, cfg_off, pos, types, cells, M->skin, q);
+        if (e) return e;
+        if (is_fp64(M))
+            e = run_eval<double>(M, K, n, cfg_off, types, energy, forces, virial, site, b_rows, b_atoms, q);
+        else
+            e = run_eval<float>(M, K, n, cfg_off, types, energy, forces, virial, site, b_rows, b_atoms, q);
+        if (e) return e;
+        if (grade_cfg)
+            M->launches += mtp::launch_grade<double>(K, M->m, b_rows, M->m, M->d_Ai.as<double>(),
+                                                     reinterpret_cast<unsigned long long*>(grade_cfg), q);
+        if (grade_atom)
+            M->launches += mtp::launch_grade<double>(n, M->m, b_atoms, M->m, M->d_Ai.as<double>(),
+                                                     reinterpret_cast<unsigned long long*>(grade_atom), q);
+        return MTP_OK;
+    };
+    // Repeated identical device-memory calls replay a CUDA graph of the whole evaluation: the first
+    // call runs eagerly (sizing every buffer), the second identical call captures, later ones replay.
+    std::vector<uintptr_t> sig;
+    if (M->graphs && !host) {
+        const uintptr_t v[] = {(uintptr_t)K, (uintptr_t)n, (uintptr_t)cfg_off, (uintptr_t)pos, (uintptr_t)types,
+                               (uintptr_t)cells, (uintptr_t)energy, (uintptr_t)forces, (uintptr_t)virial,
+                               (uintptr_t)site, (uintptr_t)b_rows, (uintptr_t)b_atoms, (uintptr_t)grade_cfg,
+                               (uintptr_t)grade_atom, (uintptr_t)flags, (uintptr_t)st, (uintptr_t)M->cap,
+                               (uintptr_t)reuse, (uintptr_t)(M->skin * 1e9), (uintptr_t)M->has_active,
+                               (uintptr_t)M->profiling};
+        sig.assign(v, v + sizeof v / sizeof v[0]);
+    }
+    bool done = false;
+    if (!sig.empty() && sig == M->g_sig) {
+        if (!M->g_exec) {
+            // capture on a private stream (the legacy default stream cannot be captured); the graph is
+            // launched on the caller's stream, which orders it exactly like the eager launches
+            bool ok = M->cap_stream || cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+            const int64_t before = M->launches;
+            cudaGraph_t g = nullptr;
+            if (ok) ok = cudaStreamBeginCapture(M->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const mtp_status e = enqueue(M->cap_stream);
+                const cudaError_t ce = cudaStreamEndCapture(M->cap_stream, &g);
+                ok = !e && ce == cudaSuccess && g;
+                if (ok) ok = cudaGraphInstantiate(&M->g_exec, g, 0) == cudaSuccess;
+                if (g) cudaGraphDestroy(g);
+            }
+            if (ok) {
+                M->g_launches = M->launches - before;
+            } else {  // not capturable here: stay eager from now on
+                cudaGetLastError();
+                M->g_exec = nullptr;
+                M->graphs = false;
+                M->launches = before;
+            }
+        } else {
+            M->launches += M->g_launches;
+        }
+        if (M->g_exec) {
+            if (cudaGraphLaunch(M->g_exec, st) != cudaSuccess) return MTP_ECUDA;
+            done = true;
+        }
+    }
+    if (!done) {
+        if (M->g_exec) {
+            cudaGraphExecDestroy(M->g_exec);
+            M->g_exec = nullptr;
+        }
+        s = enqueue(st);
+        if (s) return s;
+        M->g_sig = sig;
+    }
     if (host) {
         if (h_gcfg) cudaMemcpyAsync(h_gcfg, grade_cfg, sizeof(double) * K, cudaMemcpyDeviceToHost, st);
         if (h_gatom) cudaMemcpyAsync(h_gatom, grade_atom, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
@@ -660,6 +733,7 @@ mtp_status mtp_neighbors(mtp_model* M, int K, int n, const int32_t* cfg_off, con
 mtp_status mtp_select_active_set(mtp_model* M, int n_rows, const double* b_rows, int32_t* selected, int* n_swaps,
                                  double* max_grade, int flags, void* stream) {
     if (!M || !b_rows || n_rows < M->m) return MTP_EINVAL;
+    M->g_sig.clear();  // A^-1 may move: no replay of an older graph
     cudaStream_t st = (cudaStream_t)stream;
     const int m = M->m, n = n_rows;
     const size_t wsz = std::max((size_t)n * m, (size_t)2 * m * m) + 2 * (size_t)m + n + 16;
@@ -712,6 +786,7 @@ mtp_status mtp_select_active_set(mtp_model* M, int n_rows, const double* b_rows,
 
 mtp_status mtp_set_active_set(mtp_model* M, const double* A) {
     if (!M || !A) return MTP_EINVAL;
+    M->g_sig.clear();
     const int m = M->m;
     if (M->d_A.reserve(sizeof(double) * m * m) || M->d_Ai.reserve(sizeof(double) * m * m) ||
         M->mv_W.reserve(sizeof(double) * 2 * m * m + 16) || M->mv_status.reserve(16))

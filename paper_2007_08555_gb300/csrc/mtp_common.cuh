@@ -97,6 +97,17 @@ __host__ __device__ inline void loss_scales(int kind, double n, double* se, doub
     }
 }
 
+// A timing event on a stream; inside a stream capture it becomes an externally visible record node
+// (a plain record there is only a dependency and cannot be timed).
+inline void record_mark(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

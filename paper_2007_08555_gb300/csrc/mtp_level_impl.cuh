@@ -44,12 +44,103 @@ __device__ __forceinline__ int clamp_species(int z, int S) { return z < 0 ? 0 : 
 __device__ __forceinline__ float my_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double my_sqrt(double x) { return sqrt(x); }
 
+// Double-float numbers (hi + lo, |lo| <= ulp(hi) / 2): Knuth's TwoSum and the FMA form of Dekker's
+// TwoProduct give the exact rounding errors, so sums and products keep ~44 significant bits on the
+// FP32 pipe (GB300 issues double precision at a small fraction of the FP32 rate).
+struct Df {
+    float hi, lo;
+};
+__device__ __forceinline__ Df df_norm(float s, float e) {
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ Df df_add(Df a, Df b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return df_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ Df df_mul(Df a, Df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);
+    return df_norm(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ Df df_mulf(Df a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    const float e = __fmaf_rn(a.hi, b, -p);
+    return df_norm(p, __fmaf_rn(a.lo, b, e));
+}
+__device__ __forceinline__ Df df_neg(Df a) { return {-a.hi, -a.lo}; }
+
+// The radial functions (Eq. 3) and their derivatives in double-float arithmetic, rounded to float at
+// the end: below R_min the Chebyshev polynomials leave [-1, 1] and grow, and their float sum loses
+// the digits that this evaluation keeps.
+template <bool WANT_D>
+__device__ __forceinline__ void radial_df(const float r, const float* __restrict__ cz, const int NQ, const float rmin,
+                                       const float rcut, float* f, float* df) {
+    constexpr int NMU = G::NMU_;
+    // x = (2 r - R_min - R_cut) / (R_cut - R_min)
+    const Df span = df_add({rcut, 0.f}, {-rmin, 0.f});
+    const Df num = df_add(df_add({2.f * r, 0.f}, {-rmin, 0.f}), {-rcut, 0.f});
+    const float q = num.hi / span.hi;
+    const Df rem = df_add(num, df_neg(df_mulf(span, q)));  // num - q span
+    const Df x = df_add({q, 0.f}, {rem.hi / span.hi, 0.f});
+    const Df x2 = {2.f * x.hi, 2.f * x.lo};
+    Df F[NMU], D[NMU];
+#pragma unroll
+    for (int mu = 0; mu < NMU; ++mu) {
+        F[mu] = {cz[mu * NQ], 0.f};
+        D[mu] = {0.f, 0.f};
+    }
+    Df t0 = {1.f, 0.f}, t1 = x, d0 = {0.f, 0.f}, d1 = {1.f, 0.f};
+    for (int b = 1; b < NQ; ++b) {
+        Df tb = t1, db = d1;
+        if (b > 1) {  // T_b = 2 x T_{b-1} - T_{b-2};  T_b' = 2 T_{b-1} + 2 x T_{b-1}' - T_{b-2}'
+            tb = df_add(df_mul(x2, t1), df_neg(t0));
+            if (WANT_D) db = df_add(df_add({2.f * t1.hi, 2.f * t1.lo}, df_mul(x2, d1)), df_neg(d0));
+            t0 = t1;
+            t1 = tb;
+            if (WANT_D) {
+                d0 = d1;
+                d1 = db;
+            }
+        }
+#pragma unroll
+        for (int mu = 0; mu < NMU; ++mu) {
+            F[mu] = df_add(F[mu], df_mulf(tb, cz[mu * NQ + b]));
+            if (WANT_D) D[mu] = df_add(D[mu], df_mulf(db, cz[mu * NQ + b]));
+        }
+    }
+    // Q = T (R_cut - r)^2;  dQ/dr = T' (2 / span) (R_cut - r)^2 - 2 T (R_cut - r)
+    const Df u = df_add({rcut, 0.f}, {-r, 0.f});
+    const Df u2 = df_mul(u, u);
+    const float two_over_span = 2.f / span.hi;
+#pragma unroll
+    for (int mu = 0; mu < NMU; ++mu) {
+        const Df fu = df_mul(F[mu], u2);
+        f[mu] = fu.hi + fu.lo;
+        if (WANT_D) {
+            const Df d = df_add(df_mulf(df_mul(D[mu], u2), two_over_span), df_mulf(df_mul(F[mu], u), -2.f));
+            df[mu] = d.hi + d.lo;
+        }
+    }
+}
+
 // f_mu(r) = (R_cut - r)^2 sum_b c_b T_b(x) and its r-derivative (Eqs. 3-4); Chebyshev T_b by the
 // three-term recurrence, dT_b/dx by its derivative.  cz points at c[z_i][z_j][0][0].
+// Below R_min the Chebyshev polynomials leave [-1, 1], grow quickly and cancel in the sum; there the
+// float evaluation alone costs the float path ~1e-5 in the energy, so the float path takes those
+// (rare) pairs through radial_df; the common case stays plain float.
 template <class T, bool WANT_D>
 __device__ __forceinline__ void radial(const T r, const T* __restrict__ cz, const int NQ, const T rmin,
                                        const T rcut, const T inv_span, T* f, T* df) {
     constexpr int NMU = G::NMU_;
+    if constexpr (sizeof(T) == 4) {
+        if (r < rmin) {
+            radial_df<WANT_D>(r, cz, NQ, rmin, rcut, f, df);
+            return;
+        }
+    }
     const T x = (T(2) * r - rmin - rcut) * inv_span;
     T F[NMU], D[NMU];
 #pragma unroll
@@ -563,9 +654,9 @@ template <class T>
 int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks) {
     if (a.n_atoms == 0) return 0;
     int launches = 0;
-    if (marks) cudaEventRecord(marks[kPhaseMoments], st);
+    if (marks) record_mark(marks[kPhaseMoments], st);
     launches += launch_pairs_tpa<T>(a, st, n_sm, true);
-    if (marks) cudaEventRecord(marks[kPhaseContract], st);
+    if (marks) record_mark(marks[kPhaseContract], st);
 #if MTPGEN_HAS_UNROLLED
     if constexpr (sizeof(T) == 4) {
         const int threads = 128;
@@ -601,9 +692,9 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks)
         k_contract<T, A><<<blocks, threads, smem, st>>>(a);
         ++launches;
     }
-    if (marks) cudaEventRecord(marks[kPhasePairgrad], st);
+    if (marks) record_mark(marks[kPhasePairgrad], st);
     launches += launch_pairs_tpa<T>(a, st, n_sm, false);
-    if (marks) cudaEventRecord(marks[kPhaseGather], st);
+    if (marks) record_mark(marks[kPhaseGather], st);
     {
         const int threads = 128;
         const long work = (long)(((a.n_atoms + 31) / 32) * 32) * a.tpa;
@@ -617,7 +708,7 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks)
         }
         ++launches;
     }
-    if (marks) cudaEventRecord(marks[kPhases], st);
+    if (marks) record_mark(marks[kPhases], st);
     return launches;
 }
 

@@ -270,52 +270,67 @@ __global__ void __launch_bounds__(128) k_build(const BuildArgs a) {
             }
             const int total = __shfl_sync(0xffffffffu, incl, 31);
             const int pre = incl - bcnt;
-            for (int f0 = 0; f0 < total; f0 += 32) {
-                const int f = f0 + lane;
-                // last lane b with pre[b] <= f (then f < pre[b] + cnt[b])
-                int b = 0;
+            // two candidates per lane per round: their loads are independent and overlap
+            for (int f0 = 0; f0 < total; f0 += 64) {
+                int jj[2], svv[2][3];
+                bool acc2[2];
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int pv = __shfl_sync(0xffffffffu, pre, b + step);
-                    if (pv <= f) b += step;
-                }
-                const int qs = __shfl_sync(0xffffffffu, bstart, b), qp = __shfl_sync(0xffffffffu, pre, b);
-                const int t0 = __shfl_sync(0xffffffffu, tb0, b), t1 = __shfl_sync(0xffffffffu, tb1, b),
-                          t2 = __shfl_sync(0xffffffffu, tb2, b);
-                const float fx = __shfl_sync(0xffffffffu, ox, b), fy = __shfl_sync(0xffffffffu, oy, b),
-                            fz = __shfl_sync(0xffffffffu, oz, b);
-                bool acc = false;
-                int j = 0, sv[3] = {0, 0, 0};
-                if (f < total) {
-                    j = a.bin_atoms[qs + (f - qp)];
-                    const int wj = a.atom_wrap[j];
-                    sv[0] = t0 - unpack(wj, 0) + unpack(wi, 0);
-                    sv[1] = t1 - unpack(wj, 1) + unpack(wi, 1);
-                    sv[2] = t2 - unpack(wj, 2) + unpack(wi, 2);
-                    if (!(j == i && sv[0] == 0 && sv[1] == 0 && sv[2] == 0)) {
-                        const float4 lj = a.local[j];
-                        const float dx = (lj.x - li.x) + fx, dy = (lj.y - li.y) + fy, dz = (lj.z - li.z) + fz;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < a.lo2) {
-                            acc = true;
-                        } else if (r2 <= a.hi2) {
-                            const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1],
-                                                  a.pos[3 * (size_t)i + 2]};
-                            const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1],
-                                                  a.pos[3 * (size_t)j + 2]};
-                            double dd[3];
-                            acc = exact_r2(xi, xj, D.H, sv, dd) < a.rs2;
+                for (int h = 0; h < 2; ++h) {
+                    const int f = f0 + 32 * h + lane;
+                    // last lane b with pre[b] <= f (then f < pre[b] + cnt[b])
+                    int b = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int pv = __shfl_sync(0xffffffffu, pre, b + step);
+                        if (pv <= f) b += step;
+                    }
+                    const int qs = __shfl_sync(0xffffffffu, bstart, b), qp = __shfl_sync(0xffffffffu, pre, b);
+                    const int t0 = __shfl_sync(0xffffffffu, tb0, b), t1 = __shfl_sync(0xffffffffu, tb1, b),
+                              t2 = __shfl_sync(0xffffffffu, tb2, b);
+                    const float fx = __shfl_sync(0xffffffffu, ox, b), fy = __shfl_sync(0xffffffffu, oy, b),
+                                fz = __shfl_sync(0xffffffffu, oz, b);
+                    bool acc = false;
+                    int j = 0, sv[3] = {0, 0, 0};
+                    if (f < total) {
+                        j = a.bin_atoms[qs + (f - qp)];
+                        const int wj = a.atom_wrap[j];
+                        sv[0] = t0 - unpack(wj, 0) + unpack(wi, 0);
+                        sv[1] = t1 - unpack(wj, 1) + unpack(wi, 1);
+                        sv[2] = t2 - unpack(wj, 2) + unpack(wi, 2);
+                        if (!(j == i && sv[0] == 0 && sv[1] == 0 && sv[2] == 0)) {
+                            const float4 lj = a.local[j];
+                            const float dx = (lj.x - li.x) + fx, dy = (lj.y - li.y) + fy, dz = (lj.z - li.z) + fz;
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < a.lo2) {
+                                acc = true;
+                            } else if (r2 <= a.hi2) {
+                                const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1],
+                                                      a.pos[3 * (size_t)i + 2]};
+                                const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1],
+                                                      a.pos[3 * (size_t)j + 2]};
+                                double dd[3];
+                                acc = exact_r2(xi, xj, D.H, sv, dd) < a.rs2;
+                            }
                         }
                     }
+                    jj[h] = j;
+                    acc2[h] = acc;
+                    svv[h][0] = sv[0];
+                    svv[h][1] = sv[1];
+                    svv[h][2] = sv[2];
                 }
-                const unsigned ball = __ballot_sync(0xffffffffu, acc);
-                if (acc) {
-                    const int pos_ = cnt + __popc(ball & ((1u << lane) - 1u));
-                    if (pos_ < a.cap)
-                        keys[pos_] = ((unsigned long long)j << 24) |
-                                     (unsigned long long)(((sv[0] + 128) << 16) | ((sv[1] + 128) << 8) | (sv[2] + 128));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned ball = __ballot_sync(0xffffffffu, acc2[h]);
+                    if (acc2[h]) {
+                        const int pos_ = cnt + __popc(ball & ((1u << lane) - 1u));
+                        if (pos_ < a.cap)
+                            keys[pos_] = ((unsigned long long)jj[h] << 24) |
+                                         (unsigned long long)(((svv[h][0] + 128) << 16) | ((svv[h][1] + 128) << 8) |
+                                                              (svv[h][2] + 128));
+                    }
+                    cnt += __popc(ball);
                 }
-                cnt += __popc(ball);
             }
         }
         __syncwarp();
@@ -554,10 +569,12 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     int* cfg_bins = nb.bin_fill.as<int>();
     k_cells<<<(K + 127) / 128, 128, 0, st>>>(K, cells, cfg_off, rsearch, desc, cfg_bins, nb.err.as<int>());
     ++launches;
-    int* cfg_bin0 = nb.bin_start.as<int>();  // temporary: K+1 ints
-    launches += scan_exclusive(cfg_bins, cfg_bin0, K, tmp, st);
-    k_cells_offsets<<<(K + 127) / 128, 128, 0, st>>>(K, cfg_bin0, desc);
-    ++launches;
+    if (K > 1) {  // a single configuration starts at bin 0: no offsets to compute
+        int* cfg_bin0 = nb.bin_start.as<int>();  // temporary: K+1 ints
+        launches += scan_exclusive(cfg_bins, cfg_bin0, K, tmp, st);
+        k_cells_offsets<<<(K + 127) / 128, 128, 0, st>>>(K, cfg_bin0, desc);
+        ++launches;
+    }
     const int total_bins_upper = n + K;  // every configuration has at most max(1, atoms) bins
     cudaMemsetAsync(bin_count, 0, (size_t)(total_bins_upper + 1) * 4, st);
     cudaMemsetAsync(nb.bin_fill.p, 0, (size_t)(total_bins_upper + 1) * 4, st);

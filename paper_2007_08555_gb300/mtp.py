@@ -289,11 +289,17 @@ class Model:
         return mtp_launch_count(self.h)
 
     def eval_batch(self, pos, types, cells, cfg_off, forces=True, virial=True, site=False, b_rows=False,
-                   b_atoms=False, grade_cfg=False, grade_atom=False, stream=None, flags=0):
+                   b_atoms=False, grade_cfg=False, grade_atom=False, stream=None, flags=0, out=None):
         """Device tensors in (float64 pos [N,3], int32 types [N], float64 cells [K,3,3], int32 cfg_off [K+1]);
-        device tensors out."""
+        device tensors out.  Passing back the dict of a previous call as `out` reuses its tensors, so that
+        repeated calls have identical arguments (the library then replays its CUDA graph)."""
         import torch
 
+        if out is not None:
+            mtp_eval_batch(self.h, cells.shape[0], pos.shape[0], cfg_off, pos, types, cells, out["energy"],
+                           out.get("forces"), out.get("virial"), out.get("site"), out.get("b_rows"), out.get("b_atoms"),
+                           out.get("grade_cfg"), out.get("grade_atom"), flags, stream)
+            return out
         dev = pos.device
         K = cells.shape[0]
         N = pos.shape[0]

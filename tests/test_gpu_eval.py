@@ -221,3 +221,44 @@ def test_host_memory_path_matches_device_path(gpu_lib):
     # the per-configuration sums use double-precision atomics, so the order of additions may differ
     np.testing.assert_allclose(e, ref["energy"].cpu().numpy(), rtol=1e-13)
     np.testing.assert_allclose(f, ref["forces"].cpu().numpy(), rtol=1e-6, atol=1e-6 * np.abs(f).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_replay_tracks_new_inputs(gpu_lib, precision):
+    """Repeated identical calls replay a captured CUDA graph; the graph must read the current values."""
+    cfg = synth.bcc_128()
+    p = params(10, 1, 1)
+    model = mtp.Model.from_params(p, precision)
+    pos = dev(cfg.pos, torch.float64)
+    types, cells = dev(cfg.types, torch.int32), dev(cfg.cell.reshape(1, 3, 3), torch.float64)
+    off = dev(np.array([0, cfg.n]), torch.int32)
+    out = None
+    rng = np.random.default_rng(5)
+    for k in range(5):
+        moved = cfg.pos + rng.normal(0, 0.02, size=cfg.pos.shape)
+        pos.copy_(dev(moved, torch.float64))  # same buffer, new values
+        out = model.eval_batch(pos, types, cells, off, out=out)
+        ref = mtp.Model.from_params(p, precision).eval_batch(pos, types, cells, off)
+        assert out["energy"].item() == pytest.approx(ref["energy"].item(), rel=1e-12)
+        np.testing.assert_allclose(out["forces"].cpu().numpy(), ref["forces"].cpu().numpy(), rtol=1e-12,
+                                   atol=1e-12 * np.abs(ref["forces"].cpu().numpy()).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("L", [18, 20])
+def test_batched_small_cells_high_level(gpu_lib, precision, L):
+    """lev_max 18 and 20 (straight-line contraction with spills in the float path), scaled parameters."""
+    b = synth.small_cells(n_cfg=6, n_lo=12, n_hi=40, seed=60 + L)
+    p = synth.scaled_params(L, 3, 8, 2.0, 5.0, synth.labels_from_level_table(levels.level_table(L)), seed=61)
+    pot = oracle.Potential(p)
+    model = mtp.Model.from_params(p, precision)
+    pos, types, cells, off = batch_tensors(b)
+    out = model.eval_batch(pos, types, cells, off, b_rows=True)
+    e, f, w = out["energy"].cpu().numpy(), out["forces"].cpu().numpy(), out["virial"].cpu().numpy()
+    br = out["b_rows"].cpu().numpy()
+    tol = TOL[precision]
+    for k in range(b.n_cfg):
+        ref = pot.eval(b.config(k), want_b=True)
+        a0, a1 = b.cfg_off[k], b.cfg_off[k + 1]
+        check_config(e[k], f[a0:a1], w[k], ref, b.config(k).n, tol, msg=f"cfg {k}")
+        assert rel(br[k], ref["b_atoms"].sum(0)) <= tol["e"] * 10

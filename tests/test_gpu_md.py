@@ -25,8 +25,8 @@ def dev(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def scaled(L, S, seed, decay=1.0):
-    return synth.scaled_params(L, S, 8, 2.0, 5.0, synth.labels_from_level_table(levels.level_table(L)), seed,
+def scaled(L, S, seed, decay=1.0, r_min=2.0):
+    return synth.scaled_params(L, S, 8, r_min, 5.0, synth.labels_from_level_table(levels.level_table(L)), seed,
                                radial_decay=decay)
 
 
@@ -87,7 +87,7 @@ def test_fp32_energy_conservation(gpu_lib):
     # smooth radial functions (damped Chebyshev coefficients): a well-resolved trajectory
     rng = np.random.default_rng(21)
     cfg = synth.perturbed("fcc", (6, 6, 6), 0.0, rng, n_species=3)
-    p = scaled(16, 3, 22, decay=0.5)
+    p = scaled(16, 3, 22, decay=0.5, r_min=1.0)
     v0 = synth.maxwell_velocities(cfg.types, MASSES, 300.0, seed=23)
     runs = {}
     for prec in ("fp32", "fp64"):
