@@ -76,6 +76,7 @@ struct mtp_model {
     cudaGraphExec_t g_exec = nullptr;  // graph captured from a call with g_sig
     cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
     int64_t g_launches = 0;            // kernels in the graph
+    int* h_flags = nullptr;            // pinned: error word and largest neighbour count of the last build
 };
 
 namespace {
@@ -224,18 +225,25 @@ void collect_profile(mtp_model* M) {
     M->prof_calls += 1;
 }
 
+// Waits for the stream, then reports the errors the device recorded.  The two flag words come back
+// by stream-ordered copies into pinned memory before the one synchronisation, and the error word is
+// cleared by a stream-ordered memset, so a synchronous call costs a single wait.
 mtp_status finish(mtp_model* M, cudaStream_t st) {
+    if (!M->h_flags && cudaHostAlloc((void**)&M->h_flags, 2 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        M->h_flags = nullptr;
+        return MTP_ENOMEM;
+    }
+    M->h_flags[0] = M->h_flags[1] = 0;
+    if (M->nb.err.p) {
+        cudaMemcpyAsync(M->h_flags, M->nb.err.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(M->h_flags + 1, M->nb.max_seen.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaMemsetAsync(M->nb.err.p, 0, sizeof(int), st);
+    }
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
     collect_profile(M);
-    int err = 0, mx = 0;
-    if (M->nb.err.p) {
-        cudaMemcpy(&err, M->nb.err.p, sizeof(int), cudaMemcpyDeviceToHost);
-        cudaMemcpy(&mx, M->nb.max_seen.p, sizeof(int), cudaMemcpyDeviceToHost);
-        cudaMemset(M->nb.err.p, 0, sizeof(int));
-    }
-    M->last_max = mx;
-    return status_from_err(err);
+    M->last_max = M->h_flags[1];
+    return status_from_err(M->h_flags[0]);
 }
 
 template <class T>
@@ -337,6 +345,9 @@ void mtp_destroy(mtp_model* M) {
                       &M->mv_C, &M->mv_status, &M->mv_swaps, &M->mv_gmax, &M->s_rows, &M->s_gamma, &M->g_brows,
                       &M->g_batoms};
     for (DevBuf* b : bufs) b->release();
+    M->nb.atom_wp.release();
+    M->nb.keys_am.release();
+    if (M->h_flags) cudaFreeHost(M->h_flags);
     if (M->g_exec) cudaGraphExecDestroy(M->g_exec);
     if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
     for (cudaEvent_t& e : M->ev_nbr)

@@ -6,14 +6,16 @@
 // (small cells are visited several times with different image shifts).  Distances are first
 // taken in float from bin-local coordinates as a prefilter; pairs within 1e-3 Angstrom of the
 // cutoff are decided in double precision with the fixed operation order documented in mtp.h, so
-// the lists are identical to a brute-force double-precision search.  After compaction each lane
+// the lists are identical to a brute-force double-precision search.  One block handles one bin at a
+// time: the atoms of the surrounding bins are staged once in shared memory and every warp tests
+// them for one atom of the bin, compacting the accepted pairs with a ballot.  Each lane then
 // computes r_ij of one accepted pair: exactly in double precision for the double path, and in
 // double-float arithmetic (error-free float transformations, ~2^-44 relative) rounded once to
 // float for the float path.  Double-precision instructions are few and never divergent: on this
-// part a warp-wide double-precision instruction costs many times a float one.  Each warp owns one atom: lanes test
-// candidates, accepted pairs are compacted with a ballot, rank-sorted by (j, s) and written in
-// slot-major layout.  A last kernel records, for every pair, the slot of the reverse pair in
-// the neighbour's list (used by the deterministic force gather).
+// part a warp-wide double-precision instruction costs many times a float one.  Accepted pairs are
+// rank-sorted by (j, s) and written in slot-major layout.  A last kernel records, for every pair,
+// the slot of the reverse pair in the neighbour's list (used by the deterministic force gather).
+#include <algorithm>
 #include "mtp_internal.h"
 #include "mtp_common.cuh"
 
@@ -27,12 +29,6 @@ constexpr int kScanBlock = kScanItems * kScanThreads;
 constexpr int kMaxImageReach = 16;
 constexpr int kMaxShift = 50;  // |wrap| per atom; image shifts then stay within +-117
 constexpr double kBand = 1e-3;
-
-__device__ __forceinline__ int floordiv(int a, int b) {
-    int q = a / b;
-    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
-    return q;
-}
 
 __device__ __forceinline__ int find_cfg(const int* cfg_off, int K, int i) {
     int lo = 0, hi = K;  // cfg_off[lo] <= i < cfg_off[hi]
@@ -171,6 +167,7 @@ __device__ __forceinline__ double exact_r2(const double* xi, const double* xj, c
 
 struct BuildArgs {
     int n, cap, S;
+    int nbins;       // bins to visit (an upper bound; empty bins are skipped)
     double rs2;      // rsearch^2 (double)
     float lo2, hi2;  // (rsearch -/+ band)^2
     const double* pos;
@@ -186,6 +183,7 @@ struct BuildArgs {
     int* count;
     int* jz;
     int* shift;
+    unsigned long long* keys_am;  // [n][cap] the sorted keys, atom-major
     void* rx;
     void* ry;
     void* rz;
@@ -217,195 +215,275 @@ __device__ __forceinline__ DF df_scale(float t, float hhi, float hlo) {  // t sm
     return fast_two_sum(p, __fmaf_rn(t, hlo, e));
 }
 
+__device__ __forceinline__ int pack3(int s0, int s1, int s2) {
+    return ((s0 + 128) & 255) | (((s1 + 128) & 255) << 8) | (((s2 + 128) & 255) << 16);
+}
+// image shift inside a pair key: s_0 in the high byte, so that keys sort by (j, s_0, s_1, s_2)
+__device__ __forceinline__ int key_shift(int s0, int s1, int s2) { return pack3(s2, s1, s0); }
+__device__ __forceinline__ int key_s(int packed, int q) { return unpack(packed, 2 - q); }
+constexpr int kBias3 = 0x808080;  // three zero components
+
+// Shared-memory layout of k_build (bytes): staged candidates, the current group of neighbour bins,
+// then per warp the accepted keys and their r_ij.
+constexpr int kBuildThreads = 128, kBuildWarps = kBuildThreads / 32;
+constexpr int kGroup = kBuildThreads;  // neighbour bins described per staging round
+constexpr int kChunk = 1024;           // candidates staged per round
+constexpr size_t kSmCpos = 0;
+constexpr size_t kSmCshift = kSmCpos + sizeof(float4) * kChunk;
+constexpr size_t kSmGpre = kSmCshift + sizeof(int) * kChunk;
+constexpr size_t kSmGstart = kSmGpre + sizeof(int) * (kGroup + 4);
+constexpr size_t kSmGtb = kSmGstart + sizeof(int) * kGroup;
+constexpr size_t kSmGoff = kSmGtb + sizeof(int) * kGroup;
+constexpr size_t kSmWsum = kSmGoff + sizeof(float) * 3 * kGroup;
+constexpr size_t kSmWarp = kSmWsum + 64;
+size_t build_smem(int cap, size_t realsz) { return kSmWarp + (size_t)kBuildWarps * cap * (8 + 3 * realsz); }
+
+// One block per bin (grid-stride over the bins).  The atoms of the bins around it are the candidates
+// of every atom in it: they are staged once in shared memory (positions relative to the bin's
+// origin, image shift minus the candidate's wrap), then each warp takes one atom of the bin, tests
+// the staged candidates with its lanes and compacts the accepted ones with a ballot.  Small cells
+// whose candidates exceed one staging round are re-staged for every group of four atoms.
 template <class T>
-__global__ void __launch_bounds__(128) k_build(const BuildArgs a) {
+__global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* cpos = reinterpret_cast<float4*>(smem_raw + kSmCpos);
+    int* cshift = reinterpret_cast<int*>(smem_raw + kSmCshift);
+    int* gpre = reinterpret_cast<int*>(smem_raw + kSmGpre);
+    int* gstart = reinterpret_cast<int*>(smem_raw + kSmGstart);
+    int* gtb = reinterpret_cast<int*>(smem_raw + kSmGtb);
+    float* goff = reinterpret_cast<float*>(smem_raw + kSmGoff);
+    int* wsum = reinterpret_cast<int*>(smem_raw + kSmWsum);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw) + (size_t)warp * a.cap;
-    T* rbuf = reinterpret_cast<T*>(reinterpret_cast<unsigned long long*>(smem_raw) + (size_t)wpb * a.cap) +
-              (size_t)warp * 3 * a.cap;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw + kSmWarp) + (size_t)warp * a.cap;
+    T* rbuf = reinterpret_cast<T*>(reinterpret_cast<unsigned long long*>(smem_raw + kSmWarp) +
+                                   (size_t)kBuildWarps * a.cap) + (size_t)warp * 3 * a.cap;
     T* RX = static_cast<T*>(a.rx);
     T* RY = static_cast<T*>(a.ry);
     T* RZ = static_cast<T*>(a.rz);
-    for (int i = blockIdx.x * wpb + warp; i < a.n; i += gridDim.x * wpb) {
-        const int k = a.cfg_of[i];
+    const size_t n = (size_t)a.n;
+    __shared__ int smax;
+    if (threadIdx.x == 0) smax = 0;
+    __syncthreads();
+    for (int bin = blockIdx.x; bin < a.nbins; bin += gridDim.x) {
+        const int start = a.bin_start[bin], nat = a.bin_start[bin + 1] - start;
+        if (nat == 0) continue;
+        const int k = a.cfg_of[a.bin_atoms[start]];
         const CellDesc& D = a.desc[k];
-        const int lb = a.atom_bin[i] - D.bin0;
+        const int lb = bin - D.bin0;
         const int b2 = lb % D.n[2], b1 = (lb / D.n[2]) % D.n[1], b0 = lb / (D.n[2] * D.n[1]);
-        const int wi = a.atom_wrap[i];
-        const float4 li = a.local[i];
-        int cnt = 0;
-        // 1. candidates: float prefilter; only the rare pairs within 1e-3 Angstrom of the cutoff
-        //    take the double-precision decision.  The bins to visit are handed out one per lane
-        //    (32 at a time); their atoms are then flattened over the lanes, each lane finding its
-        //    bin by a binary search over the lanes' running candidate counts.
         const int ny = 2 * D.c[1] + 1, nz = 2 * D.c[2] + 1;
         const int n_off = (2 * D.c[0] + 1) * ny * nz;
-        for (int base = 0; base < n_off; base += 32) {
-            const int o = base + lane;
-            int bstart = 0, bcnt = 0, tb0 = 0, tb1 = 0, tb2 = 0;
-            float ox = 0.f, oy = 0.f, oz = 0.f;
-            if (o < n_off) {
-                const int o2 = o % nz - D.c[2], o1 = (o / nz) % ny - D.c[1], o0 = o / (nz * ny) - D.c[0];
-                int w0 = b0 + o0, w1 = b1 + o1, w2 = b2 + o2;
-                while (w0 < 0) { w0 += D.n[0]; --tb0; }
-                while (w0 >= D.n[0]) { w0 -= D.n[0]; ++tb0; }
-                while (w1 < 0) { w1 += D.n[1]; --tb1; }
-                while (w1 >= D.n[1]) { w1 -= D.n[1]; ++tb1; }
-                while (w2 < 0) { w2 += D.n[2]; --tb2; }
-                while (w2 >= D.n[2]) { w2 -= D.n[2]; ++tb2; }
-                ox = o0 * D.hn[0] + o1 * D.hn[3] + o2 * D.hn[6];
-                oy = o0 * D.hn[1] + o1 * D.hn[4] + o2 * D.hn[7];
-                oz = o0 * D.hn[2] + o1 * D.hn[5] + o2 * D.hn[8];
-                const int bin = D.bin0 + (w0 * D.n[1] + w1) * D.n[2] + w2;
-                bstart = a.bin_start[bin];
-                bcnt = a.bin_start[bin + 1] - bstart;
-            }
-            int incl = bcnt;
-#pragma unroll
-            for (int sh = 1; sh < 32; sh <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, sh);
-                if (lane >= sh) incl += y;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            const int pre = incl - bcnt;
-            // two candidates per lane per round: their loads are independent and overlap
-            for (int f0 = 0; f0 < total; f0 += 64) {
-                int jj[2], svv[2][3];
-                bool acc2[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int f = f0 + 32 * h + lane;
-                    // last lane b with pre[b] <= f (then f < pre[b] + cnt[b])
-                    int b = 0;
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1) {
-                        const int pv = __shfl_sync(0xffffffffu, pre, b + step);
-                        if (pv <= f) b += step;
+        bool reuse = false;  // the previous group of atoms left every candidate staged
+        int total = 0;
+        for (int ab = 0; ab < nat; ab += kBuildWarps) {
+            const bool has = ab + warp < nat;
+            const int i = has ? a.bin_atoms[start + ab + warp] : 0;
+            const float4 li = has ? a.local[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int wi = has ? a.atom_wrap[i] : pack3(0, 0, 0);
+            // the image shift of a pair is the staged (bin shift - w_j) plus w_i: biased bytes add
+            // without carries as long as every component stays within +-127
+            const int wik = key_shift(unpack(wi, 0), unpack(wi, 1), unpack(wi, 2)) - kBias3;
+            int cnt = 0;
+            for (int g0 = 0; g0 < n_off; g0 += kGroup) {
+                if (!reuse) {
+                    // 1a. this group's neighbour bins, one per thread: start, count, image shift of
+                    //     the wrap, offset of its origin; then a block-wide exclusive scan of the counts
+                    const int o = g0 + threadIdx.x;
+                    int bstart = 0, bcnt = 0, tb0 = 0, tb1 = 0, tb2 = 0;
+                    float ox = 0.f, oy = 0.f, oz = 0.f;
+                    if (o < n_off) {
+                        const int o2 = o % nz - D.c[2], o1 = (o / nz) % ny - D.c[1], o0 = o / (nz * ny) - D.c[0];
+                        int w0 = b0 + o0, w1 = b1 + o1, w2 = b2 + o2;
+                        while (w0 < 0) { w0 += D.n[0]; --tb0; }
+                        while (w0 >= D.n[0]) { w0 -= D.n[0]; ++tb0; }
+                        while (w1 < 0) { w1 += D.n[1]; --tb1; }
+                        while (w1 >= D.n[1]) { w1 -= D.n[1]; ++tb1; }
+                        while (w2 < 0) { w2 += D.n[2]; --tb2; }
+                        while (w2 >= D.n[2]) { w2 -= D.n[2]; ++tb2; }
+                        ox = o0 * D.hn[0] + o1 * D.hn[3] + o2 * D.hn[6];
+                        oy = o0 * D.hn[1] + o1 * D.hn[4] + o2 * D.hn[7];
+                        oz = o0 * D.hn[2] + o1 * D.hn[5] + o2 * D.hn[8];
+                        const int nbin = D.bin0 + (w0 * D.n[1] + w1) * D.n[2] + w2;
+                        bstart = a.bin_start[nbin];
+                        bcnt = a.bin_start[nbin + 1] - bstart;
                     }
-                    const int qs = __shfl_sync(0xffffffffu, bstart, b), qp = __shfl_sync(0xffffffffu, pre, b);
-                    const int t0 = __shfl_sync(0xffffffffu, tb0, b), t1 = __shfl_sync(0xffffffffu, tb1, b),
-                              t2 = __shfl_sync(0xffffffffu, tb2, b);
-                    const float fx = __shfl_sync(0xffffffffu, ox, b), fy = __shfl_sync(0xffffffffu, oy, b),
-                                fz = __shfl_sync(0xffffffffu, oz, b);
-                    bool acc = false;
-                    int j = 0, sv[3] = {0, 0, 0};
-                    if (f < total) {
-                        j = a.bin_atoms[qs + (f - qp)];
-                        const int wj = a.atom_wrap[j];
-                        sv[0] = t0 - unpack(wj, 0) + unpack(wi, 0);
-                        sv[1] = t1 - unpack(wj, 1) + unpack(wi, 1);
-                        sv[2] = t2 - unpack(wj, 2) + unpack(wi, 2);
-                        if (!(j == i && sv[0] == 0 && sv[1] == 0 && sv[2] == 0)) {
+                    int incl = bcnt;
+#pragma unroll
+                    for (int sh = 1; sh < 32; sh <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, sh);
+                        if (lane >= sh) incl += y;
+                    }
+                    if (lane == 31) wsum[warp] = incl;
+                    __syncthreads();
+                    int wpre = 0;
+                    total = 0;
+#pragma unroll
+                    for (int w = 0; w < kBuildWarps; ++w) {
+                        const int v = wsum[w];
+                        wpre += w < warp ? v : 0;
+                        total += v;
+                    }
+                    gpre[threadIdx.x] = wpre + incl - bcnt;
+                    gstart[threadIdx.x] = bstart;
+                    gtb[threadIdx.x] = pack3(tb0, tb1, tb2);
+                    goff[threadIdx.x] = ox;
+                    goff[kGroup + threadIdx.x] = oy;
+                    goff[2 * kGroup + threadIdx.x] = oz;
+                    __syncthreads();
+                }
+                for (int c0 = 0; c0 < total; c0 += kChunk) {
+                    const int m = min(kChunk, total - c0);
+                    if (!reuse) {
+                        // 1b. stage candidates c0 .. c0 + m: bin g holds candidate f when
+                        //     gpre[g] <= f < gpre[g + 1] (the last g with gpre[g] <= f)
+                        for (int f = threadIdx.x; f < m; f += kBuildThreads) {
+                            const int ff = c0 + f;
+                            int g = 0;
+#pragma unroll
+                            for (int step = kGroup / 2; step > 0; step >>= 1)
+                                if (gpre[g + step] <= ff) g += step;
+                            const int j = a.bin_atoms[gstart[g] + (ff - gpre[g])];
+                            const int wj = a.atom_wrap[j];
                             const float4 lj = a.local[j];
-                            const float dx = (lj.x - li.x) + fx, dy = (lj.y - li.y) + fy, dz = (lj.z - li.z) + fz;
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < a.lo2) {
-                                acc = true;
-                            } else if (r2 <= a.hi2) {
-                                const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1],
-                                                      a.pos[3 * (size_t)i + 2]};
-                                const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1],
-                                                      a.pos[3 * (size_t)j + 2]};
-                                double dd[3];
-                                acc = exact_r2(xi, xj, D.H, sv, dd) < a.rs2;
+                            cpos[f] = make_float4(lj.x + goff[g], lj.y + goff[kGroup + g], lj.z + goff[2 * kGroup + g],
+                                                  __int_as_float(j));
+                            const int tb = gtb[g];
+                            cshift[f] = key_shift(unpack(tb, 0) - unpack(wj, 0), unpack(tb, 1) - unpack(wj, 1),
+                                                  unpack(tb, 2) - unpack(wj, 2));
+                        }
+                        __syncthreads();
+                    }
+                    if (has) {
+                        // 1c. float prefilter on the staged candidates; only the rare pairs within
+                        //     1e-3 Angstrom of the cutoff take the double-precision decision
+                        for (int e0 = 0; e0 < m; e0 += 32) {
+                            const int e = e0 + lane;
+                            bool acc = false;
+                            unsigned long long key = 0;
+                            if (e < m) {
+                                const float4 cp = cpos[e];
+                                const float dx = cp.x - li.x, dy = cp.y - li.y, dz = cp.z - li.z;
+                                const float r2 = dx * dx + dy * dy + dz * dz;
+                                if (r2 <= a.hi2) {
+                                    const int j = __float_as_int(cp.w);
+                                    const int ks = cshift[e] + wik;  // key-order shift s
+                                    if (!(j == i && ks == kBias3)) {
+                                        if (r2 < a.lo2) {
+                                            acc = true;
+                                        } else {
+                                            const int sv[3] = {key_s(ks, 0), key_s(ks, 1), key_s(ks, 2)};
+                                            const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1],
+                                                                  a.pos[3 * (size_t)i + 2]};
+                                            const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1],
+                                                                  a.pos[3 * (size_t)j + 2]};
+                                            double dd[3];
+                                            acc = exact_r2(xi, xj, D.H, sv, dd) < a.rs2;
+                                        }
+                                        key = ((unsigned long long)j << 24) | (unsigned long long)ks;
+                                    }
+                                }
                             }
+                            const unsigned ball = __ballot_sync(0xffffffffu, acc);
+                            if (acc) {
+                                const int pos_ = cnt + __popc(ball & ((1u << lane) - 1u));
+                                if (pos_ < a.cap) keys[pos_] = key;
+                            }
+                            cnt += __popc(ball);
                         }
                     }
-                    jj[h] = j;
-                    acc2[h] = acc;
-                    svv[h][0] = sv[0];
-                    svv[h][1] = sv[1];
-                    svv[h][2] = sv[2];
+                    if (!reuse) __syncthreads();  // the next staging round overwrites the candidates
+                }
+            }
+            reuse = n_off <= kGroup && total <= kChunk;
+            if (!has) continue;
+            __syncwarp();
+            const int keep = min(cnt, a.cap);
+            if (lane == 0) {
+                if (cnt > a.cap) atomicOr(a.err, kErrOverflow);
+                atomicMax(&smax, cnt);  // one global update per block, at the end
+            }
+            // 2. r_ij of the accepted pairs, one pair per lane: exact double precision for the
+            //    double path, double-float arithmetic (then one rounding) for the float path
+            if (sizeof(T) == 8) {
+                const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1], a.pos[3 * (size_t)i + 2]};
+                for (int e = lane; e < keep; e += 32) {
+                    const unsigned long long key = keys[e];
+                    const int j = (int)(key >> 24);
+                    const int sp = (int)(key & 0xffffffull);
+                    const int s[3] = {key_s(sp, 0), key_s(sp, 1), key_s(sp, 2)};
+                    const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1], a.pos[3 * (size_t)j + 2]};
+                    double dd[3];
+                    exact_r2(xi, xj, D.H, s, dd);
+                    rbuf[3 * e] = (T)dd[0];
+                    rbuf[3 * e + 1] = (T)dd[1];
+                    rbuf[3 * e + 2] = (T)dd[2];
+                }
+            } else {
+                const float4 pih = a.wp[2 * (size_t)i], pil = a.wp[2 * (size_t)i + 1];
+                for (int e = lane; e < keep; e += 32) {
+                    const unsigned long long key = keys[e];
+                    const int j = (int)(key >> 24);
+                    const int sp = (int)(key & 0xffffffull);
+                    const int wj = a.atom_wrap[j];
+                    // image shift relative to the wrapped positions: t = s + w_j - w_i
+                    const float t[3] = {(float)(key_s(sp, 0) + unpack(wj, 0) - unpack(wi, 0)),
+                                        (float)(key_s(sp, 1) + unpack(wj, 1) - unpack(wi, 1)),
+                                        (float)(key_s(sp, 2) + unpack(wj, 2) - unpack(wi, 2))};
+                    const float4 pjh = a.wp[2 * (size_t)j], pjl = a.wp[2 * (size_t)j + 1];
+                    const float jh[3] = {pjh.x, pjh.y, pjh.z}, jl[3] = {pjl.x, pjl.y, pjl.z};
+                    const float ih[3] = {pih.x, pih.y, pih.z}, il[3] = {pil.x, pil.y, pil.z};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        DF d = df_add({jh[c], jl[c]}, {-ih[c], -il[c]});
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            if (t[q] != 0.f) d = df_add(d, df_scale(t[q], D.hhi[3 * q + c], D.hlo[3 * q + c]));
+                        rbuf[3 * e + c] = (T)__fadd_rn(d.hi, d.lo);
+                    }
+                }
+            }
+            __syncwarp();
+            // 3. canonical order (j, s) by rank (keys are distinct), written in slot-major layout and
+            //    atom-major for the reverse-pair search; each pass ranks two keys per lane
+            for (int e0 = 0; e0 < keep; e0 += 64) {
+                const int ea = e0 + lane, eb = e0 + 32 + lane;
+                const unsigned long long ka = ea < keep ? keys[ea] : ~0ull, kb = eb < keep ? keys[eb] : ~0ull;
+                int ra = 0, rb = 0;
+                for (int f = 0; f < keep; ++f) {
+                    const unsigned long long kf = keys[f];
+                    ra += kf < ka ? 1 : 0;
+                    rb += kf < kb ? 1 : 0;
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const unsigned ball = __ballot_sync(0xffffffffu, acc2[h]);
-                    if (acc2[h]) {
-                        const int pos_ = cnt + __popc(ball & ((1u << lane) - 1u));
-                        if (pos_ < a.cap)
-                            keys[pos_] = ((unsigned long long)jj[h] << 24) |
-                                         (unsigned long long)(((svv[h][0] + 128) << 16) | ((svv[h][1] + 128) << 8) |
-                                                              (svv[h][2] + 128));
-                    }
-                    cnt += __popc(ball);
+                    const int e = h ? eb : ea;
+                    if (e >= keep) continue;
+                    const unsigned long long key = h ? kb : ka;
+                    const int rank = h ? rb : ra;
+                    const int j = (int)(key >> 24);
+                    const size_t o = (size_t)rank * n + i;
+                    int tj = a.types[j];
+                    tj = tj < 0 ? 0 : (tj >= a.S ? a.S - 1 : tj);  // invalid species are reported by k_bin_atoms
+                    a.jz[o] = j | (tj << 24);
+                    a.shift[o] = (int)(key & 0xffffffull);
+                    a.keys_am[(size_t)i * a.cap + rank] = key;
+                    RX[o] = rbuf[3 * e];
+                    RY[o] = rbuf[3 * e + 1];
+                    RZ[o] = rbuf[3 * e + 2];
                 }
             }
+            if (lane == 0) a.count[i] = keep;
+            __syncwarp();
         }
-        __syncwarp();
-        int keep = cnt;
-        if (cnt > a.cap) {
-            keep = a.cap;
-            if (lane == 0) {
-                atomicOr(a.err, kErrOverflow);
-                atomicMax(a.max_seen, cnt);
-            }
-        } else if (lane == 0) {
-            atomicMax(a.max_seen, cnt);
-        }
-        // 2. r_ij of the accepted pairs, one pair per lane: exact double precision for the double
-        //    path, double-float arithmetic (then one rounding) for the float path
-        if (sizeof(T) == 8) {
-            const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1], a.pos[3 * (size_t)i + 2]};
-            for (int e = lane; e < keep; e += 32) {
-                const unsigned long long key = keys[e];
-                const int j = (int)(key >> 24);
-                const int s[3] = {(int)((key >> 16) & 255) - 128, (int)((key >> 8) & 255) - 128, (int)(key & 255) - 128};
-                const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1], a.pos[3 * (size_t)j + 2]};
-                double dd[3];
-                exact_r2(xi, xj, D.H, s, dd);
-                rbuf[3 * e] = (T)dd[0];
-                rbuf[3 * e + 1] = (T)dd[1];
-                rbuf[3 * e + 2] = (T)dd[2];
-            }
-        } else {
-            const float4 pih = a.wp[2 * (size_t)i], pil = a.wp[2 * (size_t)i + 1];
-            for (int e = lane; e < keep; e += 32) {
-                const unsigned long long key = keys[e];
-                const int j = (int)(key >> 24);
-                const int wj = a.atom_wrap[j];
-                // image shift relative to the wrapped positions: t = s + w_j - w_i
-                const float t[3] = {(float)((int)((key >> 16) & 255) - 128 + unpack(wj, 0) - unpack(wi, 0)),
-                                    (float)((int)((key >> 8) & 255) - 128 + unpack(wj, 1) - unpack(wi, 1)),
-                                    (float)((int)(key & 255) - 128 + unpack(wj, 2) - unpack(wi, 2))};
-                const float4 pjh = a.wp[2 * (size_t)j], pjl = a.wp[2 * (size_t)j + 1];
-                const float jh[3] = {pjh.x, pjh.y, pjh.z}, jl[3] = {pjl.x, pjl.y, pjl.z};
-                const float ih[3] = {pih.x, pih.y, pih.z}, il[3] = {pil.x, pil.y, pil.z};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    DF d = df_add({jh[c], jl[c]}, {-ih[c], -il[c]});
-#pragma unroll
-                    for (int q = 0; q < 3; ++q)
-                        if (t[q] != 0.f) d = df_add(d, df_scale(t[q], D.hhi[3 * q + c], D.hlo[3 * q + c]));
-                    rbuf[3 * e + c] = (T)__fadd_rn(d.hi, d.lo);
-                }
-            }
-        }
-        __syncwarp();
-        // 3. canonical order (j, s) by rank, written in slot-major layout
-        const size_t n = (size_t)a.n;
-        for (int e = lane; e < keep; e += 32) {
-            const unsigned long long key = keys[e];
-            int rank = 0;
-            for (int f = 0; f < keep; ++f) rank += keys[f] < key ? 1 : 0;
-            const int j = (int)(key >> 24);
-            const size_t o = (size_t)rank * n + i;
-            int tj = a.types[j];
-            tj = tj < 0 ? 0 : (tj >= a.S ? a.S - 1 : tj);  // invalid species are reported by k_bin_atoms
-            a.jz[o] = j | (tj << 24);
-            a.shift[o] = (int)(key & 0xffffffull);
-            RX[o] = rbuf[3 * e];
-            RY[o] = rbuf[3 * e + 1];
-            RZ[o] = rbuf[3 * e + 2];
-        }
-        if (lane == 0) a.count[i] = keep;
-        __syncwarp();
+        __syncthreads();  // the next bin stages over these candidates
     }
+    if (threadIdx.x == 0 && smax > 0) atomicMax(a.max_seen, smax);
 }
 
-// one thread per (slot, atom): binary search of the reverse pair (i, -s) in the neighbour's list
-__global__ void k_reverse(int n, int cap, const int* count, const int* jz, const int* shift, int* rev) {
+// one thread per (slot, atom): binary search of the reverse pair (i, -s) in the neighbour's sorted
+// keys, stored atom-major so that one search stays within a few cache lines
+__global__ void k_reverse(int n, int cap, const int* count, const int* jz, const int* shift,
+                          const unsigned long long* keys_am, int* rev) {
     const size_t N = (size_t)n;
     const size_t total = N * (size_t)cap;
     for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < total; o += (size_t)gridDim.x * blockDim.x) {
@@ -417,12 +495,11 @@ __global__ void k_reverse(int n, int cap, const int* count, const int* jz, const
         const int neg = ((256 - (sp & 255)) & 255) | (((256 - ((sp >> 8) & 255)) & 255) << 8) |
                         (((256 - ((sp >> 16) & 255)) & 255) << 16);
         const unsigned long long want = ((unsigned long long)i << 24) | (unsigned long long)neg;
+        const unsigned long long* kj = keys_am + (size_t)j * cap;
         int lo = 0, hi = count[j] - 1, found = -1;
         while (lo <= hi) {
             const int mid = (lo + hi) >> 1;
-            const size_t om = (size_t)mid * N + j;
-            const unsigned long long key = ((unsigned long long)(jz[om] & 0xffffff) << 24) |
-                                           (unsigned long long)(shift[om] & 0xffffff);
+            const unsigned long long key = kj[mid];
             if (key == want) {
                 found = mid;
                 break;
@@ -548,7 +625,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     const size_t realsz = fp64 ? 8 : 4;
     const size_t bins_max = N + K + 1;
     if (nb.count.reserve(N * 4) || nb.jz.reserve(N * cap * 4) || nb.shift.reserve(N * cap * 4) ||
-        nb.rev.reserve(N * cap * 4) || nb.rx.reserve(N * cap * realsz) || nb.ry.reserve(N * cap * realsz) ||
+        nb.rev.reserve(N * cap * 4) || nb.keys_am.reserve(N * cap * 8) || nb.rx.reserve(N * cap * realsz) || nb.ry.reserve(N * cap * realsz) ||
         nb.rz.reserve(N * cap * realsz) || nb.cfg_of.reserve(N * 4) || nb.desc.reserve(sizeof(CellDesc) * K) ||
         nb.atom_bin.reserve(N * 4) || nb.atom_wrap.reserve(N * 4) || nb.atom_local.reserve(N * 16) || nb.atom_wp.reserve(N * 32) ||
         nb.bin_count.reserve(bins_max * 4) || nb.bin_start.reserve((bins_max + 1) * 4) ||
@@ -578,13 +655,13 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     const int total_bins_upper = n + K;  // every configuration has at most max(1, atoms) bins
     cudaMemsetAsync(bin_count, 0, (size_t)(total_bins_upper + 1) * 4, st);
     cudaMemsetAsync(nb.bin_fill.p, 0, (size_t)(total_bins_upper + 1) * 4, st);
-    k_bin_atoms<<<(n + 255) / 256, 256, 0, st>>>(n, K, pos, types, S, cfg_off, desc, nb.cfg_of.as<int>(),
+    k_bin_atoms<<<(n + 63) / 64, 64, 0, st>>>(n, K, pos, types, S, cfg_off, desc, nb.cfg_of.as<int>(),
                                                 nb.atom_bin.as<int>(), nb.atom_wrap.as<int>(),
                                                 nb.atom_local.as<float4>(), nb.atom_wp.as<float4>(), bin_count,
                                                 nb.err.as<int>());
     ++launches;
     launches += scan_exclusive(bin_count, bin_start, total_bins_upper, tmp, st);
-    k_bin_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, nb.atom_bin.as<int>(), bin_start, nb.bin_fill.as<int>(),
+    k_bin_scatter<<<(n + 63) / 64, 64, 0, st>>>(n, nb.atom_bin.as<int>(), bin_start, nb.bin_fill.as<int>(),
                                                   nb.bin_atoms.as<int>());
     ++launches;
     BuildArgs a;
@@ -607,15 +684,18 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     a.count = nb.count.as<int>();
     a.jz = nb.jz.as<int>();
     a.shift = nb.shift.as<int>();
+    a.keys_am = nb.keys_am.as<unsigned long long>();
     a.rx = nb.rx.p;
     a.ry = nb.ry.p;
     a.rz = nb.rz.p;
     a.err = nb.err.as<int>();
     a.max_seen = nb.max_seen.as<int>();
-    const int threads = 128, wpb = threads / 32;
-    const size_t smem = (size_t)wpb * cap * (8 + 3 * realsz);
-    int blocks = (n + wpb - 1) / wpb;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    a.nbins = total_bins_upper;
+    const size_t smem = build_smem(cap, realsz);
+    const int per_sm = (int)std::min<size_t>(8, (200 * 1024) / smem);
+    int blocks = std::min(total_bins_upper, 152 * std::max(per_sm, 1));
+    if (blocks < 1) blocks = 1;
+    const int threads = kBuildThreads;
     static int attr64 = 0, attr32 = 0;  // largest dynamic shared memory already allowed
     if (fp64) {
         if ((int)smem > attr64) {
@@ -636,7 +716,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
         size_t blocks = (total + 255) / 256;
         if (blocks > 152 * 64) blocks = 152 * 64;
         k_reverse<<<(int)blocks, 256, 0, st>>>(n, cap, nb.count.as<int>(), nb.jz.as<int>(), nb.shift.as<int>(),
-                                              nb.rev.as<int>());
+                                              nb.keys_am.as<unsigned long long>(), nb.rev.as<int>());
     }
     ++launches;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
