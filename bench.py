@@ -50,16 +50,17 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2007_08555_gb300 import ranks
+
+    return ranks.env()
 
 
 def make_inputs(lev, reps, seed_offset=0):
     from paper_2007_08555_gb300 import codegen, synth
 
-    cfg = synth.fcc_binary(reps=reps, seed=2 + seed_offset)
+    from paper_2007_08555_gb300 import ranks
+
+    cfg = synth.fcc_binary(reps=reps, seed=ranks.replica_seed(2, seed_offset))
     m = codegen.build_basis(lev).m
     p = synth.random_params(lev, 2, 8, 2.0, 5.0, m, seed=2)
     return cfg, p
@@ -116,7 +117,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2007_08555_gb300 import flops, mtp
+    from paper_2007_08555_gb300 import flops, mtp, ranks
 
     rank, world, local = dist_env()
     if world > 1:
@@ -173,11 +174,8 @@ def run_ours(args):
     phase_ms, calls = mtp.mtp_profile_read(model.h)
     mtp.mtp_profile(model.h, False)
     ms = float(np.mean(times))
-    t_tot = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_tot, op=dist.ReduceOp.MAX)
-    ms_max = float(t_tot.item())
-    value = world * n / (ms_max * 1e-3)
+    ms_max = ranks.max_over_ranks(ms, device=dev)  # replicas: the slowest rank sets the job's time
+    value = ranks.job_throughput(ranks.sum_over_ranks(n, device=dev), ms_max)
     if args.profile_run:
         if rank == 0:
             print(json.dumps({"profile_run": True, "value": round(value, 1), "ms_per_step": ms_max,

@@ -338,7 +338,7 @@ void mtp_destroy(mtp_model* M) {
                       &M->s_energy, &M->s_forces, &M->s_virial, &M->s_site, &M->s_brows, &M->s_batoms,
                       &M->nb.count, &M->nb.jz, &M->nb.shift, &M->nb.rev, &M->nb.rx, &M->nb.ry, &M->nb.rz,
                       &M->nb.cfg_of, &M->nb.desc, &M->nb.atom_bin, &M->nb.atom_wrap, &M->nb.atom_local,
-                      &M->nb.bin_count, &M->nb.bin_start, &M->nb.bin_fill, &M->nb.bin_atoms, &M->nb.scan_tmp,
+                      &M->nb.bin_count, &M->nb.bin_start, &M->nb.bin_fill, &M->nb.bin_atoms, &M->nb.counters,
                       &M->nb.err, &M->nb.max_seen, &M->g_energy, &M->g_forces, &M->g_virial, &M->g_D, &M->g_eps, &M->g_ew,
                       &M->g_momt, &M->g_adjmt, &M->g_out, &M->g_refs, &M->md_F, &M->md_scalars, &M->md_masses,
                       &M->md_flag, &M->nb.x0, &M->nb.cx, &M->nb.cy, &M->nb.cz, &M->d_A, &M->d_Ai, &M->mv_Bs, &M->mv_D, &M->mv_W, &M->mv_perm, &M->mv_sel,

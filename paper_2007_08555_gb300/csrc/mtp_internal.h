@@ -34,6 +34,7 @@ struct CellDesc {
     double H[9], Hi[9];
     float hn[9];  // lattice vectors divided by the bin counts, rows
     float hhi[9], hlo[9];  // lattice vectors as float pairs (hi + lo = H to ~2^-48)
+    double inv_n[3];
     int n[3], c[3];
     int bin0, nbins;
 };
@@ -44,7 +45,7 @@ struct NbrState {
     bool fp64 = false;
     double rsearch = 0.0;
     DevBuf count, jz, shift, rev, rx, ry, rz, keys_am;
-    DevBuf cfg_of, desc, atom_bin, atom_wrap, atom_local, atom_wp, bin_count, bin_start, bin_fill, bin_atoms, scan_tmp;
+    DevBuf cfg_of, desc, atom_bin, atom_wrap, atom_local, atom_wp, bin_count, bin_start, bin_fill, bin_atoms, counters;
     DevBuf err, max_seen;
     // reuse with a skin: positions at the build and the current displacements (float or double)
     DevBuf x0, cx, cy, cz;

@@ -41,7 +41,7 @@ __device__ __forceinline__ int find_cfg(const int* cfg_off, int K, int i) {
 
 // Per-configuration geometry: inverse cell, perpendicular widths, bin counts and reach.
 __global__ void k_cells(int K, const double* cells, const int* cfg_off, double rsearch, CellDesc* d,
-                        int* nbins, int* err) {
+                        int* bin_total, int* err) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     CellDesc D;
@@ -85,6 +85,7 @@ __global__ void k_cells(int K, const double* cells, const int* cfg_off, double r
         }
         D.c[q] = cq;
         const double inq = 1.0 / D.n[q];
+        D.inv_n[q] = inq;
         for (int t = 0; t < 3; ++t) {
             D.hn[3 * q + t] = (float)(H[3 * q + t] * inq);
             const float hi = (float)H[3 * q + t];
@@ -93,14 +94,10 @@ __global__ void k_cells(int K, const double* cells, const int* cfg_off, double r
         }
     }
     D.nbins = D.n[0] * D.n[1] * D.n[2];
-    D.bin0 = 0;
+    // each configuration's bins are one contiguous range; where it lies depends on the order of
+    // the atomics, which changes nothing downstream (lists are sorted by (j, s))
+    D.bin0 = atomicAdd(bin_total, D.nbins);
     d[k] = D;
-    nbins[k] = D.nbins;
-}
-
-__global__ void k_cells_offsets(int K, const int* bin0, CellDesc* d) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < K) d[k].bin0 = bin0[k];
 }
 
 __global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, int S, const int* cfg_off,
@@ -124,7 +121,7 @@ __global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, i
         if (bq < 0) bq = 0;
         if (bq >= D.n[q]) bq = D.n[q] - 1;
         b[q] = bq;
-        frac[q] = (double)w[q] + (double)bq / (double)D.n[q];
+        frac[q] = (double)w[q] + (double)bq * D.inv_n[q];  // bin origin: only the float prefilter uses it
         if (w[q] > kMaxShift || w[q] < -kMaxShift) atomicOr(err, kErrShift);
     }
     double o[3], xw[3];
@@ -141,6 +138,26 @@ __global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, i
     atom_bin[i] = bin;
     atom_wrap[i] = ((w[0] + 128) & 255) | (((w[1] + 128) & 255) << 8) | (((w[2] + 128) & 255) << 16);
     atomicAdd(&bin_count[bin], 1);
+}
+
+// Start of every non-empty bin in bin_atoms: one atomic per warp on the running total (the
+// placement order is irrelevant downstream, see k_cells).
+__global__ void k_alloc_bins(int nbins, const int* bin_count, int* bin_start, int* atom_total) {
+    const int lane = threadIdx.x & 31;
+    for (int b0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; b0 < nbins; b0 += gridDim.x * blockDim.x) {
+        const int b = b0 + lane;
+        const int c = b < nbins ? bin_count[b] : 0;
+        int incl = c;
+#pragma unroll
+        for (int sh = 1; sh < 32; sh <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, sh);
+            if (lane >= sh) incl += y;
+        }
+        int base = 0;
+        if (lane == 31) base = atomicAdd(atom_total, incl);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        if (b < nbins) bin_start[b] = base + incl - c;
+    }
 }
 
 __global__ void k_bin_scatter(int n, const int* atom_bin, const int* bin_start, int* bin_fill, int* bin_atoms) {
@@ -179,6 +196,7 @@ struct BuildArgs {
     const float4* local;
     const float4* wp;
     const int* bin_start;
+    const int* bin_count;
     const int* bin_atoms;
     int* count;
     int* jz;
@@ -227,7 +245,7 @@ constexpr int kBias3 = 0x808080;  // three zero components
 // then per warp the accepted keys and their r_ij.
 constexpr int kBuildThreads = 128, kBuildWarps = kBuildThreads / 32;
 constexpr int kGroup = kBuildThreads;  // neighbour bins described per staging round
-constexpr int kChunk = 1024;           // candidates staged per round
+constexpr int kChunk = 512;            // candidates staged per round
 constexpr size_t kSmCpos = 0;
 constexpr size_t kSmCshift = kSmCpos + sizeof(float4) * kChunk;
 constexpr size_t kSmGpre = kSmCshift + sizeof(int) * kChunk;
@@ -265,8 +283,9 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
     if (threadIdx.x == 0) smax = 0;
     __syncthreads();
     for (int bin = blockIdx.x; bin < a.nbins; bin += gridDim.x) {
-        const int start = a.bin_start[bin], nat = a.bin_start[bin + 1] - start;
+        const int nat = a.bin_count[bin];
         if (nat == 0) continue;
+        const int start = a.bin_start[bin];
         const int k = a.cfg_of[a.bin_atoms[start]];
         const CellDesc& D = a.desc[k];
         const int lb = bin - D.bin0;
@@ -305,7 +324,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                         oz = o0 * D.hn[2] + o1 * D.hn[5] + o2 * D.hn[8];
                         const int nbin = D.bin0 + (w0 * D.n[1] + w1) * D.n[2] + w2;
                         bstart = a.bin_start[nbin];
-                        bcnt = a.bin_start[nbin + 1] - bstart;
+                        bcnt = a.bin_count[nbin];
                     }
                     int incl = bcnt;
 #pragma unroll
@@ -354,41 +373,51 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                         __syncthreads();
                     }
                     if (has) {
-                        // 1c. float prefilter on the staged candidates; only the rare pairs within
-                        //     1e-3 Angstrom of the cutoff take the double-precision decision
-                        for (int e0 = 0; e0 < m; e0 += 32) {
-                            const int e = e0 + lane;
-                            bool acc = false;
-                            unsigned long long key = 0;
-                            if (e < m) {
-                                const float4 cp = cpos[e];
-                                const float dx = cp.x - li.x, dy = cp.y - li.y, dz = cp.z - li.z;
-                                const float r2 = dx * dx + dy * dy + dz * dz;
-                                if (r2 <= a.hi2) {
-                                    const int j = __float_as_int(cp.w);
-                                    const int ks = cshift[e] + wik;  // key-order shift s
-                                    if (!(j == i && ks == kBias3)) {
-                                        if (r2 < a.lo2) {
-                                            acc = true;
-                                        } else {
-                                            const int sv[3] = {key_s(ks, 0), key_s(ks, 1), key_s(ks, 2)};
-                                            const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1],
-                                                                  a.pos[3 * (size_t)i + 2]};
-                                            const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1],
-                                                                  a.pos[3 * (size_t)j + 2]};
-                                            double dd[3];
-                                            acc = exact_r2(xi, xj, D.H, sv, dd) < a.rs2;
-                                        }
-                                        key = ((unsigned long long)j << 24) | (unsigned long long)ks;
-                                    }
-                                }
+                        // 1c. float prefilter on the staged candidates, two per lane per round (their
+                        //     shared-memory loads overlap); only the rare pairs within 1e-3 Angstrom of
+                        //     the cutoff take the double-precision decision
+                        auto test = [&](int e, bool& acc, unsigned long long& key) {
+                            acc = false;
+                            key = 0;
+                            if (e >= m) return;
+                            const float4 cp = cpos[e];
+                            const float dx = cp.x - li.x, dy = cp.y - li.y, dz = cp.z - li.z;
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 > a.hi2) return;
+                            const int j = __float_as_int(cp.w);
+                            const int ks = cshift[e] + wik;  // key-order shift s
+                            if (j == i && ks == kBias3) return;
+                            if (r2 < a.lo2) {
+                                acc = true;
+                            } else {
+                                const int sv[3] = {key_s(ks, 0), key_s(ks, 1), key_s(ks, 2)};
+                                const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1],
+                                                      a.pos[3 * (size_t)i + 2]};
+                                const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1],
+                                                      a.pos[3 * (size_t)j + 2]};
+                                double dd[3];
+                                acc = exact_r2(xi, xj, D.H, sv, dd) < a.rs2;
                             }
-                            const unsigned ball = __ballot_sync(0xffffffffu, acc);
-                            if (acc) {
-                                const int pos_ = cnt + __popc(ball & ((1u << lane) - 1u));
-                                if (pos_ < a.cap) keys[pos_] = key;
+                            key = ((unsigned long long)j << 24) | (unsigned long long)ks;
+                        };
+                        for (int e0 = 0; e0 < m; e0 += 64) {
+                            bool acc0, acc1;
+                            unsigned long long key0, key1;
+                            test(e0 + lane, acc0, key0);
+                            test(e0 + 32 + lane, acc1, key1);
+                            const unsigned b0 = __ballot_sync(0xffffffffu, acc0);
+                            const unsigned b1 = __ballot_sync(0xffffffffu, acc1);
+                            const unsigned below = (1u << lane) - 1u;
+                            if (acc0) {
+                                const int pos_ = cnt + __popc(b0 & below);
+                                if (pos_ < a.cap) keys[pos_] = key0;
                             }
-                            cnt += __popc(ball);
+                            cnt += __popc(b0);
+                            if (acc1) {
+                                const int pos_ = cnt + __popc(b1 & below);
+                                if (pos_ < a.cap) keys[pos_] = key1;
+                            }
+                            cnt += __popc(b1);
                         }
                     }
                     if (!reuse) __syncthreads();  // the next staging round overwrites the candidates
@@ -449,6 +478,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                 const int ea = e0 + lane, eb = e0 + 32 + lane;
                 const unsigned long long ka = ea < keep ? keys[ea] : ~0ull, kb = eb < keep ? keys[eb] : ~0ull;
                 int ra = 0, rb = 0;
+#pragma unroll 4
                 for (int f = 0; f < keep; ++f) {
                     const unsigned long long kf = keys[f];
                     ra += kf < ka ? 1 : 0;
@@ -630,7 +660,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
         nb.atom_bin.reserve(N * 4) || nb.atom_wrap.reserve(N * 4) || nb.atom_local.reserve(N * 16) || nb.atom_wp.reserve(N * 32) ||
         nb.bin_count.reserve(bins_max * 4) || nb.bin_start.reserve((bins_max + 1) * 4) ||
         nb.bin_fill.reserve(bins_max * 4) || nb.bin_atoms.reserve(N * 4 + 4) ||
-        nb.scan_tmp.reserve(4 * (scan_tmp_ints((int)bins_max) + scan_tmp_ints(K + 1) + 16)) ||
+        nb.counters.reserve(16) ||
         nb.err.reserve(4) || nb.max_seen.reserve(4))
         return -1;
     nb.n_atoms = n;
@@ -641,17 +671,11 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     CellDesc* desc = nb.desc.as<CellDesc>();
     int* bin_count = nb.bin_count.as<int>();
     int* bin_start = nb.bin_start.as<int>();
-    int* tmp = nb.scan_tmp.as<int>();
-    // bins per configuration -> offsets (reuse bin_fill as scratch for the per-config counts)
-    int* cfg_bins = nb.bin_fill.as<int>();
-    k_cells<<<(K + 127) / 128, 128, 0, st>>>(K, cells, cfg_off, rsearch, desc, cfg_bins, nb.err.as<int>());
+    // counters: [0] bins handed out to configurations, [1] atoms handed out to bins
+    int* counters = nb.counters.as<int>();
+    cudaMemsetAsync(counters, 0, 2 * sizeof(int), st);
+    k_cells<<<(K + 127) / 128, 128, 0, st>>>(K, cells, cfg_off, rsearch, desc, counters, nb.err.as<int>());
     ++launches;
-    if (K > 1) {  // a single configuration starts at bin 0: no offsets to compute
-        int* cfg_bin0 = nb.bin_start.as<int>();  // temporary: K+1 ints
-        launches += scan_exclusive(cfg_bins, cfg_bin0, K, tmp, st);
-        k_cells_offsets<<<(K + 127) / 128, 128, 0, st>>>(K, cfg_bin0, desc);
-        ++launches;
-    }
     const int total_bins_upper = n + K;  // every configuration has at most max(1, atoms) bins
     cudaMemsetAsync(bin_count, 0, (size_t)(total_bins_upper + 1) * 4, st);
     cudaMemsetAsync(nb.bin_fill.p, 0, (size_t)(total_bins_upper + 1) * 4, st);
@@ -660,7 +684,12 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
                                                 nb.atom_local.as<float4>(), nb.atom_wp.as<float4>(), bin_count,
                                                 nb.err.as<int>());
     ++launches;
-    launches += scan_exclusive(bin_count, bin_start, total_bins_upper, tmp, st);
+    {
+        int blocks = (total_bins_upper + 255) / 256;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        k_alloc_bins<<<blocks, 256, 0, st>>>(total_bins_upper, bin_count, bin_start, counters + 1);
+        ++launches;
+    }
     k_bin_scatter<<<(n + 63) / 64, 64, 0, st>>>(n, nb.atom_bin.as<int>(), bin_start, nb.bin_fill.as<int>(),
                                                   nb.bin_atoms.as<int>());
     ++launches;
@@ -680,6 +709,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     a.local = nb.atom_local.as<float4>();
     a.wp = nb.atom_wp.as<float4>();
     a.bin_start = bin_start;
+    a.bin_count = bin_count;
     a.bin_atoms = nb.bin_atoms.as<int>();
     a.count = nb.count.as<int>();
     a.jz = nb.jz.as<int>();
@@ -692,7 +722,8 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     a.max_seen = nb.max_seen.as<int>();
     a.nbins = total_bins_upper;
     const size_t smem = build_smem(cap, realsz);
-    const int per_sm = (int)std::min<size_t>(8, (200 * 1024) / smem);
+    // one block per bin when they fit in one wave (a perturbed lattice has ~12 atoms per bin)
+    const int per_sm = (int)std::min<size_t>(12, (220 * 1024) / (smem + 1024));
     int blocks = std::min(total_bins_upper, 152 * std::max(per_sm, 1));
     if (blocks < 1) blocks = 1;
     const int threads = kBuildThreads;
@@ -700,12 +731,16 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     if (fp64) {
         if ((int)smem > attr64) {
             cudaFuncSetAttribute(k_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_build<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
             attr64 = (int)smem;
         }
         k_build<double><<<blocks, threads, smem, st>>>(a);
     } else {
         if ((int)smem > attr32) {
             cudaFuncSetAttribute(k_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_build<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
             attr32 = (int)smem;
         }
         k_build<float><<<blocks, threads, smem, st>>>(a);
