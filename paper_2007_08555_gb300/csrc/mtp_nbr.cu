@@ -292,6 +292,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
         const int b2 = lb % D.n[2], b1 = (lb / D.n[2]) % D.n[1], b0 = lb / (D.n[2] * D.n[1]);
         const int ny = 2 * D.c[1] + 1, nz = 2 * D.c[2] + 1;
         const int n_off = (2 * D.c[0] + 1) * ny * nz;
+        // the visited bins are distinct (no bin seen through two images): each j is a candidate once
+        const bool uniq = D.n[0] > 2 * D.c[0] && D.n[1] > 2 * D.c[1] && D.n[2] > 2 * D.c[2];
         bool reuse = false;  // the previous group of atoms left every candidate staged
         int total = 0;
         for (int ab = 0; ab < nat; ab += kBuildWarps) {
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                                 double dd[3];
                                 acc = exact_r2(xi, xj, D.H, sv, dd) < a.rs2;
                             }
-                            key = ((unsigned long long)j << 24) | (unsigned long long)ks;
+                            key = ((unsigned long long)j << 32) | (unsigned long long)ks;
                         };
                         for (int e0 = 0; e0 < m; e0 += 64) {
                             bool acc0, acc1;
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                 const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1], a.pos[3 * (size_t)i + 2]};
                 for (int e = lane; e < keep; e += 32) {
                     const unsigned long long key = keys[e];
-                    const int j = (int)(key >> 24);
+                    const int j = (int)(key >> 32);
                     const int sp = (int)(key & 0xffffffull);
                     const int s[3] = {key_s(sp, 0), key_s(sp, 1), key_s(sp, 2)};
                     const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1], a.pos[3 * (size_t)j + 2]};
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                 const float4 pih = a.wp[2 * (size_t)i], pil = a.wp[2 * (size_t)i + 1];
                 for (int e = lane; e < keep; e += 32) {
                     const unsigned long long key = keys[e];
-                    const int j = (int)(key >> 24);
+                    const int j = (int)(key >> 32);
                     const int sp = (int)(key & 0xffffffull);
                     const int wj = a.atom_wrap[j];
                     // image shift relative to the wrapped positions: t = s + w_j - w_i
@@ -478,11 +480,22 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                 const int ea = e0 + lane, eb = e0 + 32 + lane;
                 const unsigned long long ka = ea < keep ? keys[ea] : ~0ull, kb = eb < keep ? keys[eb] : ~0ull;
                 int ra = 0, rb = 0;
+                if (uniq) {  // every j once: its index alone orders the keys (the high words)
+                    const unsigned ja = (unsigned)(ka >> 32), jb = (unsigned)(kb >> 32);
+                    const unsigned* kh = reinterpret_cast<const unsigned*>(keys) + 1;
 #pragma unroll 4
-                for (int f = 0; f < keep; ++f) {
-                    const unsigned long long kf = keys[f];
-                    ra += kf < ka ? 1 : 0;
-                    rb += kf < kb ? 1 : 0;
+                    for (int f = 0; f < keep; ++f) {
+                        const unsigned jf = kh[2 * f];
+                        ra += jf < ja ? 1 : 0;
+                        rb += jf < jb ? 1 : 0;
+                    }
+                } else {
+#pragma unroll 4
+                    for (int f = 0; f < keep; ++f) {
+                        const unsigned long long kf = keys[f];
+                        ra += kf < ka ? 1 : 0;
+                        rb += kf < kb ? 1 : 0;
+                    }
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -490,7 +503,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                     if (e >= keep) continue;
                     const unsigned long long key = h ? kb : ka;
                     const int rank = h ? rb : ra;
-                    const int j = (int)(key >> 24);
+                    const int j = (int)(key >> 32);
                     const size_t o = (size_t)rank * n + i;
                     int tj = a.types[j];
                     tj = tj < 0 ? 0 : (tj >= a.S ? a.S - 1 : tj);  // invalid species are reported by k_bin_atoms
@@ -524,7 +537,7 @@ __global__ void k_reverse(int n, int cap, const int* count, const int* jz, const
         const int sp = shift[o];
         const int neg = ((256 - (sp & 255)) & 255) | (((256 - ((sp >> 8) & 255)) & 255) << 8) |
                         (((256 - ((sp >> 16) & 255)) & 255) << 16);
-        const unsigned long long want = ((unsigned long long)i << 24) | (unsigned long long)neg;
+        const unsigned long long want = ((unsigned long long)i << 32) | (unsigned long long)neg;
         const unsigned long long* kj = keys_am + (size_t)j * cap;
         int lo = 0, hi = count[j] - 1, found = -1;
         while (lo <= hi) {
