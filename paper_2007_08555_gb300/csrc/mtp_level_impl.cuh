@@ -72,6 +72,36 @@ __device__ __forceinline__ Df df_mulf(Df a, float b) {
 }
 __device__ __forceinline__ Df df_neg(Df a) { return {-a.hi, -a.lo}; }
 
+// Radial coefficients in shared memory: per ordered species pair a block [b][mu] with mu padded to
+// a whole vector (4 floats or 2 doubles), so that the N_mu coefficients of one Chebyshev order come
+// in one or two vector loads.
+template <class T>
+struct CoefPad {
+    static constexpr int value = sizeof(T) == 4 ? ((G::NMU_ + 3) & ~3) : ((G::NMU_ + 1) & ~1);
+};
+
+template <class T>
+__device__ __forceinline__ void coefs_at(const T* __restrict__ cz, int b, T* out) {
+    constexpr int P = CoefPad<T>::value;
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < P / 4; ++k) {
+            const float4 v = reinterpret_cast<const float4*>(cz + b * P)[k];
+            out[4 * k] = v.x;
+            out[4 * k + 1] = v.y;
+            out[4 * k + 2] = v.z;
+            out[4 * k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < P / 2; ++k) {
+            const double2 v = reinterpret_cast<const double2*>(cz + b * P)[k];
+            out[2 * k] = v.x;
+            out[2 * k + 1] = v.y;
+        }
+    }
+}
+
 // The radial functions (Eq. 3) and their derivatives in double-float arithmetic, rounded to float at
 // the end: below R_min the Chebyshev polynomials leave [-1, 1] and grow, and their float sum loses
 // the digits that this evaluation keeps.
@@ -87,9 +117,11 @@ __device__ __forceinline__ void radial_df(const float r, const float* __restrict
     const Df x = df_add({q, 0.f}, {rem.hi / span.hi, 0.f});
     const Df x2 = {2.f * x.hi, 2.f * x.lo};
     Df F[NMU], D[NMU];
+    float cb[CoefPad<float>::value];
+    coefs_at(cz, 0, cb);
 #pragma unroll
     for (int mu = 0; mu < NMU; ++mu) {
-        F[mu] = {cz[mu * NQ], 0.f};
+        F[mu] = {cb[mu], 0.f};
         D[mu] = {0.f, 0.f};
     }
     Df t0 = {1.f, 0.f}, t1 = x, d0 = {0.f, 0.f}, d1 = {1.f, 0.f};
@@ -105,10 +137,11 @@ __device__ __forceinline__ void radial_df(const float r, const float* __restrict
                 d1 = db;
             }
         }
+        coefs_at(cz, b, cb);
 #pragma unroll
         for (int mu = 0; mu < NMU; ++mu) {
-            F[mu] = df_add(F[mu], df_mulf(tb, cz[mu * NQ + b]));
-            if (WANT_D) D[mu] = df_add(D[mu], df_mulf(db, cz[mu * NQ + b]));
+            F[mu] = df_add(F[mu], df_mulf(tb, cb[mu]));
+            if (WANT_D) D[mu] = df_add(D[mu], df_mulf(db, cb[mu]));
         }
     }
     // Q = T (R_cut - r)^2;  dQ/dr = T' (2 / span) (R_cut - r)^2 - 2 T (R_cut - r)
@@ -143,27 +176,30 @@ __device__ __forceinline__ void radial(const T r, const T* __restrict__ cz, cons
     }
     const T x = (T(2) * r - rmin - rcut) * inv_span;
     T F[NMU], D[NMU];
+    T cb[CoefPad<T>::value];
+    coefs_at(cz, 0, cb);
 #pragma unroll
     for (int mu = 0; mu < NMU; ++mu) {
-        F[mu] = cz[mu * NQ];
+        F[mu] = cb[mu];
         D[mu] = T(0);
     }
     if (NQ > 1) {
+        coefs_at(cz, 1, cb);
 #pragma unroll
         for (int mu = 0; mu < NMU; ++mu) {
-            F[mu] += cz[mu * NQ + 1] * x;
-            if (WANT_D) D[mu] += cz[mu * NQ + 1];
+            F[mu] += cb[mu] * x;
+            if (WANT_D) D[mu] += cb[mu];
         }
     }
     T t0 = T(1), t1 = x, d0 = T(0), d1 = T(1);
     for (int b = 2; b < NQ; ++b) {
         const T t2 = T(2) * x * t1 - t0;
         const T d2 = T(2) * t1 + T(2) * x * d1 - d0;
+        coefs_at(cz, b, cb);
 #pragma unroll
         for (int mu = 0; mu < NMU; ++mu) {
-            const T cb = cz[mu * NQ + b];
-            F[mu] += cb * t2;
-            if (WANT_D) D[mu] += cb * d2;
+            F[mu] += cb[mu] * t2;
+            if (WANT_D) D[mu] += cb[mu] * d2;
         }
         t0 = t1;
         t1 = t2;
@@ -182,9 +218,20 @@ __device__ __forceinline__ void radial(const T r, const T* __restrict__ cz, cons
 
 template <class T>
 __device__ __forceinline__ void load_c(const EvalCtx<T>& a, T* cs) {
-    const int nc = a.S * a.S * G::NMU_ * a.NQ;
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) cs[k] = a.c[k];
+    // global c[z_i][z_j][mu][b] -> shared [z_i][z_j][b][mu padded]
+    constexpr int P = CoefPad<T>::value;
+    const int nc = a.S * a.S * a.NQ * P;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+        const int mu = k % P, b = (k / P) % a.NQ, pair = k / (P * a.NQ);
+        cs[k] = mu < G::NMU_ ? a.c[((size_t)pair * G::NMU_ + mu) * a.NQ + b] : T(0);
+    }
     __syncthreads();
+}
+
+// bytes of the shared coefficient table
+template <class T>
+size_t coef_bytes(const EvalCtx<T>& a) {
+    return sizeof(T) * (size_t)a.S * a.S * a.NQ * CoefPad<T>::value;
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -199,7 +246,7 @@ __device__ __forceinline__ void moments_slice(const EvalCtx<T>& a, int i, int su
     for (int t = 0; t < SL::SIZE; ++t) acc[t] = T(0);
     const size_t n = (size_t)a.n_atoms;
     if (active) {
-        const int csz = G::NMU_ * a.NQ;
+        const int csz = CoefPad<T>::value * a.NQ;
         for (int p = sub; p < cnt; p += TPA) {
             const size_t idx = (size_t)p * n + i;
             const int zj = a.jz[idx] >> 24;
@@ -477,7 +524,7 @@ __device__ __forceinline__ void pairgrad_slice(const EvalCtx<T>& a, int i, int s
 #pragma unroll
     for (int t = 0; t < SL::SIZE; ++t) adjs[t] = src[(size_t)(SL::BEGIN + t) * 32];
     const size_t n = (size_t)a.n_atoms;
-    const int csz = G::NMU_ * a.NQ;
+    const int csz = CoefPad<T>::value * a.NQ;
     for (int p = sub; p < cnt; p += TPA) {
         const size_t idx = (size_t)p * n + i;
         const int zj = a.jz[idx] >> 24;
@@ -627,7 +674,7 @@ __global__ void __launch_bounds__(128) k_gather(const EvalCtx<T> a) {
 template <class T, int TPA>
 int launch_pairs(const EvalCtx<T>& a, cudaStream_t st, int n_sm, bool moments) {
     const int threads = 128;
-    const size_t cbytes = sizeof(T) * (size_t)a.S * a.S * G::NMU_ * a.NQ;
+    const size_t cbytes = coef_bytes(a);
     const long work = (long)(((a.n_atoms + 31) / 32) * 32) * TPA;
     int blocks = (int)((work + threads - 1) / threads);
     const int max_blocks = n_sm * 16;
@@ -798,7 +845,7 @@ __device__ __forceinline__ void tmom_slice(const EvalCtx<T>& a, int i, int sub, 
     for (int t = 0; t < SL::SIZE; ++t) acc[t] = T(0);
     const size_t n = (size_t)a.n_atoms;
     if (active) {
-        const int csz = G::NMU_ * a.NQ;
+        const int csz = CoefPad<T>::value * a.NQ;
         for (int p = sub; p < cnt; p += TPA) {
             const size_t idx = (size_t)p * n + i;
             const int jz = a.jz[idx];
@@ -1062,7 +1109,7 @@ int launch_grad_pairs(EvalCtx<T>& a, cudaStream_t st, int n_sm) {
     int blocks = (int)((work + threads - 1) / threads);
     if (blocks > n_sm * 16) blocks = n_sm * 16;
     if (blocks < 1) blocks = 1;
-    const size_t cbytes = sizeof(T) * (size_t)a.S * a.S * G::NMU_ * a.NQ;
+    const size_t cbytes = coef_bytes(a);
     k_tmom<T, TPA><<<blocks, threads, cbytes, st>>>(a);
     return 1;
 }
