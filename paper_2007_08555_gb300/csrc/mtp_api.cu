@@ -77,6 +77,7 @@ struct mtp_model {
     cudaStream_t cap_stream = nullptr; // private stream the graph is captured on
     int64_t g_launches = 0;            // kernels in the graph
     int* h_flags = nullptr;            // pinned: error word and largest neighbour count of the last build
+    int tpa_moments = 0, tpa_pairs = 0; // requested threads per atom (0 = chosen per call)
 };
 
 namespace {
@@ -124,8 +125,11 @@ mtp_status status_from_err(int err) {
     return MTP_OK;
 }
 
-int choose_tpa(int n_atoms, int n_sm) {
-    const long want = (long)n_sm * 512;
+// Threads per atom: enough threads for the whole GPU (want per SM), as few lanes per atom as that
+// allows.  The moments kernel reduces every component over its lanes, so it wants fewer lanes than
+// the pair-gradient and gather kernels, which write per pair.
+int choose_tpa(int n_atoms, int n_sm, int per_sm) {
+    const long want = (long)n_sm * per_sm;
     if (n_atoms >= want) return 1;
     if (n_atoms * 2L >= want) return 2;
     if (n_atoms * 4L >= want) return 4;
@@ -175,7 +179,8 @@ mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     a.adj_layers = M->ops->adj_layers;
     a.weights = M->d_weights.as<float>();
     a.n_weights = M->ops->n_weights;
-    a.tpa = choose_tpa(n, M->n_sm);
+    a.tpa = M->tpa_pairs ? M->tpa_pairs : choose_tpa(n, M->n_sm, 512);
+    a.tpa_m = M->tpa_moments ? M->tpa_moments : choose_tpa(n, M->n_sm, 128);
     a.mom = M->mom.as<T>();
     a.adjm = M->adjm.as<T>();
     a.gx = M->gx.as<T>();
@@ -404,12 +409,23 @@ mtp_status mtp_set_skin(mtp_model* M, double skin) {
     if (!M || !(skin >= 0.0) || skin > 10.0) return MTP_EINVAL;
     M->skin = skin;
     M->nb.has_x0 = false;
+    M->g_sig.clear();  // a captured evaluation holds the old search radius
+    return MTP_OK;
+}
+
+mtp_status mtp_set_threads_per_atom(mtp_model* M, int moments, int pairs) {
+    auto ok = [](int t) { return t == 0 || t == 1 || t == 2 || t == 4 || t == 8; };
+    if (!M || !ok(moments) || !ok(pairs)) return MTP_EINVAL;
+    M->tpa_moments = moments;
+    M->tpa_pairs = pairs;
+    M->g_sig.clear();  // a captured evaluation holds the old launch shapes
     return MTP_OK;
 }
 
 mtp_status mtp_set_neighbor_capacity(mtp_model* M, int cap) {
     if (!M || cap < 1 || cap > 1024) return MTP_EINVAL;
     M->cap = cap;
+    M->g_sig.clear();  // a captured evaluation holds the old capacity
     return MTP_OK;
 }
 

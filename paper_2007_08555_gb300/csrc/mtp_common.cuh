@@ -48,7 +48,8 @@ struct EvalCtx {
     int adj_layers;
     const float* weights;               // [n_weights] op weights
     int n_weights;
-    int tpa;              // threads per atom in the pair kernels (1, 2, 4 or 8)
+    int tpa;              // threads per atom in the pair-gradient and gather kernels (1, 2, 4 or 8)
+    int tpa_m;            // threads per atom in the moments kernel
     T* mom;               // [ceil(n/32)][C][32] moment components (tile layout)
     T* adjm;              // [ceil(n/32)][C][32] dV/dM
     T* gx;                // [cap][n] dV_i/dr_ij

@@ -69,6 +69,7 @@ _SIGS = {
     "mtp_grade": (_I, [_P, _I, _P, _P, _I, _P]),
     "mtp_param_grad": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, _D, _D, _D, _I, _P, _P, _P, _I, _P]),
     "mtp_set_skin": (_I, [_P, _D]),
+    "mtp_set_threads_per_atom": (_I, [_P, _I, _I]),
     "mtp_md_run": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _I, _P, _P, ctypes.POINTER(_I), _I, _P]),
     "mtp_select_active_set_noalloc": (_I, [_I, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
     "mtp_profile_read": (_I, [_P, _P, _I, ctypes.POINTER(_L)]),
@@ -177,6 +178,10 @@ def mtp_param_grad(h, n_cfg, n_atoms, cfg_off, pos, types, cells, e_ref, f_ref, 
 
 def mtp_set_skin(h, skin):
     _check(load().mtp_set_skin(h, float(skin)), "mtp_set_skin")
+
+
+def mtp_set_threads_per_atom(h, moments, pairs):
+    _check(load().mtp_set_threads_per_atom(h, int(moments), int(pairs)), "mtp_set_threads_per_atom")
 
 
 def mtp_md_run(h, n_atoms, pos, vel, types, cell, masses, dt, n_steps, stream=None):
@@ -341,6 +346,9 @@ class Model:
 
     def set_skin(self, skin):
         mtp_set_skin(self.h, skin)
+
+    def set_threads_per_atom(self, moments=0, pairs=0):
+        mtp_set_threads_per_atom(self.h, moments, pairs)
 
     def md_run(self, pos, vel, types, cell, masses, dt, n_steps, stream=None):
         """Velocity Verlet in place (device tensors); returns (e_pot, e_kin, rebuilds)."""

@@ -144,6 +144,31 @@ def test_batched_small_cells(gpu_lib, precision, L):
         assert site[b.cfg_off[k]:b.cfg_off[k + 1]].sum() == pytest.approx(e[k], rel=1e-9, abs=1e-9)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_threads_per_atom_variants(gpu_lib, precision):
+    """Every lanes-per-atom layout of the pair kernels gives the oracle's results; changing the
+    layout between two identical calls is honoured (the captured graph is dropped)."""
+    L = 12
+    b = synth.small_cells(n_cfg=10, n_lo=8, n_hi=120, seed=77)
+    p = params(L, 3, 9)
+    pot = oracle.Potential(p)
+    refs = [pot.eval(b.config(k)) for k in range(b.n_cfg)]
+    model = mtp.Model.from_params(p, precision)
+    pos, types, cells, off = batch_tensors(b)
+    tol = TOL[precision]
+    out = None
+    for tm, tp in [(1, 1), (2, 4), (4, 2), (8, 8), (1, 8), (8, 1), (0, 0)]:
+        model.set_threads_per_atom(tm, tp)
+        for _ in range(2):  # the second identical call replays a graph
+            out = model.eval_batch(pos, types, cells, off, out=out)
+            e, f, w = (out[k].cpu().numpy() for k in ("energy", "forces", "virial"))
+            for k in range(b.n_cfg):
+                a0, a1 = b.cfg_off[k], b.cfg_off[k + 1]
+                check_config(e[k], f[a0:a1], w[k], refs[k], b.config(k).n, tol, msg=f"tpa {tm},{tp} cfg {k}")
+    with pytest.raises(mtp.MTPError):
+        model.set_threads_per_atom(3, 1)
+
+
 @pytest.fixture(scope="module")
 def config2():
     cfg = synth.fcc_binary()
