@@ -50,7 +50,7 @@ struct mtp_model {
     DevBuf d_xi, d_c, d_seed, d_basis_value;
     DevBuf d_fwd_ops, d_fwd_layers, d_adj_ops, d_adj_layers, d_weights;
     mtp::NbrState nb;
-    DevBuf mom, adjm, gx, gy, gz;
+    DevBuf mom, adjm, gx;  // gx: pair gradients as 4-vectors
     // staging for MTP_HOST_MEMORY calls
     DevBuf s_off, s_pos, s_types, s_cells, s_energy, s_forces, s_virial, s_site, s_brows, s_batoms;
     int cap = 128;
@@ -144,7 +144,7 @@ mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     const size_t tiles = (N + 31) / 32;
     const int cap = M->nb.cap;
     if (M->mom.reserve(tiles * M->C * 32 * sizeof(T)) || M->adjm.reserve(tiles * M->C * 32 * sizeof(T)) ||
-        M->gx.reserve(N * cap * sizeof(T)) || M->gy.reserve(N * cap * sizeof(T)) || M->gz.reserve(N * cap * sizeof(T)))
+        M->gx.reserve(N * cap * sizeof(mtp::Vec4<T>)))
         return MTP_ENOMEM;
     if (energy) cudaMemsetAsync(energy, 0, sizeof(double) * K, st);
     if (virial) cudaMemsetAsync(virial, 0, sizeof(double) * 9 * K, st);
@@ -183,9 +183,7 @@ mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     a.tpa_m = M->tpa_moments ? M->tpa_moments : choose_tpa(n, M->n_sm, 128);
     a.mom = M->mom.as<T>();
     a.adjm = M->adjm.as<T>();
-    a.gx = M->gx.as<T>();
-    a.gy = M->gy.as<T>();
-    a.gz = M->gz.as<T>();
+    a.g = M->gx.as<mtp::Vec4<T>>();
     a.energy = energy;
     a.site = site;
     a.b_atoms = batoms;
@@ -339,9 +337,9 @@ void mtp_destroy(mtp_model* M) {
     if (!M) return;
     DevBuf* bufs[] = {&M->d_xi, &M->d_c, &M->d_seed, &M->d_basis_value, &M->d_fwd_ops, &M->d_fwd_layers,
                       &M->d_adj_ops, &M->d_adj_layers, &M->d_weights, &M->mom,
-                      &M->adjm, &M->gx, &M->gy, &M->gz, &M->s_off, &M->s_pos, &M->s_types, &M->s_cells,
+                      &M->adjm, &M->gx, &M->s_off, &M->s_pos, &M->s_types, &M->s_cells,
                       &M->s_energy, &M->s_forces, &M->s_virial, &M->s_site, &M->s_brows, &M->s_batoms,
-                      &M->nb.count, &M->nb.jz, &M->nb.shift, &M->nb.rev, &M->nb.rx, &M->nb.ry, &M->nb.rz,
+                      &M->nb.count, &M->nb.jz, &M->nb.rev, &M->nb.rx, &M->nb.ry, &M->nb.rz,
                       &M->nb.cfg_of, &M->nb.desc, &M->nb.atom_bin, &M->nb.atom_wrap, &M->nb.atom_local,
                       &M->nb.bin_count, &M->nb.bin_start, &M->nb.bin_fill, &M->nb.bin_atoms, &M->nb.counters,
                       &M->nb.err, &M->nb.max_seen, &M->g_energy, &M->g_forces, &M->g_virial, &M->g_D, &M->g_eps, &M->g_ew,

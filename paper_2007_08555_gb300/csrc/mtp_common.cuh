@@ -20,6 +20,12 @@ enum : int {
 };
 
 // Inputs and outputs of one evaluation; every array is device memory.
+// Three components padded to a 16- (float) or 32-byte (double) vector: one load or store per pair.
+template <class T>
+struct alignas(4 * sizeof(T)) Vec4 {
+    T x, y, z, w;
+};
+
 template <class T>
 struct EvalCtx {
     int n_atoms;      // atoms in the batch
@@ -52,9 +58,7 @@ struct EvalCtx {
     int tpa_m;            // threads per atom in the moments kernel
     T* mom;               // [ceil(n/32)][C][32] moment components (tile layout)
     T* adjm;              // [ceil(n/32)][C][32] dV/dM
-    T* gx;                // [cap][n] dV_i/dr_ij
-    T* gy;
-    T* gz;
+    Vec4<T>* g;           // [cap][n] dV_i/dr_ij (x, y, z, unused): one vector load per pair
     double* energy;       // [n_cfg] (accumulated; zeroed by the caller) or NULL
     double* site;         // [n] or NULL
     double* b_atoms;      // [n][M] or NULL

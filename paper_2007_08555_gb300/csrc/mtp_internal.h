@@ -44,7 +44,7 @@ struct NbrState {
     int n_atoms = 0, n_cfg = 0, cap = 0;
     bool fp64 = false;
     double rsearch = 0.0;
-    DevBuf count, jz, shift, rev, rx, ry, rz, keys_am;
+    DevBuf count, jz, rev, rx, ry, rz, keys_am;
     DevBuf cfg_of, desc, atom_bin, atom_wrap, atom_local, atom_wp, bin_count, bin_start, bin_fill, bin_atoms, counters;
     DevBuf err, max_seen;
     // reuse with a skin: positions at the build and the current displacements (float or double)

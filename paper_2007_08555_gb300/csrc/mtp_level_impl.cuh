@@ -539,13 +539,10 @@ __device__ __forceinline__ void pairgrad_slice(const EvalCtx<T>& a, int i, int s
         gy += sr * y;
         gz += sr * z;
         if (S == 0) {
-            a.gx[idx] = gx;
-            a.gy[idx] = gy;
-            a.gz[idx] = gz;
+            a.g[idx] = Vec4<T>{gx, gy, gz, T(0)};
         } else {
-            a.gx[idx] += gx;
-            a.gy[idx] += gy;
-            a.gz[idx] += gz;
+            const Vec4<T> o = a.g[idx];
+            a.g[idx] = Vec4<T>{o.x + gx, o.y + gy, o.z + gz, T(0)};
         }
     }
 }
@@ -598,7 +595,8 @@ __global__ void __launch_bounds__(128) k_gather(const EvalCtx<T> a) {
             const int cnt = a.count[i];
             for (int p = sub; p < cnt; p += TPA) {
                 const size_t idx = (size_t)p * n + i;
-                const T g3[3] = {a.gx[idx], a.gy[idx], a.gz[idx]};
+                const Vec4<T> gv = a.g[idx];
+                const T g3[3] = {gv.x, gv.y, gv.z};
                 const T r[3] = {a.rx[idx], a.ry[idx], a.rz[idx]};
 #pragma unroll
                 for (int u = 0; u < 3; ++u) {
@@ -609,9 +607,10 @@ __global__ void __launch_bounds__(128) k_gather(const EvalCtx<T> a) {
                 const int q = a.rev[idx];
                 if (q >= 0) {
                     const size_t ridx = (size_t)q * n + (a.jz[idx] & 0xffffff);
-                    F[0] -= a.gx[ridx];
-                    F[1] -= a.gy[ridx];
-                    F[2] -= a.gz[ridx];
+                    const Vec4<T> gr = a.g[ridx];
+                    F[0] -= gr.x;
+                    F[1] -= gr.y;
+                    F[2] -= gr.z;
                 }
             }
         }

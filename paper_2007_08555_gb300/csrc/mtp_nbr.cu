@@ -200,7 +200,6 @@ struct BuildArgs {
     const int* bin_atoms;
     int* count;
     int* jz;
-    int* shift;
     unsigned long long* keys_am;  // [n][cap] the sorted keys, atom-major
     void* rx;
     void* ry;
@@ -508,7 +507,6 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                     int tj = a.types[j];
                     tj = tj < 0 ? 0 : (tj >= a.S ? a.S - 1 : tj);  // invalid species are reported by k_bin_atoms
                     a.jz[o] = j | (tj << 24);
-                    a.shift[o] = (int)(key & 0xffffffull);
                     a.keys_am[(size_t)i * a.cap + rank] = key;
                     RX[o] = rbuf[3 * e];
                     RY[o] = rbuf[3 * e + 1];
@@ -525,7 +523,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
 
 // one thread per (slot, atom): binary search of the reverse pair (i, -s) in the neighbour's sorted
 // keys, stored atom-major so that one search stays within a few cache lines
-__global__ void k_reverse(int n, int cap, const int* count, const int* jz, const int* shift,
+__global__ void k_reverse(int n, int cap, const int* count, const int* jz,
                           const unsigned long long* keys_am, int* rev) {
     const size_t N = (size_t)n;
     const size_t total = N * (size_t)cap;
@@ -534,7 +532,7 @@ __global__ void k_reverse(int n, int cap, const int* count, const int* jz, const
         const int i = (int)(o - (size_t)p * N);
         if (p >= count[i]) continue;
         const int j = jz[o] & 0xffffff;
-        const int sp = shift[o];
+        const int sp = (int)(keys_am[(size_t)i * cap + p] & 0xffffffull);
         const int neg = ((256 - (sp & 255)) & 255) | (((256 - ((sp >> 8) & 255)) & 255) << 8) |
                         (((256 - ((sp >> 16) & 255)) & 255) << 16);
         const unsigned long long want = ((unsigned long long)i << 32) | (unsigned long long)neg;
@@ -620,8 +618,9 @@ __global__ void k_scan_add(int* out, int n, const int* sums) {
     if (i < n) out[i] += sums[i / kScanBlock];
 }
 
-__global__ void k_export(int n, const double* pos, const CellDesc* desc, const int* cfg_of, const int* count,
-                         const int* jz, const int* shift, const int* offsets, int* nbr_j, int* nbr_s, double* r_ij) {
+__global__ void k_export(int n, int cap, const double* pos, const CellDesc* desc, const int* cfg_of, const int* count,
+                         const int* jz, const unsigned long long* keys_am, const int* offsets, int* nbr_j, int* nbr_s,
+                         double* r_ij) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const CellDesc& D = desc[cfg_of[i]];
@@ -630,7 +629,7 @@ __global__ void k_export(int n, const double* pos, const CellDesc* desc, const i
     for (int p = 0; p < cnt; ++p) {
         const size_t o = (size_t)p * n + i;
         const int j = jz[o] & 0xffffff;
-        const int sp = shift[o];
+        const int sp = (int)(keys_am[(size_t)i * cap + p] & 0xffffffull);  // slot p of the sorted keys
         const int s[3] = {((sp >> 16) & 255) - 128, ((sp >> 8) & 255) - 128, (sp & 255) - 128};
         const size_t q = (size_t)offsets[i] + p;
         nbr_j[q] = j;
@@ -667,7 +666,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     const size_t N = (size_t)n;
     const size_t realsz = fp64 ? 8 : 4;
     const size_t bins_max = N + K + 1;
-    if (nb.count.reserve(N * 4) || nb.jz.reserve(N * cap * 4) || nb.shift.reserve(N * cap * 4) ||
+    if (nb.count.reserve(N * 4) || nb.jz.reserve(N * cap * 4) ||
         nb.rev.reserve(N * cap * 4) || nb.keys_am.reserve(N * cap * 8) || nb.rx.reserve(N * cap * realsz) || nb.ry.reserve(N * cap * realsz) ||
         nb.rz.reserve(N * cap * realsz) || nb.cfg_of.reserve(N * 4) || nb.desc.reserve(sizeof(CellDesc) * K) ||
         nb.atom_bin.reserve(N * 4) || nb.atom_wrap.reserve(N * 4) || nb.atom_local.reserve(N * 16) || nb.atom_wp.reserve(N * 32) ||
@@ -726,7 +725,6 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     a.bin_atoms = nb.bin_atoms.as<int>();
     a.count = nb.count.as<int>();
     a.jz = nb.jz.as<int>();
-    a.shift = nb.shift.as<int>();
     a.keys_am = nb.keys_am.as<unsigned long long>();
     a.rx = nb.rx.p;
     a.ry = nb.ry.p;
@@ -763,7 +761,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
         const size_t total = N * (size_t)cap;
         size_t blocks = (total + 255) / 256;
         if (blocks > 152 * 64) blocks = 152 * 64;
-        k_reverse<<<(int)blocks, 256, 0, st>>>(n, cap, nb.count.as<int>(), nb.jz.as<int>(), nb.shift.as<int>(),
+        k_reverse<<<(int)blocks, 256, 0, st>>>(n, cap, nb.count.as<int>(), nb.jz.as<int>(),
                                               nb.keys_am.as<unsigned long long>(), nb.rev.as<int>());
     }
     ++launches;
@@ -773,9 +771,9 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
 int export_neighbors(const NbrState& nb, const double* pos, const int* offsets, int* nbr_j, int* nbr_s,
                      double* r_ij, cudaStream_t st) {
     const int n = nb.n_atoms;
-    k_export<<<(n + 127) / 128, 128, 0, st>>>(n, pos, nb.desc.as<CellDesc>(), nb.cfg_of.as<int>(),
-                                              nb.count.as<int>(), nb.jz.as<int>(), nb.shift.as<int>(), offsets,
-                                              nbr_j, nbr_s, r_ij);
+    k_export<<<(n + 127) / 128, 128, 0, st>>>(n, nb.cap, pos, nb.desc.as<CellDesc>(), nb.cfg_of.as<int>(),
+                                              nb.count.as<int>(), nb.jz.as<int>(),
+                                              nb.keys_am.as<unsigned long long>(), offsets, nbr_j, nbr_s, r_ij);
     return 1;
 }
 
