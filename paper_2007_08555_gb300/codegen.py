@@ -716,53 +716,121 @@ def flop_counts(prog: Program):
 UNROLLED_MAX_LEVEL = int(os.environ.get("MTP_UNROLLED_MAX_LEVEL", "20"))
 
 
-def emit_unrolled(prog: Program):
-    """Straight-line thread-per-atom contraction (float): forward program in creation order, site
-    energy, then the adjoint in reverse creation order, every value an SSA register (the compiler
-    spills what does not fit).  Moments are read from and dV/dM written to the tile layout
-    [tile][C][32] at src[c * 32] / dst[c * 32]."""
+# The float contraction is split by basis functions into CONTRACT_PARTS[L] programs; each part evaluates the sub-network its basis functions need (shared
+# sub-networks are recomputed by every part that needs them), so that one part's values fit in
+# registers.  Each warp runs one part for 32 atoms.
+CONTRACT_PARTS = {2: 1, 4: 1, 6: 1, 8: 1, 10: 1, 12: 2, 14: 2, 16: 4, 18: 8, 20: 8}
+PART_BALANCE = 0.2  # weight of a part's operation count against its value count when assigning
+
+
+def partition_program(prog: Program, parts: int, balance: float = PART_BALANCE):
+    """Split the basis functions into `parts` groups.  Greedy, largest sub-network first: each
+    basis function joins the group whose value set grows least, plus `balance` times the group's
+    operation count (so that parts take similar time).  Returns [(values, basis indices)]."""
+    by_k = defaultdict(list)
+    for (k, i, j, w) in prog.ops:
+        by_k[k].append((i, j))
+    deps = {}
+    for k in sorted(set(range(prog.n_values))):
+        d = {k}
+        for (i, j) in by_k.get(k, []):
+            d |= deps[i]
+            d |= deps[j]
+        deps[k] = frozenset(d)
+    nops = {k: len(v) for k, v in by_k.items()}
+    groups = [(set(), []) for _ in range(parts)]
+    gops = [0] * parts
+    order = sorted(range(len(prog.basis_value)), key=lambda a: (-len(deps[prog.basis_value[a]]), a))
+    for a in order:
+        d = deps[prog.basis_value[a]]
+        best = None
+        for g in range(parts):
+            new = d - groups[g][0]
+            add = sum(nops.get(k, 0) for k in new)
+            cost = len(groups[g][0]) + len(new) + balance * (gops[g] + add)
+            if best is None or cost < best[0]:
+                best = (cost, g, add)
+        _, g, add = best
+        groups[g][0].update(d)
+        groups[g][1].append(a)
+        gops[g] += add
+    return [(vals, sorted(alphas)) for vals, alphas in groups]
+
+
+def emit_parts(prog: Program, parts: int):
+    """Straight-line float contraction split into parts (see CONTRACT_PARTS).  Part g reads the
+    moments it needs from the tile layout (src[c * 32]), computes its values in creation order, its
+    share of the site energy and of b, then the adjoint of its sub-network seeded by its own basis
+    functions, and writes dV/dM of its moments to adjoint slots (dst[slot * 32]).  Slots are
+    numbered by component, then part, so that dV/dM_c is the sum of slots slot_begin[c] ..
+    slot_begin[c + 1] - 1 in that order."""
     C = len(prog.comp_list)
     by_k = defaultdict(list)
     for (k, i, j, w) in prog.ops:
         by_k[k].append((i, j, w))
-    out = ["template <bool WANT_B>",
-           "__device__ __forceinline__ float contract_unrolled(const float* __restrict__ src, float* __restrict__ dst, "
-           "const float* __restrict__ xi, double* __restrict__ bout) {"]
+    groups = partition_program(prog, parts)
+    slot_of = {}
+    slot_begin = []
     for c in range(C):
-        out.append(f"  const float v{c} = src[{c * 32}];")
+        slot_begin.append(len(slot_of))
+        for g, (vals, _) in enumerate(groups):
+            if c in vals:
+                slot_of[(g, c)] = len(slot_of)
+    slot_begin.append(len(slot_of))
+    out = [f"#define MTPGEN_HAS_PARTS 1", f"constexpr int NPART = {parts}, NSLOT = {len(slot_of)};",
+           "static __device__ const int slot_begin[] = {" + ",".join(map(str, slot_begin)) + "};",
+           "template <int PART> struct Part;"]
 
     def lit(w):
         return "" if w == 1.0 else f"{w!r}f * "
 
-    for k in sorted(by_k):
-        terms = [f"{lit(w)}v{i} * v{j}" for (i, j, w) in by_k[k]]
-        out.append(f"  const float v{k} = " + " + ".join(terms) + ";")
-    out.append("  float e = 0.f;")
-    for a, v in enumerate(prog.basis_value):
-        out.append(f"  e += xi[{a}] * v{v};")
-        out.append(f"  if (WANT_B) bout[{a}] = (double)v{v};")
-    seed = defaultdict(list)
-    for a, v in enumerate(prog.basis_value):
-        seed[v].append(a)
-    declared = set()
+    for g, (vals, alphas) in enumerate(groups):
+        out.append(f"template <> struct Part<{g}> {{")
+        out.append("  template <bool WANT_B> static __device__ __forceinline__ float run(const float* __restrict__ src, "
+                   "float* __restrict__ dst, const float* __restrict__ xi, double* __restrict__ bout) {")
+        comps = sorted(v for v in vals if v < C)
+        for c in comps:
+            out.append(f"    const float v{c} = src[{c * 32}];")
+        inner = sorted(v for v in vals if v >= C)
+        for k in inner:
+            terms = [f"{lit(w)}v{i} * v{j}" for (i, j, w) in by_k[k]]
+            out.append(f"    const float v{k} = " + " + ".join(terms) + ";")
+        out.append("    float e = 0.f;")
+        seed = defaultdict(list)
+        for a in alphas:
+            v = prog.basis_value[a]
+            out.append(f"    e += xi[{a}] * v{v};")
+            out.append(f"    if (WANT_B) bout[{a}] = (double)v{v};")
+            seed[v].append(a)
+        declared = set()
 
-    def aref(v):
-        if v not in declared:
-            declared.add(v)
-            init = " + ".join(f"xi[{a}]" for a in seed.get(v, [])) or "0.f"
-            out.append(f"  float a{v} = {init};")
-        return f"a{v}"
+        def aref(v):
+            if v not in declared:
+                declared.add(v)
+                init = " + ".join(f"xi[{a}]" for a in seed.get(v, [])) or "0.f"
+                out.append(f"    float a{v} = {init};")
+            return f"a{v}"
 
-    for k in sorted(by_k, reverse=True):
-        ak = aref(k)
-        for (i, j, w) in by_k[k]:
-            ai = aref(i)
-            aj = aref(j)
-            out.append(f"  {ai} += {lit(w)}v{j} * {ak};")
-            out.append(f"  {aj} += {lit(w)}v{i} * {ak};")
-    for c in range(C):
-        out.append(f"  dst[{c * 32}] = {aref(c)};")
-    out.append("  return e;")
+        for k in reversed(inner):
+            ak = aref(k)
+            for (i, j, w) in by_k[k]:
+                ai = aref(i)
+                aj = aref(j)
+                out.append(f"    {ai} += {lit(w)}v{j} * {ak};")
+                out.append(f"    {aj} += {lit(w)}v{i} * {ak};")
+        for c in comps:
+            out.append(f"    dst[{slot_of[(g, c)] * 32}] = {aref(c)};")
+        out.append("    return e;")
+        out.append("  }")
+        out.append("};")
+    out.append("template <bool WANT_B>")
+    out.append("__device__ __forceinline__ float contract_part(int part, const float* __restrict__ src, "
+               "float* __restrict__ dst, const float* __restrict__ xi, double* __restrict__ bout) {")
+    out.append("  switch (part) {")
+    for g in range(parts):
+        out.append(f"    case {g}: return Part<{g}>::template run<WANT_B>(src, dst, xi, bout);")
+    out.append("  }")
+    out.append("  return 0.f;")
     out.append("}")
     return out
 
@@ -821,15 +889,19 @@ def emit_level(L, outdir):
         lines.append(f"static const int {name}_size[] = {{" + ",".join(str(len(c)) for _, c in sl) + "};")
         for s, (_, comps) in enumerate(sl):
             assert comps == list(range(min(comps), min(comps) + len(comps)))
+    nparts, nslots = 1, 0
     if L <= UNROLLED_MAX_LEVEL and prog.ops:
-        lines.append("#define MTPGEN_HAS_UNROLLED 1")
-        lines += emit_unrolled(prog)
+        nparts = CONTRACT_PARTS.get(L, 1)
+        part_lines = emit_parts(prog, nparts)
+        nslots = int(part_lines[1].split("NSLOT = ")[1].rstrip(";"))
+        lines += part_lines
     else:
-        lines.append("#define MTPGEN_HAS_UNROLLED 0")
+        lines.append("#define MTPGEN_HAS_PARTS 0")
     lines += emit_slice_functions(prog, s32, "f")
     lines += emit_slice_functions(prog, s64, "d")
     lines.append("struct Traits {")
     lines.append("  static constexpr int L_ = L, C_ = C, V_ = V, M_ = M, NMU_ = NMU, NUMAX_ = NUMAX, NS32_ = NS32, NS64_ = NS64;")
+    lines.append(f"  static constexpr int NPART_ = {nparts}, NSLOT_ = {max(nslots, 1)};")
     lines.append("  template <int S> using F32 = SliceF<S>;")
     lines.append("  template <int S> using F64 = SliceD<S>;")
     lines.append("};")

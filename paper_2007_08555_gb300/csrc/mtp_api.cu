@@ -51,6 +51,7 @@ struct mtp_model {
     DevBuf d_fwd_ops, d_fwd_layers, d_adj_ops, d_adj_layers, d_weights;
     mtp::NbrState nb;
     DevBuf mom, adjm, gx;  // gx: pair gradients as 4-vectors
+    DevBuf aslots, epart;  // float contraction: per-part dV/dM slots and site-energy shares
     // staging for MTP_HOST_MEMORY calls
     DevBuf s_off, s_pos, s_types, s_cells, s_energy, s_forces, s_virial, s_site, s_brows, s_batoms;
     int cap = 128;
@@ -143,6 +144,10 @@ mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     const size_t N = (size_t)n;
     const size_t tiles = (N + 31) / 32;
     const int cap = M->nb.cap;
+    const bool parts = sizeof(T) == 4;  // the float path splits its contraction into parts
+    if (parts && (M->aslots.reserve(tiles * M->ops->contract_slots * 32 * sizeof(T) + 16) ||
+                  M->epart.reserve(N * M->ops->contract_parts * sizeof(T) + 16)))
+        return MTP_ENOMEM;
     if (M->mom.reserve(tiles * M->C * 32 * sizeof(T)) || M->adjm.reserve(tiles * M->C * 32 * sizeof(T)) ||
         M->gx.reserve(N * cap * sizeof(mtp::Vec4<T>)))
         return MTP_ENOMEM;
@@ -183,6 +188,8 @@ mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     a.tpa_m = M->tpa_moments ? M->tpa_moments : choose_tpa(n, M->n_sm, 128);
     a.mom = M->mom.as<T>();
     a.adjm = M->adjm.as<T>();
+    a.aslots = parts ? M->aslots.as<T>() : nullptr;
+    a.epart = parts ? M->epart.as<T>() : nullptr;
     a.g = M->gx.as<mtp::Vec4<T>>();
     a.energy = energy;
     a.site = site;
@@ -350,6 +357,8 @@ void mtp_destroy(mtp_model* M) {
     for (DevBuf* b : bufs) b->release();
     M->nb.atom_wp.release();
     M->nb.keys_am.release();
+    M->aslots.release();
+    M->epart.release();
     if (M->h_flags) cudaFreeHost(M->h_flags);
     if (M->g_exec) cudaGraphExecDestroy(M->g_exec);
     if (M->cap_stream) cudaStreamDestroy(M->cap_stream);

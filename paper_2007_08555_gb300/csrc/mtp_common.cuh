@@ -58,6 +58,8 @@ struct EvalCtx {
     int tpa_m;            // threads per atom in the moments kernel
     T* mom;               // [ceil(n/32)][C][32] moment components (tile layout)
     T* adjm;              // [ceil(n/32)][C][32] dV/dM
+    T* aslots;            // [ceil(n/32)][NSLOT][32] dV/dM shares of the contraction parts (float path)
+    T* epart;             // [NPART][n] site-energy shares of the contraction parts (float path)
     Vec4<T>* g;           // [cap][n] dV_i/dr_ij (x, y, z, unused): one vector load per pair
     double* energy;       // [n_cfg] (accumulated; zeroed by the caller) or NULL
     double* site;         // [n] or NULL

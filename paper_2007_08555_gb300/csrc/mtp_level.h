@@ -20,6 +20,7 @@ struct LevelOps {
     int n_weights;
     int program_ops;
     int flop_pair_moments, flop_pair_adjoint, flop_atom_program;
+    int contract_parts, contract_slots;  // float contraction parts and their dV/dM slots per atom
     // launchers (stream-ordered, no synchronisation); return the number of kernels launched
     int (*eval_f32)(const EvalCtx<float>&, cudaStream_t, int n_sm, cudaEvent_t* marks);
     int (*eval_f64)(const EvalCtx<double>&, cudaStream_t, int n_sm, cudaEvent_t* marks);

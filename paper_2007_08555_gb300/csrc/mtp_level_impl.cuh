@@ -458,20 +458,53 @@ __global__ void __launch_bounds__(256) k_contract(const EvalCtx<T> a) {
     }
 }
 
-#if MTPGEN_HAS_UNROLLED
-// thread per atom: the generated straight-line contraction (float)
-__global__ void __launch_bounds__(128) k_contract_unrolled(const EvalCtx<float> a) {
-    constexpr int C = G::C_, M = G::M_;
+#if MTPGEN_HAS_PARTS
+// Float contraction, split into NPART generated parts (basis functions grouped so that one part's
+// values fit in registers): warp w runs part w / n_tiles for the 32 atoms of tile w % n_tiles, so
+// that the warps on an SM mostly run the same code.  Each part writes its site-energy share and
+// dV/dM of its moments to slots; k_contract_sum adds them up in a fixed order.
+__global__ void __launch_bounds__(128) k_contract_parts(const EvalCtx<float> a) {
+    const int lane = threadIdx.x & 31;
+    const int n_tiles = (a.n_atoms + 31) >> 5;
+    const int total = n_tiles * G::NPART_;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += (gridDim.x * blockDim.x) >> 5) {
+        const int part = w / n_tiles, tile = w - part * n_tiles;
+        const int i = tile * 32 + lane;
+        if (i >= a.n_atoms) continue;
+        const float* src = a.mom + (size_t)tile * G::C_ * 32 + lane;
+        float* dst = a.aslots + (size_t)tile * G::NSLOT_ * 32 + lane;
+        double* bout = a.b_atoms ? a.b_atoms + (size_t)i * G::M_ : nullptr;
+        const float e = bout ? ::MTP_GEN_NS::contract_part<true>(part, src, dst, a.xi, bout)
+                             : ::MTP_GEN_NS::contract_part<false>(part, src, dst, a.xi, nullptr);
+        a.epart[(size_t)part * a.n_atoms + i] = e;
+    }
+}
+
+// dV/dM_c = sum of its slots (slot order), site energies = sum of the parts' shares (part order),
+// configuration energies accumulated in double
+__global__ void __launch_bounds__(128) k_contract_sum(const EvalCtx<float> a) {
+    constexpr int C = G::C_;
+    const int lane = threadIdx.x & 31;
+    const int n_tiles = (a.n_atoms + 31) >> 5;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    // one warp per (tile, component): 32 atoms, coalesced
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_tiles * C; w += warps) {
+        const int tile = w / C, c = w - tile * C;
+        const float* sl = a.aslots + (size_t)tile * G::NSLOT_ * 32 + lane;
+        const int s0 = ::MTP_GEN_NS::slot_begin[c], s1 = ::MTP_GEN_NS::slot_begin[c + 1];
+        float acc = 0.f;
+        for (int s = s0; s < s1; ++s) acc += sl[s * 32];
+        a.adjm[((size_t)tile * C + c) * 32 + lane] = acc;
+    }
+    const int stride = gridDim.x * blockDim.x;
     __shared__ double s_e[128];
     __shared__ int s_c[128];
     double erun = 0.0;
     int ecfg = -1;
-    const int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_atoms; i += stride) {
-        const size_t t = (size_t)(i >> 5) * C * 32 + (i & 31);
-        double* bout = a.b_atoms ? a.b_atoms + (size_t)i * M : nullptr;
-        const float e = bout ? ::MTP_GEN_NS::contract_unrolled<true>(a.mom + t, a.adjm + t, a.xi, bout)
-                             : ::MTP_GEN_NS::contract_unrolled<false>(a.mom + t, a.adjm + t, a.xi, nullptr);
+        float e = 0.f;
+#pragma unroll
+        for (int p = 0; p < G::NPART_; ++p) e += a.epart[(size_t)p * a.n_atoms + i];
         if (a.site) a.site[i] = (double)e;
         const int cfg = a.cfg_of[i];
         if (cfg != ecfg) {
@@ -703,13 +736,18 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks)
     if (marks) record_mark(marks[kPhaseMoments], st);
     launches += launch_pairs_tpa<T>(a, st, n_sm, true);
     if (marks) record_mark(marks[kPhaseContract], st);
-#if MTPGEN_HAS_UNROLLED
+#if MTPGEN_HAS_PARTS
     if constexpr (sizeof(T) == 4) {
         const int threads = 128;
-        int blocks = (a.n_atoms + threads - 1) / threads;
+        const long warps = (long)((a.n_atoms + 31) / 32) * G::NPART_;
+        int blocks = (int)((warps + 3) / 4);
         if (blocks > n_sm * 16) blocks = n_sm * 16;
-        k_contract_unrolled<<<blocks, threads, 0, st>>>(a);
-        ++launches;
+        k_contract_parts<<<blocks, threads, 0, st>>>(a);
+        const long sums = (long)((a.n_atoms + 31) / 32) * G::C_ * 32;
+        int sblocks = (int)((sums + threads - 1) / threads);
+        if (sblocks > n_sm * 32) sblocks = n_sm * 32;
+        k_contract_sum<<<sblocks, threads, 0, st>>>(a);
+        launches += 2;
         if (a.b_rows) {  // the caller provides per-atom rows whenever b rows are requested
             k_brows<T><<<a.n_cfg, 128, 0, st>>>(a, a.cfg_off);
             ++launches;
@@ -1168,6 +1206,7 @@ const LevelOps* MTP_LEVEL_FN() {
         g::fwd_ops, g::fwd_layer_rows, g::FWD_ROWS, g::FWD_LAYERS,
         g::adj_ops, g::adj_layer_rows, g::ADJ_ROWS, g::ADJ_LAYERS, g::weights, g::NWEIGHTS,
         g::PROGRAM_OPS, g::FLOP_PAIR_MOMENTS, g::FLOP_PAIR_ADJOINT, g::FLOP_ATOM_PROGRAM,
+        g::Traits::NPART_, g::Traits::NSLOT_,
         &MTP_GEN_NS::eval_f32, &MTP_GEN_NS::eval_f64, &MTP_GEN_NS::grad_f32, &MTP_GEN_NS::grad_f64};
     return &ops;
 }
