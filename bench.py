@@ -49,6 +49,9 @@ def parse():
     return ap.parse_args()
 
 
+PAIRGRAD_DRAM_BYTES = 21414912 + 256  # dram__bytes_read.sum + dram__bytes_write.sum, one launch
+
+
 def dist_env():
     from paper_2007_08555_gb300 import ranks
 
@@ -232,8 +235,11 @@ def run_ours(args):
     peak = flops.fp32_peak_tflops()
     achieved = fl[dom] / (kern[dom] * 1e-3) / 1e12
     total_flops = sum(fl.values())
+    # DRAM bytes (read + write) of one k_pairgrad launch on this workload, from the ncu capture in
+    # profiles/kernels_fcc16_lev16.md; valid while that kernel is unchanged
+    traffic = PAIRGRAD_DRAM_BYTES if (dom == "pairgrad" and args.lev == 16 and args.reps == 16) else None
     roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_note": "FP32 FMA peak derived: 152 SM x 128 lanes x 2 flop x 2.07 GHz",
                 "path_frac": round(total_flops / (ms * 1e-3) / 1e12 / peak, 4)}
     out = None
