@@ -237,6 +237,17 @@ size_t coef_bytes(const EvalCtx<T>& a) {
 // ----------------------------------------------------------------------------------------------
 // k_moments
 // ----------------------------------------------------------------------------------------------
+// one pair's inputs: r_ij and the neighbour's species
+template <class T>
+struct PairIn {
+    T x, y, z;
+    int zj;
+};
+template <class T>
+__device__ __forceinline__ PairIn<T> load_pair(const EvalCtx<T>& a, size_t idx) {
+    return PairIn<T>{a.rx[idx], a.ry[idx], a.rz[idx], a.jz[idx] >> 24};
+}
+
 template <class T, int S, int TPA>
 __device__ __forceinline__ void moments_slice(const EvalCtx<T>& a, int i, int sub, bool active, int zi, int cnt,
                                               const T* cs) {
@@ -247,13 +258,15 @@ __device__ __forceinline__ void moments_slice(const EvalCtx<T>& a, int i, int su
     const size_t n = (size_t)a.n_atoms;
     if (active) {
         const int csz = CoefPad<T>::value * a.NQ;
+        // the next pair's loads are issued before this pair's arithmetic (their latency overlaps it)
+        PairIn<T> nx = load_pair(a, sub < cnt ? (size_t)sub * n + i : (size_t)i);
         for (int p = sub; p < cnt; p += TPA) {
-            const size_t idx = (size_t)p * n + i;
-            const int zj = a.jz[idx] >> 24;
-            const T x = a.rx[idx], y = a.ry[idx], z = a.rz[idx];
+            const PairIn<T> cur = nx;
+            if (p + TPA < cnt) nx = load_pair(a, (size_t)(p + TPA) * n + i);
+            const T x = cur.x, y = cur.y, z = cur.z;
             const T r = my_sqrt(x * x + y * y + z * z);
             T f[G::NMU_];
-            radial<T, false>(r, cs + (zi * a.S + zj) * csz, a.NQ, a.rmin, a.rcut, a.inv_span, f, nullptr);
+            radial<T, false>(r, cs + (zi * a.S + cur.zj) * csz, a.NQ, a.rmin, a.rcut, a.inv_span, f, nullptr);
             SL::template mom<T>(x, y, z, f, acc);
         }
     }
@@ -558,13 +571,16 @@ __device__ __forceinline__ void pairgrad_slice(const EvalCtx<T>& a, int i, int s
     for (int t = 0; t < SL::SIZE; ++t) adjs[t] = src[(size_t)(SL::BEGIN + t) * 32];
     const size_t n = (size_t)a.n_atoms;
     const int csz = CoefPad<T>::value * a.NQ;
+    // the next pair's loads are issued before this pair's arithmetic (their latency overlaps it)
+    PairIn<T> nx = load_pair(a, sub < cnt ? (size_t)sub * n + i : (size_t)i);
     for (int p = sub; p < cnt; p += TPA) {
         const size_t idx = (size_t)p * n + i;
-        const int zj = a.jz[idx] >> 24;
-        const T x = a.rx[idx], y = a.ry[idx], z = a.rz[idx];
+        const PairIn<T> cur = nx;
+        if (p + TPA < cnt) nx = load_pair(a, (size_t)(p + TPA) * n + i);
+        const T x = cur.x, y = cur.y, z = cur.z;
         const T r = my_sqrt(x * x + y * y + z * z);
         T f[G::NMU_], df[G::NMU_];
-        radial<T, true>(r, cs + (zi * a.S + zj) * csz, a.NQ, a.rmin, a.rcut, a.inv_span, f, df);
+        radial<T, true>(r, cs + (zi * a.S + cur.zj) * csz, a.NQ, a.rmin, a.rcut, a.inv_span, f, df);
         T s = T(0), gx = T(0), gy = T(0), gz = T(0);
         SL::template grad<T>(x, y, z, f, df, adjs, s, gx, gy, gz);
         const T sr = s / r;
