@@ -34,7 +34,7 @@ struct CellDesc {
     double H[9], Hi[9];
     float hn[9];  // lattice vectors divided by the bin counts, rows
     float hhi[9], hlo[9];  // lattice vectors as float pairs (hi + lo = H to ~2^-48)
-    double inv_n[3];
+    float inv_n[3];
     int n[3], c[3];
     int bin0, nbins;
 };

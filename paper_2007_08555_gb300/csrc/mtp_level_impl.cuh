@@ -620,8 +620,15 @@ __global__ void __launch_bounds__(128) k_pairgrad(const EvalCtx<T> a) {
 // ----------------------------------------------------------------------------------------------
 // k_gather: forces and virial
 // ----------------------------------------------------------------------------------------------
+template <class T>
+struct GatherIn {
+    Vec4<T> g;
+    T rx, ry, rz;
+    int rev, j;
+};
+
 template <class T, int TPA>
-__global__ void __launch_bounds__(128) k_gather(const EvalCtx<T> a) {
+__global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<T> a) {
     __shared__ int s_cfg[128];
     __shared__ double s_w[9][128];
     const size_t n = (size_t)a.n_atoms;
@@ -642,24 +649,70 @@ __global__ void __launch_bounds__(128) k_gather(const EvalCtx<T> a) {
         if (active) {
             cfg = a.cfg_of[i];
             const int cnt = a.count[i];
-            for (int p = sub; p < cnt; p += TPA) {
-                const size_t idx = (size_t)p * n + i;
-                const Vec4<T> gv = a.g[idx];
-                const T g3[3] = {gv.x, gv.y, gv.z};
-                const T r[3] = {a.rx[idx], a.ry[idx], a.rz[idx]};
+            if constexpr (TPA >= 4) {
+                // few pairs per lane: the other warps hide the load latency
+                for (int p = sub; p < cnt; p += TPA) {
+                    const size_t idx = (size_t)p * n + i;
+                    const Vec4<T> gv = a.g[idx];
+                    const T g3[3] = {gv.x, gv.y, gv.z};
+                    const T r[3] = {a.rx[idx], a.ry[idx], a.rz[idx]};
 #pragma unroll
-                for (int u = 0; u < 3; ++u) {
-                    F[u] += g3[u];
+                    for (int u = 0; u < 3; ++u) {
+                        F[u] += g3[u];
 #pragma unroll
-                    for (int v = 0; v < 3; ++v) W[3 * u + v] -= g3[u] * r[v];
+                        for (int v = 0; v < 3; ++v) W[3 * u + v] -= g3[u] * r[v];
+                    }
+                    const int q = a.rev[idx];
+                    if (q >= 0) {
+                        const Vec4<T> gr = a.g[(size_t)q * n + (a.jz[idx] & 0xffffff)];
+                        F[0] -= gr.x;
+                        F[1] -= gr.y;
+                        F[2] -= gr.z;
+                    }
                 }
-                const int q = a.rev[idx];
-                if (q >= 0) {
-                    const size_t ridx = (size_t)q * n + (a.jz[idx] & 0xffffff);
-                    const Vec4<T> gr = a.g[ridx];
-                    F[0] -= gr.x;
-                    F[1] -= gr.y;
-                    F[2] -= gr.z;
+            } else {
+                // two-stage pipeline: the direct loads of pair p + 2 TPA and the reverse-pair load of
+                // pair p + TPA are in flight while pair p is accumulated
+                auto direct = [&](int p) {
+                    GatherIn<T> d;
+                    const size_t idx = (size_t)p * n + i;
+                    d.g = a.g[idx];
+                    d.rx = a.rx[idx];
+                    d.ry = a.ry[idx];
+                    d.rz = a.rz[idx];
+                    d.rev = a.rev[idx];
+                    d.j = a.jz[idx] & 0xffffff;
+                    return d;
+                };
+                auto reverse = [&](const GatherIn<T>& d) {
+                    return d.rev >= 0 ? a.g[(size_t)d.rev * n + d.j] : Vec4<T>{T(0), T(0), T(0), T(0)};
+                };
+                GatherIn<T> d0, d1;
+                Vec4<T> r0{T(0), T(0), T(0), T(0)};
+                if (sub < cnt) {
+                    d0 = direct(sub);
+                    r0 = reverse(d0);
+                }
+                if (sub + TPA < cnt) d1 = direct(sub + TPA);
+                for (int p = sub; p < cnt; p += TPA) {
+                    const GatherIn<T> cur = d0;
+                    const Vec4<T> cr = r0;
+                    if (p + TPA < cnt) {
+                        d0 = d1;
+                        r0 = reverse(d0);
+                        if (p + 2 * TPA < cnt) d1 = direct(p + 2 * TPA);
+                    }
+                    const T g3[3] = {cur.g.x, cur.g.y, cur.g.z};
+                    const T r[3] = {cur.rx, cur.ry, cur.rz};
+    #pragma unroll
+                    for (int u = 0; u < 3; ++u) {
+                        F[u] += g3[u];
+    #pragma unroll
+                        for (int v = 0; v < 3; ++v) W[3 * u + v] -= g3[u] * r[v];
+                    }
+                    F[0] -= cr.x;
+                    F[1] -= cr.y;
+                    F[2] -= cr.z;
                 }
             }
         }

@@ -41,29 +41,40 @@ __device__ __forceinline__ int find_cfg(const int* cfg_off, int K, int i) {
 
 // Per-configuration geometry: inverse cell, perpendicular widths, bin counts and reach.
 __global__ void k_cells(int K, const double* cells, const int* cfg_off, double rsearch, CellDesc* d,
-                        int* bin_total, int* err) {
+                        int* bin_total, int* err, int* zero_a, int* zero_b, int n_zero) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    // the launch also clears the per-bin counters for k_bin_atoms and k_bin_scatter
+    for (int t = k; t < n_zero; t += gridDim.x * blockDim.x) zero_a[t] = zero_b[t] = 0;
     if (k >= K) return;
     CellDesc D;
     const double* H = cells + 9 * (size_t)k;
     for (int q = 0; q < 9; ++q) D.H[q] = H[q];
-    const double a = H[0], b = H[1], c = H[2], e = H[3], f = H[4], g = H[5], h = H[6], ii = H[7], jj = H[8];
-    // double-precision division and square root are long instruction sequences on this part, and
-    // this thread's chain is serial: one reciprocal, three reciprocal square roots, no divisions
-    const double det = a * (f * jj - g * ii) - b * (e * jj - g * h) + c * (e * ii - f * h);
-    const double id = 1.0 / det;
-    D.Hi[0] = (f * jj - g * ii) * id; D.Hi[1] = (c * ii - b * jj) * id; D.Hi[2] = (b * g - c * f) * id;
-    D.Hi[3] = (g * h - e * jj) * id; D.Hi[4] = (a * jj - c * h) * id; D.Hi[5] = (c * e - a * g) * id;
-    D.Hi[6] = (e * ii - f * h) * id; D.Hi[7] = (b * h - a * ii) * id; D.Hi[8] = (a * f - b * e) * id;
-    const double vol = fabs(det);
-    const double irs = 1.0 / rsearch;
-    double w[3];
+    // The inverse cell in double (fractional coordinates of atoms far from the origin need it),
+    // with a single reciprocal; the bin geometry below in float: this thread's chain is serial,
+    // and a double-precision division or square root costs many float operations here.  Float is
+    // enough for bins: counts and reaches keep 1e-5 relative margins, and the 1e-3 Angstrom band
+    // covers atoms binned slightly off; every neighbour decision is taken in double elsewhere.
+    {
+        const double a = H[0], b = H[1], c = H[2], e = H[3], f = H[4], g = H[5], h = H[6], ii = H[7], jj = H[8];
+        const double det = a * (f * jj - g * ii) - b * (e * jj - g * h) + c * (e * ii - f * h);
+        const double id = 1.0 / det;
+        D.Hi[0] = (f * jj - g * ii) * id; D.Hi[1] = (c * ii - b * jj) * id; D.Hi[2] = (b * g - c * f) * id;
+        D.Hi[3] = (g * h - e * jj) * id; D.Hi[4] = (a * jj - c * h) * id; D.Hi[5] = (c * e - a * g) * id;
+        D.Hi[6] = (e * ii - f * h) * id; D.Hi[7] = (b * h - a * ii) * id; D.Hi[8] = (a * f - b * e) * id;
+    }
+    const float a = (float)H[0], b = (float)H[1], c = (float)H[2], e = (float)H[3], f = (float)H[4],
+                g = (float)H[5], h = (float)H[6], ii = (float)H[7], jj = (float)H[8];
+    const float det = a * (f * jj - g * ii) - b * (e * jj - g * h) + c * (e * ii - f * h);
+    const float vol = fabsf(det);
+    const float irs = 1.f / (float)rsearch;
+    const float Hf[9] = {a, b, c, e, f, g, h, ii, jj};
+    float w[3];
     for (int q = 0; q < 3; ++q) {
-        const double* u = H + ((q + 1) % 3) * 3;
-        const double* v = H + ((q + 2) % 3) * 3;
-        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
-        w[q] = vol * rsqrt(cx * cx + cy * cy + cz * cz);
-        int nq = (int)floor(w[q] * irs * (1.0 - 1e-12));  // bins no thinner than the search radius
+        const float* u = Hf + ((q + 1) % 3) * 3;
+        const float* v = Hf + ((q + 2) % 3) * 3;
+        const float cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+        w[q] = vol * rsqrtf(cx * cx + cy * cy + cz * cz);
+        int nq = (int)floorf(w[q] * irs * (1.f - 1e-5f));  // bins no thinner than the search radius
         D.n[q] = nq < 1 ? 1 : (nq > 1024 ? 1024 : nq);
     }
     const long natoms = cfg_off[k + 1] - cfg_off[k];
@@ -76,21 +87,20 @@ __global__ void k_cells(int K, const double* cells, const int* cfg_off, double r
         if (D.n[0] * D.n[1] * D.n[2] == 1) break;
     }
     for (int q = 0; q < 3; ++q) {
-        // bins to visit: ceil((rsearch + band) / width) with width = w / n; rounded up for safety
-        int cq = (int)ceil((rsearch + kBand) * D.n[q] * (1.0 / w[q]) * (1.0 + 1e-12));
+        // bins to visit: ceil((rsearch + band) / width) with width = w / n, rounded up with a margin
+        int cq = (int)ceilf(((float)rsearch + (float)kBand) * (float)D.n[q] / w[q] * (1.f + 1e-5f));
         if (cq < 1) cq = 1;
         if (cq > kMaxImageReach) {
             atomicOr(err, kErrCellThin);
             cq = kMaxImageReach;
         }
         D.c[q] = cq;
-        const double inq = 1.0 / D.n[q];
+        const float inq = 1.f / (float)D.n[q];
         D.inv_n[q] = inq;
         for (int t = 0; t < 3; ++t) {
-            D.hn[3 * q + t] = (float)(H[3 * q + t] * inq);
-            const float hi = (float)H[3 * q + t];
-            D.hhi[3 * q + t] = hi;
-            D.hlo[3 * q + t] = (float)(H[3 * q + t] - (double)hi);
+            D.hn[3 * q + t] = Hf[3 * q + t] * inq;
+            D.hhi[3 * q + t] = Hf[3 * q + t];
+            D.hlo[3 * q + t] = (float)(H[3 * q + t] - (double)Hf[3 * q + t]);
         }
     }
     D.nbins = D.n[0] * D.n[1] * D.n[2];
@@ -116,12 +126,12 @@ __global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, i
         const double fq = x[0] * D.Hi[0 * 3 + q] + x[1] * D.Hi[1 * 3 + q] + x[2] * D.Hi[2 * 3 + q];
         const double fl = floor(fq);
         w[q] = (int)fl;
-        double fr = fq - fl;
-        int bq = (int)(fr * D.n[q]);
+        const float fr = (float)(fq - fl);
+        int bq = (int)(fr * (float)D.n[q]);
         if (bq < 0) bq = 0;
         if (bq >= D.n[q]) bq = D.n[q] - 1;
         b[q] = bq;
-        frac[q] = (double)w[q] + (double)bq * D.inv_n[q];  // bin origin: only the float prefilter uses it
+        frac[q] = (double)w[q] + (double)((float)bq * D.inv_n[q]);  // bin origin: only the float prefilter uses it
         if (w[q] > kMaxShift || w[q] < -kMaxShift) atomicOr(err, kErrShift);
     }
     double o[3], xw[3];
@@ -522,7 +532,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
 }
 
 // one thread per (slot, atom): binary search of the reverse pair (i, -s) in the neighbour's sorted
-// keys, stored atom-major so that one search stays within a few cache lines
+// keys, stored atom-major so that one search stays within a few cache lines; rev starts at -1
 __global__ void k_reverse(int n, int cap, const int* count, const int* jz,
                           const unsigned long long* keys_am, int* rev) {
     const size_t N = (size_t)n;
@@ -535,6 +545,9 @@ __global__ void k_reverse(int n, int cap, const int* count, const int* jz,
         const int sp = (int)(keys_am[(size_t)i * cap + p] & 0xffffffull);
         const int neg = ((256 - (sp & 255)) & 255) | (((256 - ((sp >> 8) & 255)) & 255) << 8) |
                         (((256 - ((sp >> 16) & 255)) & 255) << 16);
+        // each pair is searched once, from its canonical side (i < j, or s above -s for an atom's
+        // own images), which writes both slots; a pair without a partner keeps -1 (set before)
+        if (!(i < j || (i == j && sp > neg))) continue;
         const unsigned long long want = ((unsigned long long)i << 32) | (unsigned long long)neg;
         const unsigned long long* kj = keys_am + (size_t)j * cap;
         int lo = 0, hi = count[j] - 1, found = -1;
@@ -548,6 +561,7 @@ __global__ void k_reverse(int n, int cap, const int* count, const int* jz,
             if (key < want) lo = mid + 1; else hi = mid - 1;
         }
         rev[o] = found;
+        if (found >= 0) rev[(size_t)found * N + j] = p;
     }
 }
 
@@ -667,8 +681,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     const size_t realsz = fp64 ? 8 : 4;
     const size_t bins_max = N + K + 1;
     if (nb.count.reserve(N * 4) || nb.jz.reserve(N * cap * 4) ||
-        nb.rev.reserve(N * cap * 4) || nb.keys_am.reserve(N * cap * 8) || nb.rx.reserve(N * cap * realsz) || nb.ry.reserve(N * cap * realsz) ||
-        nb.rz.reserve(N * cap * realsz) || nb.cfg_of.reserve(N * 4) || nb.desc.reserve(sizeof(CellDesc) * K) ||
+        nb.rev.reserve(N * cap * 4) || nb.keys_am.reserve(N * cap * 8) || nb.rx.reserve(N * cap * realsz) || nb.ry.reserve(N * cap * realsz) || nb.rz.reserve(N * cap * realsz) || nb.cfg_of.reserve(N * 4) || nb.desc.reserve(sizeof(CellDesc) * K) ||
         nb.atom_bin.reserve(N * 4) || nb.atom_wrap.reserve(N * 4) || nb.atom_local.reserve(N * 16) || nb.atom_wp.reserve(N * 32) ||
         nb.bin_count.reserve(bins_max * 4) || nb.bin_start.reserve((bins_max + 1) * 4) ||
         nb.bin_fill.reserve(bins_max * 4) || nb.bin_atoms.reserve(N * 4 + 4) ||
@@ -686,11 +699,15 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     // counters: [0] bins handed out to configurations, [1] atoms handed out to bins
     int* counters = nb.counters.as<int>();
     cudaMemsetAsync(counters, 0, 2 * sizeof(int), st);
-    k_cells<<<(K + 127) / 128, 128, 0, st>>>(K, cells, cfg_off, rsearch, desc, counters, nb.err.as<int>());
-    ++launches;
     const int total_bins_upper = n + K;  // every configuration has at most max(1, atoms) bins
-    cudaMemsetAsync(bin_count, 0, (size_t)(total_bins_upper + 1) * 4, st);
-    cudaMemsetAsync(nb.bin_fill.p, 0, (size_t)(total_bins_upper + 1) * 4, st);
+    {
+        const int nz = total_bins_upper + 1;
+        int blocks = (std::max(K, nz) + 127) / 128;
+        if (blocks > 152 * 8) blocks = std::max(152 * 8, (K + 127) / 128);
+        k_cells<<<blocks, 128, 0, st>>>(K, cells, cfg_off, rsearch, desc, counters, nb.err.as<int>(), bin_count,
+                                        nb.bin_fill.as<int>(), nz);
+    }
+    ++launches;
     k_bin_atoms<<<(n + 63) / 64, 64, 0, st>>>(n, K, pos, types, S, cfg_off, desc, nb.cfg_of.as<int>(),
                                                 nb.atom_bin.as<int>(), nb.atom_wrap.as<int>(),
                                                 nb.atom_local.as<float4>(), nb.atom_wp.as<float4>(), bin_count,
@@ -761,6 +778,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
         const size_t total = N * (size_t)cap;
         size_t blocks = (total + 255) / 256;
         if (blocks > 152 * 64) blocks = 152 * 64;
+        cudaMemsetAsync(nb.rev.p, 0xff, sizeof(int) * total, st);
         k_reverse<<<(int)blocks, 256, 0, st>>>(n, cap, nb.count.as<int>(), nb.jz.as<int>(),
                                               nb.keys_am.as<unsigned long long>(), nb.rev.as<int>());
     }
