@@ -79,6 +79,11 @@ struct mtp_model {
     int64_t g_launches = 0;            // kernels in the graph
     int* h_flags = nullptr;            // pinned: error word and largest neighbour count of the last build
     int tpa_moments = 0, tpa_pairs = 0; // requested threads per atom (0 = chosen per call)
+    // the reverse-pair search runs on a side stream, overlapping the evaluation kernels; the force
+    // gather of the next evaluation waits for ev_join
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool rev_pending = false;
 };
 
 namespace {
@@ -211,9 +216,10 @@ mtp_status run_eval(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     int l;
     cudaEvent_t* marks = M->profiling ? M->ev_phase : nullptr;
     if constexpr (sizeof(T) == 8)
-        l = M->ops->eval_f64(a, st, M->n_sm, marks);
+        l = M->ops->eval_f64(a, st, M->n_sm, marks, M->rev_pending ? M->ev_join : nullptr);
     else
-        l = M->ops->eval_f32(a, st, M->n_sm, marks);
+        l = M->ops->eval_f32(a, st, M->n_sm, marks, M->rev_pending ? M->ev_join : nullptr);
+    M->rev_pending = false;
     if (l < 0) return MTP_EUNSUPPORTED;
     M->launches += l;
     if (keep) *keep = a;
@@ -244,6 +250,7 @@ mtp_status finish(mtp_model* M, cudaStream_t st) {
         return MTP_ENOMEM;
     }
     M->h_flags[0] = M->h_flags[1] = 0;
+    if (M->rev_pending) cudaStreamWaitEvent(st, M->ev_join, 0);  // side-stream work of the last build
     if (M->nb.err.p) {
         cudaMemcpyAsync(M->h_flags, M->nb.err.p, sizeof(int), cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(M->h_flags + 1, M->nb.max_seen.p, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -362,6 +369,9 @@ void mtp_destroy(mtp_model* M) {
     if (M->h_flags) cudaFreeHost(M->h_flags);
     if (M->g_exec) cudaGraphExecDestroy(M->g_exec);
     if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
+    if (M->side) cudaStreamDestroy(M->side);
+    if (M->ev_fork) cudaEventDestroy(M->ev_fork);
+    if (M->ev_join) cudaEventDestroy(M->ev_join);
     for (cudaEvent_t& e : M->ev_nbr)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t& e : M->ev_phase)
@@ -457,8 +467,21 @@ static mtp_status prepare_neighbors(mtp_model* M, int K, int n, const int* off, 
     }
     cudaMemsetAsync(M->nb.max_seen.p, 0, sizeof(int), st);
     if (M->profiling) mtp::record_mark(M->ev_nbr[0], st);
+    // a reverse search still running from a build that no evaluation consumed (mtp_neighbors) must
+    // finish before the lists are re-sized or rewritten
+    if (M->rev_pending && cap_status == cudaStreamCaptureStatusNone) {
+        cudaEventSynchronize(M->ev_join);
+        M->rev_pending = false;
+    }
+    if (!M->side) {  // created on first use
+        if (cudaStreamCreateWithFlags(&M->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming) != cudaSuccess)
+            return cuda_status(cudaGetLastError());
+    }
     const int l = mtp::build_neighbors(M->nb, K, n, off, pos, types, cells, M->rcut + skin, is_fp64(M), M->cap,
-                                       st, M->S);
+                                       st, M->S, M->side, M->ev_fork, M->ev_join);
+    M->rev_pending = true;
     if (M->profiling) mtp::record_mark(M->ev_nbr[1], st);
     if (l < 0) return cuda_status(cudaGetLastError());
     M->launches += l;

@@ -53,10 +53,14 @@ struct NbrState {
 };
 
 // Build the neighbour list of a batch (device inputs).  r_ij are written in float or double.
-// Returns the number of kernels launched, or -1 on a CUDA error (cudaGetLastError holds it).
+// With a side stream, the reverse-pair slots (needed only by the force gather) are computed there,
+// after `fork` is recorded on st, and `join` is recorded when they are done: the caller makes the
+// gather wait on `join`.  Returns the number of kernels launched, or -1 on a CUDA error
+// (cudaGetLastError holds it).
 int build_neighbors(NbrState& nb, int n_cfg, int n_atoms, const int* cfg_off, const double* pos,
                     const int* types, const double* cells, double rsearch, bool fp64, int cap,
-                    cudaStream_t st, int n_species);
+                    cudaStream_t st, int n_species, cudaStream_t side = nullptr, cudaEvent_t fork = nullptr,
+                    cudaEvent_t join = nullptr);
 
 // Exclusive prefix sum of n ints: out[0..n] with out[n] = total; tmp holds >= scan_tmp_ints(n) ints.
 size_t scan_tmp_ints(int n);

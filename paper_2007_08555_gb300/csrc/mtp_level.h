@@ -22,8 +22,9 @@ struct LevelOps {
     int flop_pair_moments, flop_pair_adjoint, flop_atom_program;
     int contract_parts, contract_slots;  // float contraction parts and their dV/dM slots per atom
     // launchers (stream-ordered, no synchronisation); return the number of kernels launched
-    int (*eval_f32)(const EvalCtx<float>&, cudaStream_t, int n_sm, cudaEvent_t* marks);
-    int (*eval_f64)(const EvalCtx<double>&, cudaStream_t, int n_sm, cudaEvent_t* marks);
+    // gather_after (or NULL): an event the force gather waits for (the reverse-pair slots)
+    int (*eval_f32)(const EvalCtx<float>&, cudaStream_t, int n_sm, cudaEvent_t* marks, cudaEvent_t gather_after);
+    int (*eval_f64)(const EvalCtx<double>&, cudaStream_t, int n_sm, cudaEvent_t* marks, cudaEvent_t gather_after);
     // loss gradient after an evaluation: residuals -> tangent moments -> dual contraction -> dc
     int (*grad_f32)(EvalCtx<float>&, const LossArgs&, cudaStream_t, int n_sm);
     int (*grad_f64)(EvalCtx<double>&, const LossArgs&, cudaStream_t, int n_sm);

@@ -799,7 +799,7 @@ int launch_pairs_tpa(const EvalCtx<T>& a, cudaStream_t st, int n_sm, bool moment
 }
 
 template <class T>
-int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks) {
+int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks, cudaEvent_t gather_after) {
     if (a.n_atoms == 0) return 0;
     int launches = 0;
     if (marks) record_mark(marks[kPhaseMoments], st);
@@ -847,6 +847,7 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks)
     }
     if (marks) record_mark(marks[kPhasePairgrad], st);
     launches += launch_pairs_tpa<T>(a, st, n_sm, false);
+    if (gather_after) cudaStreamWaitEvent(st, gather_after, 0);
     if (marks) record_mark(marks[kPhaseGather], st);
     {
         const int threads = 128;
@@ -865,11 +866,11 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks)
     return launches;
 }
 
-int eval_f32(const EvalCtx<float>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks) {
-    return eval_all<float>(a, st, n_sm, marks);
+int eval_f32(const EvalCtx<float>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks, cudaEvent_t gather_after) {
+    return eval_all<float>(a, st, n_sm, marks, gather_after);
 }
-int eval_f64(const EvalCtx<double>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks) {
-    return eval_all<double>(a, st, n_sm, marks);
+int eval_f64(const EvalCtx<double>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks, cudaEvent_t gather_after) {
+    return eval_all<double>(a, st, n_sm, marks, gather_after);
 }
 
 

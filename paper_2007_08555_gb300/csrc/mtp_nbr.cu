@@ -675,7 +675,8 @@ int scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_t st) {
 }
 
 int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double* pos, const int* types,
-                    const double* cells, double rsearch, bool fp64, int cap, cudaStream_t st, int S) {
+                    const double* cells, double rsearch, bool fp64, int cap, cudaStream_t st, int S,
+                    cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
     int launches = 0;
     const size_t N = (size_t)n;
     const size_t realsz = fp64 ? 8 : 4;
@@ -778,9 +779,16 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
         const size_t total = N * (size_t)cap;
         size_t blocks = (total + 255) / 256;
         if (blocks > 152 * 64) blocks = 152 * 64;
-        cudaMemsetAsync(nb.rev.p, 0xff, sizeof(int) * total, st);
-        k_reverse<<<(int)blocks, 256, 0, st>>>(n, cap, nb.count.as<int>(), nb.jz.as<int>(),
+        cudaStream_t rs = st;
+        if (side) {  // overlaps the moments, contraction and pair-gradient kernels
+            cudaEventRecord(fork, st);
+            cudaStreamWaitEvent(side, fork, 0);
+            rs = side;
+        }
+        cudaMemsetAsync(nb.rev.p, 0xff, sizeof(int) * total, rs);
+        k_reverse<<<(int)blocks, 256, 0, rs>>>(n, cap, nb.count.as<int>(), nb.jz.as<int>(),
                                               nb.keys_am.as<unsigned long long>(), nb.rev.as<int>());
+        if (side) cudaEventRecord(join, side);
     }
     ++launches;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
