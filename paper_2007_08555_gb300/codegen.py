@@ -584,7 +584,7 @@ def _closure(monos):
     return need
 
 
-def emit_slice_functions(prog: Program, slc, tag):
+def emit_slice_functions(prog: Program, slc, tag, slot_begin=None):
     """Specialisations Slice<tag><S> for every slice S (a list of (monomials, component indices)):
        mom(x,y,z,f,acc):   acc[t] += f[mu] * x^a y^b z^c                    (moments, Sec. 2.1)
        grad(x,y,z,f,df,adj,s,gx,gy,gz):
@@ -594,6 +594,14 @@ def emit_slice_functions(prog: Program, slc, tag):
     for si, (monos, comps) in enumerate(slc):
         out.append(f"template <> struct {name}<{si}> {{")
         out.append(f"  static constexpr int BEGIN = {min(comps)}, SIZE = {len(comps)};")
+        if slot_begin is not None:
+            # dV/dM of this slice's components from the contraction parts' slots (slot order)
+            out.append("  template <class T> static __device__ __forceinline__ void adj_from_slots("
+                       "const T* __restrict__ sl, T* __restrict__ adj) {")
+            for t, ci in enumerate(comps):
+                terms = [f"sl[{s * 32}]" for s in range(slot_begin[ci], slot_begin[ci + 1])] or ["T(0)"]
+                out.append(f"    adj[{t}] = " + " + ".join(terms) + ";")
+            out.append("  }")
         need = _closure(monos)
         out.append("  template <class T> static __device__ __forceinline__ void mom(const T x, const T y, const T z, "
                    "const T* __restrict__ f, T* __restrict__ acc) {")
@@ -889,19 +897,22 @@ def emit_level(L, outdir):
         lines.append(f"static const int {name}_size[] = {{" + ",".join(str(len(c)) for _, c in sl) + "};")
         for s, (_, comps) in enumerate(sl):
             assert comps == list(range(min(comps), min(comps) + len(comps)))
-    nparts, nslots = 1, 0
+    nparts, nslots, has_parts = 1, 0, False
     if L <= UNROLLED_MAX_LEVEL and prog.ops:
+        has_parts = True
         nparts = CONTRACT_PARTS.get(L, 1)
         part_lines = emit_parts(prog, nparts)
+        slot_begin = [int(x) for x in part_lines[2].split("{")[1].rstrip("};").split(",")]
         nslots = int(part_lines[1].split("NSLOT = ")[1].rstrip(";"))
         lines += part_lines
     else:
         lines.append("#define MTPGEN_HAS_PARTS 0")
-    lines += emit_slice_functions(prog, s32, "f")
+    lines += emit_slice_functions(prog, s32, "f", slot_begin if has_parts else None)
     lines += emit_slice_functions(prog, s64, "d")
     lines.append("struct Traits {")
     lines.append("  static constexpr int L_ = L, C_ = C, V_ = V, M_ = M, NMU_ = NMU, NUMAX_ = NUMAX, NS32_ = NS32, NS64_ = NS64;")
     lines.append(f"  static constexpr int NPART_ = {nparts}, NSLOT_ = {max(nslots, 1)};")
+    lines.append(f"  static constexpr bool HAS_PARTS_ = {'true' if has_parts else 'false'};")
     lines.append("  template <int S> using F32 = SliceF<S>;")
     lines.append("  template <int S> using F64 = SliceD<S>;")
     lines.append("};")

@@ -475,7 +475,8 @@ __global__ void __launch_bounds__(256) k_contract(const EvalCtx<T> a) {
 // Float contraction, split into NPART generated parts (basis functions grouped so that one part's
 // values fit in registers): warp w runs part w / n_tiles for the 32 atoms of tile w % n_tiles, so
 // that the warps on an SM mostly run the same code.  Each part writes its site-energy share and
-// dV/dM of its moments to slots; k_contract_sum adds them up in a fixed order.
+// dV/dM of its moments to slots; the pair-gradient kernel adds the slots of each component and the
+// gather the energy shares, in a fixed order.
 __global__ void __launch_bounds__(128) k_contract_parts(const EvalCtx<float> a) {
     const int lane = threadIdx.x & 31;
     const int n_tiles = (a.n_atoms + 31) >> 5;
@@ -493,9 +494,9 @@ __global__ void __launch_bounds__(128) k_contract_parts(const EvalCtx<float> a) 
     }
 }
 
-// dV/dM_c = sum of its slots (slot order), site energies = sum of the parts' shares (part order),
-// configuration energies accumulated in double
-__global__ void __launch_bounds__(128) k_contract_sum(const EvalCtx<float> a) {
+// dV/dM_c = sum of its slots in slot order (the loss gradient needs dV/dM itself; the evaluation
+// reads the slots directly)
+__global__ void __launch_bounds__(128) k_adjm_from_slots(const EvalCtx<float> a) {
     constexpr int C = G::C_;
     const int lane = threadIdx.x & 31;
     const int n_tiles = (a.n_atoms + 31) >> 5;
@@ -509,40 +510,6 @@ __global__ void __launch_bounds__(128) k_contract_sum(const EvalCtx<float> a) {
         for (int s = s0; s < s1; ++s) acc += sl[s * 32];
         a.adjm[((size_t)tile * C + c) * 32 + lane] = acc;
     }
-    const int stride = gridDim.x * blockDim.x;
-    __shared__ double s_e[128];
-    __shared__ int s_c[128];
-    double erun = 0.0;
-    int ecfg = -1;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_atoms; i += stride) {
-        float e = 0.f;
-#pragma unroll
-        for (int p = 0; p < G::NPART_; ++p) e += a.epart[(size_t)p * a.n_atoms + i];
-        if (a.site) a.site[i] = (double)e;
-        const int cfg = a.cfg_of[i];
-        if (cfg != ecfg) {
-            flush_sum(a.energy, ecfg, erun);
-            ecfg = cfg;
-            erun = 0.0;
-        }
-        erun += (double)e;
-    }
-    // block-level combine (tree when the block ends in one configuration)
-    s_c[threadIdx.x] = ecfg;
-    __syncthreads();
-    const int c0 = s_c[0];
-    const bool uniform = __syncthreads_and(ecfg == c0 || ecfg < 0) && c0 >= 0;
-    if (!uniform) {
-        flush_sum(a.energy, ecfg, erun);
-        return;
-    }
-    s_e[threadIdx.x] = erun;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) s_e[threadIdx.x] += s_e[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) flush_sum(a.energy, c0, s_e[0]);
 }
 #endif
 
@@ -566,9 +533,17 @@ template <class T, int S, int TPA>
 __device__ __forceinline__ void pairgrad_slice(const EvalCtx<T>& a, int i, int sub, int zi, int cnt, const T* cs) {
     using SL = typename SliceSel<T, S>::type;
     T adjs[SL::SIZE];
-    const T* src = a.adjm + (size_t)(i >> 5) * G::C_ * 32 + (i & 31);
+#if MTPGEN_HAS_PARTS
+    if constexpr (sizeof(T) == 4) {
+        // dV/dM straight from the contraction parts' slots (fixed order, as k_adjm_from_slots)
+        SL::template adj_from_slots<T>(a.aslots + (size_t)(i >> 5) * G::NSLOT_ * 32 + (i & 31), adjs);
+    } else
+#endif
+    {
+        const T* src = a.adjm + (size_t)(i >> 5) * G::C_ * 32 + (i & 31);
 #pragma unroll
-    for (int t = 0; t < SL::SIZE; ++t) adjs[t] = src[(size_t)(SL::BEGIN + t) * 32];
+        for (int t = 0; t < SL::SIZE; ++t) adjs[t] = src[(size_t)(SL::BEGIN + t) * 32];
+    }
     const size_t n = (size_t)a.n_atoms;
     const int csz = CoefPad<T>::value * a.NQ;
     // the next pair's loads are issued before this pair's arithmetic (their latency overlaps it)
@@ -620,6 +595,16 @@ __global__ void __launch_bounds__(128) k_pairgrad(const EvalCtx<T> a) {
 // ----------------------------------------------------------------------------------------------
 // k_gather: forces and virial
 // ----------------------------------------------------------------------------------------------
+// running per-configuration sums of the gather: virial (9) and energy
+template <class T>
+__device__ __forceinline__ void flush_run(const EvalCtx<T>& a, int cfg, const double* run, bool want_e) {
+    if (a.virial) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) atomicAdd(&a.virial[(size_t)cfg * 9 + k], run[k]);
+    }
+    if (want_e) atomicAdd(&a.energy[cfg], run[9]);
+}
+
 template <class T>
 struct GatherIn {
     Vec4<T> g;
@@ -629,14 +614,21 @@ struct GatherIn {
 
 template <class T, int TPA>
 __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<T> a) {
+    // float path with contraction parts: the site energies are the sums of the parts' shares
+#if MTPGEN_HAS_PARTS
+    constexpr bool kE = sizeof(T) == 4;
+#else
+    constexpr bool kE = false;
+#endif
+    const bool want_e = kE && a.energy != nullptr;
     __shared__ int s_cfg[128];
-    __shared__ double s_w[9][128];
+    __shared__ double s_w[10][128];
     const size_t n = (size_t)a.n_atoms;
     const int stride = gridDim.x * blockDim.x;
     const int n_groups = ((a.n_atoms + 31) / 32) * 32;  // whole warps stay converged for the shuffles
-    double Wrun[9];
+    double Wrun[10];  // virial, then energy
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Wrun[k] = 0.0;
+    for (int k = 0; k < 10; ++k) Wrun[k] = 0.0;
     int wcfg = -1;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups * TPA; g += stride) {
         const int i = g / TPA, sub = g % TPA;
@@ -728,21 +720,29 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
             a.forces[3 * (size_t)i + 1] = (double)F[1];
             a.forces[3 * (size_t)i + 2] = (double)F[2];
         }
-        if (active && a.virial) {
+        double e_i = 0.0;
+        if constexpr (kE) {
+            if (active && sub == 0) {
+                float e = 0.f;
+#pragma unroll
+                for (int p = 0; p < G::NPART_; ++p) e += a.epart[(size_t)p * n + i];
+                if (a.site) a.site[i] = (double)e;
+                e_i = (double)e;
+            }
+        }
+        if (active && (a.virial || want_e)) {
             if (cfg != wcfg) {
-                if (wcfg >= 0) {
+                if (wcfg >= 0) flush_run(a, wcfg, Wrun, want_e);
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) atomicAdd(&a.virial[(size_t)wcfg * 9 + k], Wrun[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < 9; ++k) Wrun[k] = 0.0;
+                for (int k = 0; k < 10; ++k) Wrun[k] = 0.0;
                 wcfg = cfg;
             }
 #pragma unroll
             for (int k = 0; k < 9; ++k) Wrun[k] += (double)W[k];
+            Wrun[9] += e_i;
         }
     }
-    if (!a.virial) return;
+    if (!a.virial && !want_e) return;
     // block-level combine of the running sums: a tree reduction when the whole block ends in one
     // configuration (large cells), otherwise one atomic per thread and component
     s_cfg[threadIdx.x] = wcfg;
@@ -750,23 +750,21 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
     const int c0 = s_cfg[0];
     const bool uniform = __syncthreads_and(wcfg == c0 || wcfg < 0) && c0 >= 0;
     if (!uniform) {
-        if (wcfg >= 0) {
-#pragma unroll
-            for (int k = 0; k < 9; ++k) atomicAdd(&a.virial[(size_t)wcfg * 9 + k], Wrun[k]);
-        }
+        if (wcfg >= 0) flush_run(a, wcfg, Wrun, want_e);
         return;
     }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) s_w[k][threadIdx.x] = Wrun[k];
+    for (int k = 0; k < 10; ++k) s_w[k][threadIdx.x] = Wrun[k];
     __syncthreads();
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
         if (threadIdx.x < h) {
 #pragma unroll
-            for (int k = 0; k < 9; ++k) s_w[k][threadIdx.x] += s_w[k][threadIdx.x + h];
+            for (int k = 0; k < 10; ++k) s_w[k][threadIdx.x] += s_w[k][threadIdx.x + h];
         }
         __syncthreads();
     }
-    if (threadIdx.x < 9) atomicAdd(&a.virial[(size_t)c0 * 9 + threadIdx.x], s_w[threadIdx.x][0]);
+    if (threadIdx.x < 9 && a.virial) atomicAdd(&a.virial[(size_t)c0 * 9 + threadIdx.x], s_w[threadIdx.x][0]);
+    if (threadIdx.x == 9 && want_e) atomicAdd(&a.energy[c0], s_w[9][0]);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -812,11 +810,7 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks,
         int blocks = (int)((warps + 3) / 4);
         if (blocks > n_sm * 16) blocks = n_sm * 16;
         k_contract_parts<<<blocks, threads, 0, st>>>(a);
-        const long sums = (long)((a.n_atoms + 31) / 32) * G::C_ * 32;
-        int sblocks = (int)((sums + threads - 1) / threads);
-        if (sblocks > n_sm * 32) sblocks = n_sm * 32;
-        k_contract_sum<<<sblocks, threads, 0, st>>>(a);
-        launches += 2;
+        ++launches;
         if (a.b_rows) {  // the caller provides per-atom rows whenever b rows are requested
             k_brows<T><<<a.n_cfg, 128, 0, st>>>(a, a.cfg_off);
             ++launches;
@@ -1224,6 +1218,15 @@ int launch_grad_pairs(EvalCtx<T>& a, cudaStream_t st, int n_sm) {
 template <class T>
 int grad_all(EvalCtx<T>& a, const LossArgs& L, cudaStream_t st, int n_sm) {
     int launches = 0;
+#if MTPGEN_HAS_PARTS
+    if constexpr (sizeof(T) == 4) {  // dV/dM itself, from the contraction parts' slots
+        const long work = (long)((a.n_atoms + 31) / 32) * G::C_ * 32;
+        int blocks = (int)((work + 127) / 128);
+        if (blocks > n_sm * 32) blocks = n_sm * 32;
+        if (blocks > 0) k_adjm_from_slots<<<blocks, 128, 0, st>>>(a);
+        ++launches;
+    }
+#endif
     T* D = const_cast<T*>(a.gD);
     T* eps = const_cast<T*>(a.geps);
     k_resid_atoms<T><<<min((a.n_atoms + 127) / 128 + 1, n_sm * 8), 128, 0, st>>>(a, L, D);
