@@ -132,8 +132,8 @@ mtp_status status_from_err(int err) {
 }
 
 // Threads per atom: enough threads for the whole GPU (want per SM), as few lanes per atom as that
-// allows.  The moments kernel reduces every component over its lanes, so it wants fewer lanes than
-// the pair-gradient and gather kernels, which write per pair.
+// allows.  The moments and pair-gradient kernels hold a whole slice of components per lane (and
+// the moments kernel reduces it over the lanes), so they want fewer lanes than the gather.
 int choose_tpa(int n_atoms, int n_sm, int per_sm) {
     const long want = (long)n_sm * per_sm;
     if (n_atoms >= want) return 1;

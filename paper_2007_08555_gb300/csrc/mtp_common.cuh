@@ -54,8 +54,8 @@ struct EvalCtx {
     int adj_layers;
     const float* weights;               // [n_weights] op weights
     int n_weights;
-    int tpa;              // threads per atom in the pair-gradient and gather kernels (1, 2, 4 or 8)
-    int tpa_m;            // threads per atom in the moments kernel
+    int tpa;              // threads per atom in the gather and loss-gradient kernels (1, 2, 4 or 8)
+    int tpa_m;            // threads per atom in the moments and pair-gradient kernels
     T* mom;               // [ceil(n/32)][C][32] moment components (tile layout)
     T* adjm;              // [ceil(n/32)][C][32] dV/dM
     T* aslots;            // [ceil(n/32)][NSLOT][32] dV/dM shares of the contraction parts (float path)

@@ -788,7 +788,7 @@ int launch_pairs(const EvalCtx<T>& a, cudaStream_t st, int n_sm, bool moments) {
 
 template <class T>
 int launch_pairs_tpa(const EvalCtx<T>& a, cudaStream_t st, int n_sm, bool moments) {
-    switch (moments ? a.tpa_m : a.tpa) {
+    switch (a.tpa_m) {
         case 8: return launch_pairs<T, 8>(a, st, n_sm, moments);
         case 4: return launch_pairs<T, 4>(a, st, n_sm, moments);
         case 2: return launch_pairs<T, 2>(a, st, n_sm, moments);
