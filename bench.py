@@ -360,15 +360,24 @@ def run_batch(args):
     A, _, _ = mtp.mtp_get_active_set(m64.h, m)
     mtp.mtp_set_active_set(model.h, A)
     t_sel = time.perf_counter() - t0
-    ms = _timed(lambda: model.eval_batch(pos, types, cells, off, grade_cfg=True, grade_atom=True), args.steps,
-                args.warmup, stream)
-    ms_eval = _timed(lambda: model.eval_batch(pos, types, cells, off), args.steps, args.warmup, stream)
-    ms64 = _timed(lambda: m64.eval_batch(pos, types, cells, off), max(2, args.steps // 4), 1, stream)
+    outs = {}
+
+    def call(mod, key, **kw):  # the same output tensors every call: the library replays its CUDA graph
+        outs[key] = mod.eval_batch(pos, types, cells, off, out=outs.get(key), **kw)
+
+    # the workload: E/F/W plus the grade of every configuration (Sec. 2.3)
+    ms = _timed(lambda: call(model, "cfg", grade_cfg=True), args.steps, args.warmup, stream)
+    # per-atom grades as well (a diagnostic: one [atoms x m] x [m x m] product in double precision)
+    ms_atom = _timed(lambda: call(model, "atom", grade_cfg=True, grade_atom=True), args.steps, args.warmup, stream)
+    ms_eval = _timed(lambda: call(model, "eval"), args.steps, args.warmup, stream)
+    ms64 = _timed(lambda: call(m64, "fp64"), max(2, args.steps // 4), 1, stream)
     n = b.n_atoms
-    _line(args, "4096 cells, E+F+W + per-cell and per-atom MaxVol grades", n / (ms * 1e-3), ms,
+    _line(args, "4096 cells, E+F+W + per-cell MaxVol grades", n / (ms * 1e-3), ms,
           {"workload": f"4096 strained fcc/bcc/hcp cells of 8-256 atoms ({n} atoms), 1-3 species, lev_max=16",
            "n_atoms": n, "n_cfg": 4096, "l2": "inputs ~12 MB, not flushed"},
-          {"eval_only_atoms_per_s": round(n / (ms_eval * 1e-3), 1), "fp64_path_atoms_per_s": round(n / (ms64 * 1e-3), 1),
+          {"eval_only_atoms_per_s": round(n / (ms_eval * 1e-3), 1),
+           "with_atom_grades_atoms_per_s": round(n / (ms_atom * 1e-3), 1),
+           "fp64_path_atoms_per_s": round(n / (ms64 * 1e-3), 1),
            "maxvol": {"rows": 2 * m, "m": m, "swaps": swaps, "select_s_incl_host": round(t_sel, 3)}})
 
 
