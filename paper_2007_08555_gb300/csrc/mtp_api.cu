@@ -156,8 +156,10 @@ mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     if (M->mom.reserve(tiles * M->C * 32 * sizeof(T)) || M->adjm.reserve(tiles * M->C * 32 * sizeof(T)) ||
         M->gx.reserve(N * cap * sizeof(mtp::Vec4<T>)))
         return MTP_ENOMEM;
-    if (energy) cudaMemsetAsync(energy, 0, sizeof(double) * K, st);
-    if (virial) cudaMemsetAsync(virial, 0, sizeof(double) * 9 * K, st);
+    if (n == 0) {  // otherwise the moments kernel clears them
+        if (energy) cudaMemsetAsync(energy, 0, sizeof(double) * K, st);
+        if (virial) cudaMemsetAsync(virial, 0, sizeof(double) * 9 * K, st);
+    }
     if (brows) cudaMemsetAsync(brows, 0, sizeof(double) * (size_t)M->m * K, st);
     a = mtp::EvalCtx<T>{};
     a.n_atoms = n;
@@ -253,7 +255,7 @@ mtp_status finish(mtp_model* M, cudaStream_t st) {
     if (M->rev_pending) cudaStreamWaitEvent(st, M->ev_join, 0);  // side-stream work of the last build
     if (M->nb.err.p) {
         cudaMemcpyAsync(M->h_flags, M->nb.err.p, sizeof(int), cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(M->h_flags + 1, M->nb.max_seen.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(M->h_flags + 1, M->nb.counters.as<int>() + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
         cudaMemsetAsync(M->nb.err.p, 0, sizeof(int), st);
     }
     cudaError_t e = cudaStreamSynchronize(st);
@@ -356,7 +358,7 @@ void mtp_destroy(mtp_model* M) {
                       &M->nb.count, &M->nb.jz, &M->nb.rev, &M->nb.rx, &M->nb.ry, &M->nb.rz,
                       &M->nb.cfg_of, &M->nb.desc, &M->nb.atom_bin, &M->nb.atom_wrap, &M->nb.atom_local,
                       &M->nb.bin_count, &M->nb.bin_start, &M->nb.bin_fill, &M->nb.bin_atoms, &M->nb.counters,
-                      &M->nb.err, &M->nb.max_seen, &M->g_energy, &M->g_forces, &M->g_virial, &M->g_D, &M->g_eps, &M->g_ew,
+                      &M->nb.err, &M->g_energy, &M->g_forces, &M->g_virial, &M->g_D, &M->g_eps, &M->g_ew,
                       &M->g_momt, &M->g_adjmt, &M->g_out, &M->g_refs, &M->md_F, &M->md_scalars, &M->md_masses,
                       &M->md_flag, &M->nb.x0, &M->nb.cx, &M->nb.cy, &M->nb.cz, &M->d_A, &M->d_Ai, &M->mv_Bs, &M->mv_D, &M->mv_W, &M->mv_perm, &M->mv_sel,
                       &M->mv_C, &M->mv_status, &M->mv_swaps, &M->mv_gmax, &M->s_rows, &M->s_gamma, &M->g_brows,
@@ -462,10 +464,9 @@ static mtp_status prepare_neighbors(mtp_model* M, int K, int n, const int* off, 
     cudaStreamIsCapturing(st, &cap_status);
     if (cap_status == cudaStreamCaptureStatusNone) M->g_sig.clear();  // scratch may be re-sized: no replay
     if (!M->nb.err.p) {  // the error word starts at zero and is cleared after every read
-        if (M->nb.err.reserve(4) || M->nb.max_seen.reserve(4)) return MTP_ENOMEM;
+        if (M->nb.err.reserve(4) || M->nb.counters.reserve(16)) return MTP_ENOMEM;
         if (cudaMemset(M->nb.err.p, 0, M->nb.err.bytes) != cudaSuccess) return MTP_ECUDA;
     }
-    cudaMemsetAsync(M->nb.max_seen.p, 0, sizeof(int), st);
     if (M->profiling) mtp::record_mark(M->ev_nbr[0], st);
     // a reverse search still running from a build that no evaluation consumed (mtp_neighbors) must
     // finish before the lists are re-sized or rewritten

@@ -46,7 +46,7 @@ struct NbrState {
     double rsearch = 0.0;
     DevBuf count, jz, rev, rx, ry, rz, keys_am;
     DevBuf cfg_of, desc, atom_bin, atom_wrap, atom_local, atom_wp, bin_count, bin_start, bin_fill, bin_atoms, counters;
-    DevBuf err, max_seen;
+    DevBuf err;
     // reuse with a skin: positions at the build and the current displacements (float or double)
     DevBuf x0, cx, cy, cz;
     bool has_x0 = false;

@@ -302,6 +302,15 @@ __global__ void __launch_bounds__(128) k_moments(const EvalCtx<T> a) {
     load_c(a, cs);
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
+    // the first evaluation kernel clears the per-configuration sums (energy, virial) that later
+    // kernels accumulate
+    for (int t = gtid; t < 10 * a.n_cfg; t += stride) {
+        if (t < a.n_cfg) {
+            if (a.energy) a.energy[t] = 0.0;
+        } else if (a.virial) {
+            a.virial[t - a.n_cfg] = 0.0;
+        }
+    }
     const int n_groups = ((a.n_atoms + 31) / 32) * 32;  // whole warps stay converged for the shuffles
     for (int g = gtid; g < n_groups * TPA; g += stride) {
         const int i = g / TPA, sub = g % TPA;

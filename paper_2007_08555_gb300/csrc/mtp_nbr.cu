@@ -687,7 +687,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
         nb.bin_count.reserve(bins_max * 4) || nb.bin_start.reserve((bins_max + 1) * 4) ||
         nb.bin_fill.reserve(bins_max * 4) || nb.bin_atoms.reserve(N * 4 + 4) ||
         nb.counters.reserve(16) ||
-        nb.err.reserve(4) || nb.max_seen.reserve(4))
+        nb.err.reserve(4))
         return -1;
     nb.n_atoms = n;
     nb.n_cfg = K;
@@ -697,9 +697,10 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     CellDesc* desc = nb.desc.as<CellDesc>();
     int* bin_count = nb.bin_count.as<int>();
     int* bin_start = nb.bin_start.as<int>();
-    // counters: [0] bins handed out to configurations, [1] atoms handed out to bins
+    // counters: [0] bins handed out to configurations, [1] atoms handed out to bins, [2] largest
+    // neighbour count seen
     int* counters = nb.counters.as<int>();
-    cudaMemsetAsync(counters, 0, 2 * sizeof(int), st);
+    cudaMemsetAsync(counters, 0, 3 * sizeof(int), st);
     const int total_bins_upper = n + K;  // every configuration has at most max(1, atoms) bins
     {
         const int nz = total_bins_upper + 1;
@@ -748,7 +749,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     a.ry = nb.ry.p;
     a.rz = nb.rz.p;
     a.err = nb.err.as<int>();
-    a.max_seen = nb.max_seen.as<int>();
+    a.max_seen = nb.counters.as<int>() + 2;
     a.nbins = total_bins_upper;
     const size_t smem = build_smem(cap, realsz);
     // one block per bin when they fit in one wave (a perturbed lattice has ~12 atoms per bin)
