@@ -843,6 +843,89 @@ def emit_parts(prog: Program, parts: int):
     return out
 
 
+# Parts of the tangent (forward-over-reverse) contraction of the loss gradient: every value carries
+# a tangent, so a part holds twice the values of a forward part and wants more parts.
+DUAL_PARTS = {2: 1, 4: 1, 6: 1, 8: 1, 10: 1, 12: 2, 14: 4, 16: 8, 18: 16, 20: 16}
+
+
+def emit_dual_parts(prog: Program, parts: int):
+    """Straight-line tangent contraction split into parts, for the loss gradient (Sec. 2.2).  Part g
+    reads moments M and their tangents T (directional derivatives along the force and stress
+    residuals) for its sub-network, evaluates values v and tangents t (t_k = sum w (t_i v_j + v_i t_j)),
+    adds ek v - t of its basis functions over the warp's 32 atoms into dxt[alpha] (lane 0 writes),
+    then runs the adjoint a and its tangent at (seeds: xi, 0) and writes dV/dM and its tangent of
+    its moments to dual slots (adj[slot * 32], adt[slot * 32]), numbered by component then part."""
+    C = len(prog.comp_list)
+    by_k = defaultdict(list)
+    for (k, i, j, w) in prog.ops:
+        by_k[k].append((i, j, w))
+    groups = partition_program(prog, parts)
+    slot_of = {}
+    slot_begin = []
+    for c in range(C):
+        slot_begin.append(len(slot_of))
+        for g, (vals, _) in enumerate(groups):
+            if c in vals:
+                slot_of[(g, c)] = len(slot_of)
+    slot_begin.append(len(slot_of))
+    out = [f"constexpr int NDPART = {parts}, NDSLOT = {len(slot_of)};",
+           "static __device__ const int dslot_begin[] = {" + ",".join(map(str, slot_begin)) + "};",
+           "template <int PART> struct DPart;"]
+
+    def lit(w):
+        return "" if w == 1.0 else f"{w!r}f * "
+
+    for g, (vals, alphas) in enumerate(groups):
+        out.append(f"template <> struct DPart<{g}> {{")
+        out.append("  static __device__ __forceinline__ void run(const float* __restrict__ m, const float* __restrict__ mt, "
+                   "float* __restrict__ adj, float* __restrict__ adt, const float* __restrict__ xi, double ek, bool act, "
+                   "bool lane0, double* __restrict__ dxt) {")
+        comps = sorted(v for v in vals if v < C)
+        for c in comps:
+            out.append(f"    const float v{c} = m[{c * 32}], t{c} = mt[{c * 32}];")
+        inner = sorted(v for v in vals if v >= C)
+        for k in inner:
+            out.append(f"    const float v{k} = " + " + ".join(f"{lit(w)}v{i} * v{j}" for (i, j, w) in by_k[k]) + ";")
+            out.append(f"    const float t{k} = " + " + ".join(f"{lit(w)}(t{i} * v{j} + v{i} * t{j})"
+                                                           for (i, j, w) in by_k[k]) + ";")
+        seed = defaultdict(list)
+        for a in alphas:
+            v = prog.basis_value[a]
+            seed[v].append(a)
+            out.append(f"    {{ double d = act ? ek * (double)v{v} - (double)t{v} : 0.0;")
+            out.append("      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);")
+            out.append(f"      if (lane0) dxt[{a}] = d; }}")
+        declared = set()
+
+        def aref(v):
+            if v not in declared:
+                declared.add(v)
+                init = " + ".join(f"xi[{a}]" for a in seed.get(v, [])) or "0.f"
+                out.append(f"    float a{v} = {init}, b{v} = 0.f;")
+            return f"a{v}", f"b{v}"
+
+        for k in reversed(inner):
+            ak, bk = aref(k)
+            for (i, j, w) in by_k[k]:
+                ai, bi = aref(i)
+                aj, bj = aref(j)
+                out.append(f"    {ai} += {lit(w)}v{j} * {ak}; {bi} += {lit(w)}(t{j} * {ak} + v{j} * {bk});")
+                out.append(f"    {aj} += {lit(w)}v{i} * {ak}; {bj} += {lit(w)}(t{i} * {ak} + v{i} * {bk});")
+        for c in comps:
+            a_, b_ = aref(c)
+            out.append(f"    adj[{slot_of[(g, c)] * 32}] = {a_}; adt[{slot_of[(g, c)] * 32}] = {b_};")
+        out.append("  }")
+        out.append("};")
+    out.append("__device__ __forceinline__ void dual_part(int part, const float* m, const float* mt, float* adj, float* adt, "
+               "const float* xi, double ek, bool act, bool lane0, double* dxt) {")
+    out.append("  switch (part) {")
+    for g in range(parts):
+        out.append(f"    case {g}: DPart<{g}>::run(m, mt, adj, adt, xi, ek, act, lane0, dxt); return;")
+    out.append("  }")
+    out.append("}")
+    return out
+
+
 def emit_level(L, outdir):
     prog = build_program(L)
     fwd_rows, fwd_layers = encode_layout(forward_layout(prog))
@@ -898,6 +981,7 @@ def emit_level(L, outdir):
         for s, (_, comps) in enumerate(sl):
             assert comps == list(range(min(comps), min(comps) + len(comps)))
     nparts, nslots, has_parts = 1, 0, False
+    ndparts, ndslots = 1, 0
     if L <= UNROLLED_MAX_LEVEL and prog.ops:
         has_parts = True
         nparts = CONTRACT_PARTS.get(L, 1)
@@ -905,6 +989,10 @@ def emit_level(L, outdir):
         slot_begin = [int(x) for x in part_lines[2].split("{")[1].rstrip("};").split(",")]
         nslots = int(part_lines[1].split("NSLOT = ")[1].rstrip(";"))
         lines += part_lines
+        ndparts = DUAL_PARTS.get(L, nparts)
+        dual_lines = emit_dual_parts(prog, ndparts)
+        ndslots = int(dual_lines[0].split("NDSLOT = ")[1].rstrip(";"))
+        lines += dual_lines
     else:
         lines.append("#define MTPGEN_HAS_PARTS 0")
     lines += emit_slice_functions(prog, s32, "f", slot_begin if has_parts else None)
@@ -913,6 +1001,7 @@ def emit_level(L, outdir):
     lines.append("  static constexpr int L_ = L, C_ = C, V_ = V, M_ = M, NMU_ = NMU, NUMAX_ = NUMAX, NS32_ = NS32, NS64_ = NS64;")
     lines.append(f"  static constexpr int NPART_ = {nparts}, NSLOT_ = {max(nslots, 1)};")
     lines.append(f"  static constexpr bool HAS_PARTS_ = {'true' if has_parts else 'false'};")
+    lines.append(f"  static constexpr int NDPART_ = {ndparts}, NDSLOT_ = {max(ndslots, 1)};")
     lines.append("  template <int S> using F32 = SliceF<S>;")
     lines.append("  template <int S> using F64 = SliceD<S>;")
     lines.append("};")

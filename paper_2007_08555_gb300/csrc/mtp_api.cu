@@ -52,6 +52,7 @@ struct mtp_model {
     mtp::NbrState nb;
     DevBuf mom, adjm, gx;  // gx: pair gradients as 4-vectors
     DevBuf aslots, epart;  // float contraction: per-part dV/dM slots and site-energy shares
+    DevBuf g_dslots, g_dxt;  // loss gradient: tangent-contraction slots, per-tile dL/dxi shares
     // staging for MTP_HOST_MEMORY calls
     DevBuf s_off, s_pos, s_types, s_cells, s_energy, s_forces, s_virial, s_site, s_brows, s_batoms;
     int cap = 128;
@@ -367,6 +368,8 @@ void mtp_destroy(mtp_model* M) {
     M->nb.atom_wp.release();
     M->nb.keys_am.release();
     M->aslots.release();
+    M->g_dslots.release();
+    M->g_dxt.release();
     M->epart.release();
     if (M->h_flags) cudaFreeHost(M->h_flags);
     if (M->g_exec) cudaGraphExecDestroy(M->g_exec);
@@ -524,6 +527,10 @@ mtp_status run_param_grad(mtp_model* M, int K, int n, const int* off, const int*
         M->g_momt.reserve(((N + 31) / 32) * M->C * 32 * sizeof(T)) ||
         M->g_adjmt.reserve(((N + 31) / 32) * M->C * 32 * sizeof(T)))
         return MTP_ENOMEM;
+    const bool dual_parts = sizeof(T) == 4 && M->ops->contract_parts > 0;  // float tangent contraction in parts
+    if (dual_parts && (M->g_dslots.reserve(2 * ((N + 31) / 32) * M->ops->dual_slots * 32 * sizeof(T) + 16) ||
+                       M->g_dxt.reserve(((N + 31) / 32) * M->m * sizeof(double) + 16)))
+        return MTP_ENOMEM;
     mtp::EvalCtx<T> a;
     mtp_status s = run_eval<T>(M, K, n, off, types, M->g_energy.as<double>(), M->g_forces.as<double>(),
                                M->g_virial.as<double>(), nullptr, nullptr, nullptr, st, &a);
@@ -535,6 +542,8 @@ mtp_status run_param_grad(mtp_model* M, int K, int n, const int* off, const int*
     a.gew = M->g_ew.as<double>();
     a.momt = M->g_momt.as<T>();
     a.adjmt = M->g_adjmt.as<T>();
+    a.dslots = dual_parts ? M->g_dslots.as<T>() : nullptr;
+    a.dxt = dual_parts ? M->g_dxt.as<double>() : nullptr;
     a.dxi = out + 1;
     a.dc = out + 1 + M->m;
     mtp::LossArgs L;

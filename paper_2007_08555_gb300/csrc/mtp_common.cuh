@@ -75,6 +75,8 @@ struct EvalCtx {
     T* momt;              // tangent of the moments along u (tile layout)
     T* adjmt;             // tangent of dV/dM (tile layout)
     double* dxi;          // [M] accumulated dL/dxi
+    T* dslots;            // [2][ceil(n/32)][NDSLOT][32] dV/dM and its tangent, per tangent-contraction part
+    double* dxt;          // [ceil(n/32)][M] per-tile shares of dL/dxi from the tangent contraction
     double* dc;           // [S][S][NMU][NQ] accumulated dL/dc
 };
 

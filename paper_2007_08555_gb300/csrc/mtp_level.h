@@ -21,6 +21,7 @@ struct LevelOps {
     int program_ops;
     int flop_pair_moments, flop_pair_adjoint, flop_atom_program;
     int contract_parts, contract_slots;  // float contraction parts and their dV/dM slots per atom
+    int dual_parts, dual_slots;          // the same for the tangent contraction of the loss gradient
     // launchers (stream-ordered, no synchronisation); return the number of kernels launched
     // gather_after (or NULL): an event the force gather waits for (the reverse-pair slots)
     int (*eval_f32)(const EvalCtx<float>&, cudaStream_t, int n_sm, cudaEvent_t* marks, cudaEvent_t gather_after);

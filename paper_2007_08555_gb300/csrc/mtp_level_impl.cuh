@@ -503,23 +503,6 @@ __global__ void __launch_bounds__(128) k_contract_parts(const EvalCtx<float> a) 
     }
 }
 
-// dV/dM_c = sum of its slots in slot order (the loss gradient needs dV/dM itself; the evaluation
-// reads the slots directly)
-__global__ void __launch_bounds__(128) k_adjm_from_slots(const EvalCtx<float> a) {
-    constexpr int C = G::C_;
-    const int lane = threadIdx.x & 31;
-    const int n_tiles = (a.n_atoms + 31) >> 5;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    // one warp per (tile, component): 32 atoms, coalesced
-    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_tiles * C; w += warps) {
-        const int tile = w / C, c = w - tile * C;
-        const float* sl = a.aslots + (size_t)tile * G::NSLOT_ * 32 + lane;
-        const int s0 = ::MTP_GEN_NS::slot_begin[c], s1 = ::MTP_GEN_NS::slot_begin[c + 1];
-        float acc = 0.f;
-        for (int s = s0; s < s1; ++s) acc += sl[s * 32];
-        a.adjm[((size_t)tile * C + c) * 32 + lane] = acc;
-    }
-}
 #endif
 
 // b rows as sums of the per-atom rows of each configuration (one block per configuration)
@@ -544,7 +527,7 @@ __device__ __forceinline__ void pairgrad_slice(const EvalCtx<T>& a, int i, int s
     T adjs[SL::SIZE];
 #if MTPGEN_HAS_PARTS
     if constexpr (sizeof(T) == 4) {
-        // dV/dM straight from the contraction parts' slots (fixed order, as k_adjm_from_slots)
+        // dV/dM straight from the contraction parts' slots, summed in slot order
         SL::template adj_from_slots<T>(a.aslots + (size_t)(i >> 5) * G::NSLOT_ * 32 + (i & 31), adjs);
     } else
 #endif
@@ -1062,6 +1045,67 @@ __device__ __forceinline__ void run_program_dual(const unsigned long long* __res
     }
 }
 
+#if MTPGEN_HAS_PARTS
+// Tangent contraction of the loss gradient (float), split into NDPART generated parts like the
+// forward contraction: warp w runs part w / n_tiles for the 32 atoms of tile w % n_tiles.  Each part
+// writes dV/dM and its tangent for its moments to dual slots and its basis functions' shares of
+// dL/dxi (summed over the tile's atoms) to dxt[tile].
+__global__ void __launch_bounds__(128) k_contract_tan_parts(const EvalCtx<float> a) {
+    const int lane = threadIdx.x & 31;
+    const int n_tiles = (a.n_atoms + 31) >> 5;
+    const int total = n_tiles * G::NDPART_;
+    const size_t half = (size_t)n_tiles * G::NDSLOT_ * 32;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += (gridDim.x * blockDim.x) >> 5) {
+        const int part = w / n_tiles, tile = w - part * n_tiles;
+        const int i = tile * 32 + lane;
+        const bool act = i < a.n_atoms;
+        const double ek = act ? a.gew[a.cfg_of[i]] : 0.0;
+        const size_t mo = (size_t)tile * G::C_ * 32 + lane;
+        const size_t so = (size_t)tile * G::NDSLOT_ * 32 + lane;
+        ::MTP_GEN_NS::dual_part(part, a.mom + mo, a.momt + mo, a.dslots + so, a.dslots + half + so, a.xi, ek, act,
+                                lane == 0, a.dxt + (size_t)tile * G::M_);
+    }
+}
+
+// dV/dM and its tangent = sums of their dual slots (slot order), one warp per (tile, component)
+__global__ void __launch_bounds__(128) k_dual_sum(const EvalCtx<float> a) {
+    constexpr int C = G::C_;
+    const int lane = threadIdx.x & 31;
+    const int n_tiles = (a.n_atoms + 31) >> 5;
+    const size_t half = (size_t)n_tiles * G::NDSLOT_ * 32;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_tiles * C; w += warps) {
+        const int tile = w / C, c = w - tile * C;
+        const float* sl = a.dslots + (size_t)tile * G::NDSLOT_ * 32 + lane;
+        const int s0 = ::MTP_GEN_NS::dslot_begin[c], s1 = ::MTP_GEN_NS::dslot_begin[c + 1];
+        float va = 0.f, vt = 0.f;
+        for (int s = s0; s < s1; ++s) {
+            va += sl[s * 32];
+            vt += sl[half + s * 32];
+        }
+        const size_t q = ((size_t)tile * C + c) * 32 + lane;
+        a.adjm[q] = va;
+        a.adjmt[q] = vt;
+    }
+}
+
+// dL/dxi += sum over tiles of dxt (one block per basis function, fixed reduction order)
+__global__ void __launch_bounds__(128) k_dx_sum(const EvalCtx<float> a) {
+    __shared__ double s[128];
+    const int alpha = blockIdx.x;
+    const int n_tiles = (a.n_atoms + 31) >> 5;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) acc += a.dxt[(size_t)t * G::M_ + alpha];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&a.dxi[alpha], s[0]);
+}
+#endif
+
 template <class T>
 __global__ void __launch_bounds__(128) k_contract_tan(const EvalCtx<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1227,15 +1271,6 @@ int launch_grad_pairs(EvalCtx<T>& a, cudaStream_t st, int n_sm) {
 template <class T>
 int grad_all(EvalCtx<T>& a, const LossArgs& L, cudaStream_t st, int n_sm) {
     int launches = 0;
-#if MTPGEN_HAS_PARTS
-    if constexpr (sizeof(T) == 4) {  // dV/dM itself, from the contraction parts' slots
-        const long work = (long)((a.n_atoms + 31) / 32) * G::C_ * 32;
-        int blocks = (int)((work + 127) / 128);
-        if (blocks > n_sm * 32) blocks = n_sm * 32;
-        if (blocks > 0) k_adjm_from_slots<<<blocks, 128, 0, st>>>(a);
-        ++launches;
-    }
-#endif
     T* D = const_cast<T*>(a.gD);
     T* eps = const_cast<T*>(a.geps);
     k_resid_atoms<T><<<min((a.n_atoms + 127) / 128 + 1, n_sm * 8), 128, 0, st>>>(a, L, D);
@@ -1248,6 +1283,19 @@ int grad_all(EvalCtx<T>& a, const LossArgs& L, cudaStream_t st, int n_sm) {
         case 2: launches += launch_grad_pairs<T, 2>(a, st, n_sm); break;
         default: launches += launch_grad_pairs<T, 1>(a, st, n_sm); break;
     }
+#if MTPGEN_HAS_PARTS
+    if constexpr (sizeof(T) == 4) {
+        const int n_tiles = (a.n_atoms + 31) / 32;
+        int blocks = (int)(((long)n_tiles * G::NDPART_ + 3) / 4);
+        if (blocks > n_sm * 16) blocks = n_sm * 16;
+        k_contract_tan_parts<<<blocks, 128, 0, st>>>(a);
+        int sblocks = (int)(((long)n_tiles * G::C_ + 3) / 4);
+        if (sblocks > n_sm * 32) sblocks = n_sm * 32;
+        k_dual_sum<<<sblocks, 128, 0, st>>>(a);
+        k_dx_sum<<<G::M_, 128, 0, st>>>(a);
+        launches += 3;
+    } else
+#endif
     {
         const int threads = 128, wpb = 4;
         const size_t smem = sizeof(T) * (size_t)G::V_ * (1 + 4 * wpb) + sizeof(float) * (a.n_weights + 4) + 64;
@@ -1288,7 +1336,7 @@ const LevelOps* MTP_LEVEL_FN() {
         g::fwd_ops, g::fwd_layer_rows, g::FWD_ROWS, g::FWD_LAYERS,
         g::adj_ops, g::adj_layer_rows, g::ADJ_ROWS, g::ADJ_LAYERS, g::weights, g::NWEIGHTS,
         g::PROGRAM_OPS, g::FLOP_PAIR_MOMENTS, g::FLOP_PAIR_ADJOINT, g::FLOP_ATOM_PROGRAM,
-        g::Traits::NPART_, g::Traits::NSLOT_,
+        g::Traits::NPART_, g::Traits::NSLOT_, g::Traits::NDPART_, g::Traits::NDSLOT_,
         &MTP_GEN_NS::eval_f32, &MTP_GEN_NS::eval_f64, &MTP_GEN_NS::grad_f32, &MTP_GEN_NS::grad_f64};
     return &ops;
 }
