@@ -1170,9 +1170,10 @@ __device__ __forceinline__ void pdot_all(const T* adjp, const T* adjtp, T x, T y
     }
 }
 
-// dL/dc: thread group per atom, one pass per neighbour species (register accumulators), then
-// shared-memory and global double atomics
-template <class T, int TPA>
+// dL/dc: thread group per atom, one pass per neighbour species (register accumulators, when the
+// radial basis size NQC is a compile-time constant; 0 = any size), then shared-memory and global
+// double atomics
+template <class T, int TPA, int NQC>
 __global__ void __launch_bounds__(128) k_dc(const EvalCtx<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NMU = G::NMU_;
@@ -1181,7 +1182,8 @@ __global__ void __launch_bounds__(128) k_dc(const EvalCtx<T> a) {
     for (int k = threadIdx.x; k < nc; k += blockDim.x) dcs[k] = 0.0;
     __syncthreads();
     const size_t n = (size_t)a.n_atoms;
-    const int NQ = a.NQ;
+    const int NQ = NQC ? NQC : a.NQ;
+    constexpr int NQM = NQC ? NQC : kMaxRadial;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_atoms * TPA; g += gridDim.x * blockDim.x) {
         const int i = g / TPA, sub = g % TPA;
         const int zi = clamp_species(a.types[i], a.S);
@@ -1193,11 +1195,11 @@ __global__ void __launch_bounds__(128) k_dc(const EvalCtx<T> a) {
         for (int q = 0; q < 9; ++q) E[q] = a.geps[9 * (size_t)k + q];
         const size_t tb = (size_t)(i >> 5) * G::C_ * 32 + (i & 31);
         for (int zp = 0; zp < a.S; ++zp) {
-            T acc[NMU][kMaxRadial];
+            T acc[NMU][NQM];
 #pragma unroll
             for (int mu = 0; mu < NMU; ++mu)
 #pragma unroll
-                for (int b = 0; b < kMaxRadial; ++b) acc[mu][b] = T(0);
+                for (int b = 0; b < NQM; ++b) acc[mu][b] = T(0);
             bool any = false;
             for (int p = sub; p < cnt; p += TPA) {
                 const size_t idx = (size_t)p * n + i;
@@ -1219,8 +1221,8 @@ __global__ void __launch_bounds__(128) k_dc(const EvalCtx<T> a) {
                 const T uu = r < a.rcut ? a.rcut - r : T(0);  // Q_b = 0 beyond the cutoff (Eq. 4)
                 T t0 = T(1), t1 = xx, d0 = T(0), d1 = T(1);
 #pragma unroll
-                for (int b = 0; b < kMaxRadial; ++b) {
-                    if (b >= NQ) break;
+                for (int b = 0; b < NQM; ++b) {
+                    if (!NQC && b >= NQ) break;
                     T tb_, db_;
                     if (b == 0) {
                         tb_ = t0;
@@ -1247,7 +1249,9 @@ __global__ void __launch_bounds__(128) k_dc(const EvalCtx<T> a) {
                 double* dst = dcs + (size_t)((zi * a.S + zp) * NMU) * NQ;
 #pragma unroll
                 for (int mu = 0; mu < NMU; ++mu)
-                    for (int b = 0; b < NQ; ++b) atomicAdd(&dst[mu * NQ + b], (double)acc[mu][b]);
+#pragma unroll
+                    for (int b = 0; b < NQM; ++b)
+                        if (NQC || b < NQ) atomicAdd(&dst[mu * NQ + b], (double)acc[mu][b]);
             }
         }
     }
@@ -1317,7 +1321,10 @@ int grad_all(EvalCtx<T>& a, const LossArgs& L, cudaStream_t st, int n_sm) {
         const size_t smem = sizeof(double) * (size_t)a.S * a.S * G::NMU_ * a.NQ;
         int blocks = (a.n_atoms + threads - 1) / threads;
         if (blocks > n_sm * 8) blocks = n_sm * 8;
-        k_dc<T, 1><<<blocks, threads, smem, st>>>(a);
+        if (a.NQ == 8)
+            k_dc<T, 1, 8><<<blocks, threads, smem, st>>>(a);
+        else
+            k_dc<T, 1, 0><<<blocks, threads, smem, st>>>(a);
         ++launches;
     }
     return launches;
