@@ -587,14 +587,16 @@ __global__ void __launch_bounds__(128) k_pairgrad(const EvalCtx<T> a) {
 // ----------------------------------------------------------------------------------------------
 // k_gather: forces and virial
 // ----------------------------------------------------------------------------------------------
-// running per-configuration sums of the gather: virial (9) and energy
+// running per-configuration sums of the gather: the virial in the working precision T (its
+// per-pair terms are T already), the energy in double (so that E equals the double sum of the site
+// energies, Eq. 2, to double rounding); both reach the double outputs by atomics
 template <class T>
-__device__ __forceinline__ void flush_run(const EvalCtx<T>& a, int cfg, const double* run, bool want_e) {
+__device__ __forceinline__ void flush_run(const EvalCtx<T>& a, int cfg, const T* run, double erun, bool want_e) {
     if (a.virial) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) atomicAdd(&a.virial[(size_t)cfg * 9 + k], run[k]);
+        for (int k = 0; k < 9; ++k) atomicAdd(&a.virial[(size_t)cfg * 9 + k], (double)run[k]);
     }
-    if (want_e) atomicAdd(&a.energy[cfg], run[9]);
+    if (want_e) atomicAdd(&a.energy[cfg], erun);
 }
 
 template <class T>
@@ -613,14 +615,17 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
     constexpr bool kE = false;
 #endif
     const bool want_e = kE && a.energy != nullptr;
-    __shared__ int s_cfg[128];
-    __shared__ double s_w[10][128];
+    constexpr int kWarps = 4;  // blockDim.x == 128
+    __shared__ int s_cfg[kWarps];
+    __shared__ T s_w[kWarps][9];
+    __shared__ double s_e[kWarps];
     const size_t n = (size_t)a.n_atoms;
     const int stride = gridDim.x * blockDim.x;
     const int n_groups = ((a.n_atoms + 31) / 32) * 32;  // whole warps stay converged for the shuffles
-    double Wrun[10];  // virial, then energy
+    T Wrun[9];
+    double Erun = 0.0;
 #pragma unroll
-    for (int k = 0; k < 10; ++k) Wrun[k] = 0.0;
+    for (int k = 0; k < 9; ++k) Wrun[k] = T(0);
     int wcfg = -1;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups * TPA; g += stride) {
         const int i = g / TPA, sub = g % TPA;
@@ -712,51 +717,78 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
             a.forces[3 * (size_t)i + 1] = (double)F[1];
             a.forces[3 * (size_t)i + 2] = (double)F[2];
         }
-        double e_i = 0.0;
+        float e_i = 0.f;
         if constexpr (kE) {
             if (active && sub == 0) {
                 float e = 0.f;
 #pragma unroll
                 for (int p = 0; p < G::NPART_; ++p) e += a.epart[(size_t)p * n + i];
                 if (a.site) a.site[i] = (double)e;
-                e_i = (double)e;
+                e_i = e;
             }
         }
         if (active && (a.virial || want_e)) {
             if (cfg != wcfg) {
-                if (wcfg >= 0) flush_run(a, wcfg, Wrun, want_e);
+                if (wcfg >= 0) flush_run(a, wcfg, Wrun, Erun, want_e);
 #pragma unroll
-                for (int k = 0; k < 10; ++k) Wrun[k] = 0.0;
+                for (int k = 0; k < 9; ++k) Wrun[k] = T(0);
+                Erun = 0.0;
                 wcfg = cfg;
             }
 #pragma unroll
-            for (int k = 0; k < 9; ++k) Wrun[k] += (double)W[k];
-            Wrun[9] += e_i;
+            for (int k = 0; k < 9; ++k) Wrun[k] += W[k];
+            if (want_e) Erun += (double)e_i;
         }
     }
     if (!a.virial && !want_e) return;
-    // block-level combine of the running sums: a tree reduction when the whole block ends in one
-    // configuration (large cells), otherwise one atomic per thread and component
-    s_cfg[threadIdx.x] = wcfg;
-    __syncthreads();
-    const int c0 = s_cfg[0];
-    const bool uniform = __syncthreads_and(wcfg == c0 || wcfg < 0) && c0 >= 0;
-    if (!uniform) {
-        if (wcfg >= 0) flush_run(a, wcfg, Wrun, want_e);
-        return;
-    }
+    // combine the running sums: a warp whose lanes all end in one configuration (lanes without atoms
+    // hold zeros) sums them with shuffles, any other warp flushes lane by lane; then one thread per
+    // component adds the warp sums, one double atomic per run of warps of equal configuration
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cmax = __reduce_max_sync(0xffffffffu, wcfg);
+    const bool wuni = __all_sync(0xffffffffu, wcfg == cmax || wcfg < 0);
+    if (wuni) {
+        if (a.virial) {
 #pragma unroll
-    for (int k = 0; k < 10; ++k) s_w[k][threadIdx.x] = Wrun[k];
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
+            for (int k = 0; k < 9; ++k) {
 #pragma unroll
-            for (int k = 0; k < 10; ++k) s_w[k][threadIdx.x] += s_w[k][threadIdx.x + h];
+                for (int o = 16; o > 0; o >>= 1) Wrun[k] += __shfl_xor_sync(0xffffffffu, Wrun[k], o);
+            }
         }
-        __syncthreads();
+        if (want_e) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) Erun += __shfl_xor_sync(0xffffffffu, Erun, o);
+        }
+        if (lane < 9) {
+            T v = Wrun[0];
+#pragma unroll
+            for (int k = 1; k < 9; ++k) v = lane == k ? Wrun[k] : v;
+            s_w[warp][lane] = v;
+        }
+        if (lane == 9) s_e[warp] = Erun;
+    } else if (wcfg >= 0) {
+        flush_run(a, wcfg, Wrun, Erun, want_e);
     }
-    if (threadIdx.x < 9 && a.virial) atomicAdd(&a.virial[(size_t)c0 * 9 + threadIdx.x], s_w[threadIdx.x][0]);
-    if (threadIdx.x == 9 && want_e) atomicAdd(&a.energy[c0], s_w[9][0]);
+    if (lane == 0) s_cfg[warp] = wuni ? cmax : -1;  // -1: nothing left to add
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        const int k = threadIdx.x;
+        const bool use = k < 9 ? a.virial != nullptr : want_e;
+        double acc = 0.0;
+        int cur = -1;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const int c = s_cfg[w];
+            if (c < 0) continue;
+            if (c != cur) {
+                if (cur >= 0 && use) atomicAdd(k < 9 ? &a.virial[(size_t)cur * 9 + k] : &a.energy[cur], acc);
+                acc = 0.0;
+                cur = c;
+            }
+            acc += k < 9 ? (double)s_w[w][k] : s_e[w];
+        }
+        if (cur >= 0 && use) atomicAdd(k < 9 ? &a.virial[(size_t)cur * 9 + k] : &a.energy[cur], acc);
+    }
 }
 
 // ----------------------------------------------------------------------------------------------
