@@ -113,8 +113,8 @@ mtp_status mtp_set_params(mtp_model* model, const double* xi, const double* c);
  * rebuild before any atom has moved by skin / 2. */
 mtp_status mtp_set_skin(mtp_model* model, double skin);
 
-/* Threads per atom in the pair kernels: `moments` for the moment accumulation (Eq. 5) and the pair
- * gradients, `pairs` for the force gather and the loss-gradient kernels; each 1, 2, 4 or 8, or 0
+/* Threads per atom in the pair kernels: `moments` for the moment accumulation (Eq. 5), `pairs` for
+ * the pair gradients, the force gather and the loss-gradient kernels; each 1, 2, 4 or 8, or 0
  * (default) to choose per call from the atom count.  A tuning knob without a counterpart in the paper: results agree to
  * rounding whatever the choice (summation order changes).  Other values are MTP_EINVAL. */
 mtp_status mtp_set_threads_per_atom(mtp_model* model, int moments, int pairs);

@@ -602,6 +602,15 @@ def emit_slice_functions(prog: Program, slc, tag, slot_begin=None):
                 terms = [f"sl[{s * 32}]" for s in range(slot_begin[ci], slot_begin[ci + 1])] or ["T(0)"]
                 out.append(f"    adj[{t}] = " + " + ".join(terms) + ";")
             out.append("  }")
+            # the same sums written to shared memory in groups of four components (one 16-byte
+            # vector per group and atom, groups NS vectors apart), component t by the lane with
+            # t % TPA == sub of the atom's TPA lanes
+            out.append("  template <class T, int TPA, int NS> static __device__ __forceinline__ void adj_to_shared("
+                       "const T* __restrict__ sl, T* __restrict__ dst, const int sub) {")
+            for t, ci in enumerate(comps):
+                terms = [f"sl[{s * 32}]" for s in range(slot_begin[ci], slot_begin[ci + 1])] or ["T(0)"]
+                out.append(f"    if ({t} % TPA == sub) dst[{(t // 4) * 4} * NS + {t % 4}] = " + " + ".join(terms) + ";")
+            out.append("  }")
         need = _closure(monos)
         out.append("  template <class T> static __device__ __forceinline__ void mom(const T x, const T y, const T z, "
                    "const T* __restrict__ f, T* __restrict__ acc) {")
@@ -611,6 +620,8 @@ def emit_slice_functions(prog: Program, slc, tag, slot_begin=None):
             mv = "T(1)" if m == (0, 0, 0) else _mono_name(m)
             out.append(f"    acc[{t}] += f[{mu}] * {mv};")
         out.append("  }")
+        # adjoint of one pair: P_mu = sum_m adj[mu,m] m gives the radial part s = sum_mu df_mu P_mu;
+        # alpha_m = sum_mu adj[mu,m] f_mu times the gradient of each monomial gives the rest
         grads = set()
         for m in monos:
             for k in range(3):
@@ -619,21 +630,29 @@ def emit_slice_functions(prog: Program, slc, tag, slot_begin=None):
                     mm[k] -= 1
                     grads.add(tuple(mm))
         need = _closure(set(monos) | grads)
-        out.append("  template <class T> static __device__ __forceinline__ void grad(const T x, const T y, const T z, "
-                   "const T* __restrict__ f, const T* __restrict__ df, const T* __restrict__ adj, "
+        out.append("  template <class T, class A> static __device__ __forceinline__ void grad(const T x, const T y, "
+                   "const T z, const T* __restrict__ f, const T* __restrict__ df, const A adj, "
                    "T& s, T& gx, T& gy, T& gz) {")
         out += ["    " + l for l in _mono_code(need, "T")]
         by_m = defaultdict(list)
         for t, ci in enumerate(comps):
             mu, m = prog.comp_list[ci]
             by_m[m].append((t, mu))
+        mus = sorted({mu for ts in by_m.values() for _, mu in ts})
+        p_terms = defaultdict(list)
         for m in monos:
+            nm = None if m == (0, 0, 0) else _mono_name(m)
+            for t, mu in by_m[m]:
+                p_terms[mu].append(f"adj[{t}]" if nm is None else f"adj[{t}] * {nm}")
+        for mu in mus:
+            out.append(f"    const T P{mu} = " + " + ".join(p_terms[mu]) + ";")
+        out.append("    s += " + " + ".join(f"df[{mu}] * P{mu}" for mu in mus) + ";")
+        for m in monos:
+            if m == (0, 0, 0):
+                continue
             terms = by_m[m]
             al = " + ".join(f"adj[{t}] * f[{mu}]" for t, mu in terms)
-            be = " + ".join(f"adj[{t}] * df[{mu}]" for t, mu in terms)
-            nm = "T(1)" if m == (0, 0, 0) else _mono_name(m)
-            out.append(f"    {{ const T al = {al}; const T be = {be};")
-            out.append(f"      s += be * {nm};")
+            out.append(f"    {{ const T al = {al};")
             for k, gv in enumerate(("gx", "gy", "gz")):
                 if m[k] > 0:
                     mm = list(m)
@@ -708,10 +727,10 @@ def flop_counts(prog: Program):
         "components": C,
         "monomials": n_mono,
         "program_ops": n_ops,
-        # per pair: moments 2C + monomials; adjoint: 4C (alpha, beta) + 2 per monomial (s) +
-        # 2 per nonzero gradient term + monomials; plus the geometry/radial terms added by the caller
+        # per pair: moments 2C + monomials; adjoint: 4C (P, alpha) + 2 N_mu (s) + 2 per nonzero
+        # gradient term + monomials; plus the geometry/radial terms added by the caller
         "pair_moments": 2 * C + n_mono,
-        "pair_adjoint": 4 * C + 2 * n_mono + 2 * sum(sum(1 for k in range(3) if m[k] > 0) for m in monos)
+        "pair_adjoint": 4 * C + 2 * prog.n_mu + 2 * sum(sum(1 for k in range(3) if m[k] > 0) for m in monos)
         + 2 * n_mono,
         # per atom: forward 2 flops per op, adjoint 4 flops per op (two contributions of 2 flops)
         "atom_program": 2 * n_ops + 4 * n_ops,
@@ -942,7 +961,7 @@ def emit_level(L, outdir):
              "#pragma once", "#include \"mtp_gen_common.h\"", f"namespace mtpgen_{tag} {{"]
     lines.append(f"constexpr int L = {L}, C = {C}, V = {V}, M = {prog.basis.m}, NMU = {prog.n_mu}, "
                  f"NUMAX = {prog.numax};")
-    lines.append(f"constexpr int NS32 = {len(s32)}, NS64 = {len(s64)};")
+    lines.append(f"constexpr int NS32 = {len(s32)}, NS64 = {len(s64)}, MAXS32 = {max(len(c) for _, c in s32)};")
     lines.append(f"constexpr int FWD_ROWS = {len(fwd_rows)}, ADJ_ROWS = {len(adj_rows)};")
     lines.append(f"constexpr int FWD_LAYERS = {len(fwd_layers)}, ADJ_LAYERS = {len(adj_layers)};")
     lines.append(f"constexpr int PROGRAM_OPS = {len(prog.ops)};")
@@ -998,7 +1017,8 @@ def emit_level(L, outdir):
     lines += emit_slice_functions(prog, s32, "f", slot_begin if has_parts else None)
     lines += emit_slice_functions(prog, s64, "d")
     lines.append("struct Traits {")
-    lines.append("  static constexpr int L_ = L, C_ = C, V_ = V, M_ = M, NMU_ = NMU, NUMAX_ = NUMAX, NS32_ = NS32, NS64_ = NS64;")
+    lines.append("  static constexpr int L_ = L, C_ = C, V_ = V, M_ = M, NMU_ = NMU, NUMAX_ = NUMAX, NS32_ = NS32, NS64_ = NS64, "
+                 "MAXS32_ = MAXS32;")
     lines.append(f"  static constexpr int NPART_ = {nparts}, NSLOT_ = {max(nslots, 1)};")
     lines.append(f"  static constexpr bool HAS_PARTS_ = {'true' if has_parts else 'false'};")
     lines.append(f"  static constexpr int NDPART_ = {ndparts}, NDSLOT_ = {max(ndslots, 1)};")

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <utility>
 
 namespace mtp {
 
@@ -54,8 +55,8 @@ struct EvalCtx {
     int adj_layers;
     const float* weights;               // [n_weights] op weights
     int n_weights;
-    int tpa;              // threads per atom in the gather and loss-gradient kernels (1, 2, 4 or 8)
-    int tpa_m;            // threads per atom in the moments and pair-gradient kernels
+    int tpa;              // threads per atom in the pair-gradient, gather and loss-gradient kernels (1, 2, 4 or 8)
+    int tpa_m;            // threads per atom in the moments kernel
     T* mom;               // [ceil(n/32)][C][32] moment components (tile layout)
     T* adjm;              // [ceil(n/32)][C][32] dV/dM
     T* aslots;            // [ceil(n/32)][NSLOT][32] dV/dM shares of the contraction parts (float path)
@@ -115,6 +116,35 @@ inline void record_mark(cudaEvent_t e, cudaStream_t st) {
         cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
     else
         cudaEventRecord(e, st);
+}
+
+// Programmatic dependent launch (sm_90 and later).  A kernel started by launch_pdl may begin while
+// the previous kernel of its stream is still running; before its first global-memory access it
+// calls pdl_wait, which returns once that kernel has completed and its writes are visible (a no-op
+// for a kernel launched the ordinary way).  pdl_trigger lets the next kernel of the stream start
+// launching; it changes no ordering of memory accesses.  Kernels of the evaluation chain call both
+// at entry, so only the launch latency of the next kernel overlaps the current one.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_trigger();
+}
+
+template <class... P, class... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), int grid, int block, size_t smem, cudaStream_t st,
+                              A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

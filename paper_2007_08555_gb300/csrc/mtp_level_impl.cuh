@@ -230,7 +230,7 @@ __device__ __forceinline__ void load_c(const EvalCtx<T>& a, T* cs) {
 
 // bytes of the shared coefficient table
 template <class T>
-size_t coef_bytes(const EvalCtx<T>& a) {
+__host__ __device__ inline size_t coef_bytes(const EvalCtx<T>& a) {
     return sizeof(T) * (size_t)a.S * a.S * a.NQ * CoefPad<T>::value;
 }
 
@@ -297,6 +297,7 @@ __device__ __forceinline__ void moments_all(const EvalCtx<T>& a, int i, int sub,
 
 template <class T, int TPA>
 __global__ void __launch_bounds__(128) k_moments(const EvalCtx<T> a) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* cs = reinterpret_cast<T*>(smem_raw);
     load_c(a, cs);
@@ -374,6 +375,7 @@ __device__ __forceinline__ void flush_sum(double* dst, int cfg, double v) {
 // warp per group of A consecutive atoms (contiguous chunks per warp)
 template <class T, int A>
 __global__ void __launch_bounds__(256) k_contract(const EvalCtx<T> a) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int V = G::V_, C = G::C_, M = G::M_;
     constexpr int MB = (M + 31) / 32;  // basis values per lane
@@ -487,6 +489,7 @@ __global__ void __launch_bounds__(256) k_contract(const EvalCtx<T> a) {
 // dV/dM of its moments to slots; the pair-gradient kernel adds the slots of each component and the
 // gather the energy shares, in a fixed order.
 __global__ void __launch_bounds__(128) k_contract_parts(const EvalCtx<float> a) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int n_tiles = (a.n_atoms + 31) >> 5;
     const int total = n_tiles * G::NPART_;
@@ -508,6 +511,7 @@ __global__ void __launch_bounds__(128) k_contract_parts(const EvalCtx<float> a) 
 // b rows as sums of the per-atom rows of each configuration (one block per configuration)
 template <class T>
 __global__ void k_brows(const EvalCtx<T> a, const int* cfg_off) {
+    pdl_enter();
     constexpr int M = G::M_;
     const int k = blockIdx.x;
     const int i0 = cfg_off[k], i1 = cfg_off[k + 1];
@@ -521,25 +525,43 @@ __global__ void k_brows(const EvalCtx<T> a, const int* cfg_off) {
 // ----------------------------------------------------------------------------------------------
 // k_pairgrad: g_ij = dV_i/dr_ij
 // ----------------------------------------------------------------------------------------------
-template <class T, int S, int TPA>
-__device__ __forceinline__ void pairgrad_slice(const EvalCtx<T>& a, int i, int sub, int zi, int cnt, const T* cs) {
-    using SL = typename SliceSel<T, S>::type;
-    T adjs[SL::SIZE];
-#if MTPGEN_HAS_PARTS
-    if constexpr (sizeof(T) == 4) {
-        // dV/dM straight from the contraction parts' slots, summed in slot order
-        SL::template adj_from_slots<T>(a.aslots + (size_t)(i >> 5) * G::NSLOT_ * 32 + (i & 31), adjs);
-    } else
-#endif
-    {
-        const T* src = a.adjm + (size_t)(i >> 5) * G::C_ * 32 + (i & 31);
-#pragma unroll
-        for (int t = 0; t < SL::SIZE; ++t) adjs[t] = src[(size_t)(SL::BEGIN + t) * 32];
+// dV/dM of one atom held in shared memory: components 4k .. 4k+3 in the vector q[k * NS] (NS atoms
+// per block); repeated reads of one vector are merged by the compiler (no stores in between)
+template <class T, int NS>
+struct SharedAdj {
+    const Vec4<T>* q;
+    __device__ __forceinline__ T operator[](int t) const {
+        const Vec4<T> v = q[(t >> 2) * NS];
+        const int c = t & 3;
+        return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
     }
+};
+
+// the float path keeps dV/dM in shared memory, shared by the TPA lanes of an atom, which leaves
+// the registers to the per-pair arithmetic (more resident warps); the double path keeps them in
+// registers
+template <class T>
+struct PairgradShared {
+#if MTPGEN_HAS_PARTS
+    static constexpr bool value = sizeof(T) == 4;
+#else
+    static constexpr bool value = false;
+#endif
+};
+
+template <class T, int TPA>
+constexpr size_t pairgrad_adj_bytes() {
+    return PairgradShared<T>::value ? sizeof(T) * (size_t)((G::MAXS32_ + 3) / 4 * 4) * (128 / TPA) : 0;
+}
+
+template <class T, int S, int TPA, class A>
+__device__ __forceinline__ void pairgrad_pairs(const EvalCtx<T>& a, int i, int sub, int zi, int cnt, const T* cs,
+                                               const A adj) {
     const size_t n = (size_t)a.n_atoms;
     const int csz = CoefPad<T>::value * a.NQ;
     // the next pair's loads are issued before this pair's arithmetic (their latency overlaps it)
-    PairIn<T> nx = load_pair(a, sub < cnt ? (size_t)sub * n + i : (size_t)i);
+    PairIn<T> nx{};
+    if (sub < cnt) nx = load_pair(a, (size_t)sub * n + i);
     for (int p = sub; p < cnt; p += TPA) {
         const size_t idx = (size_t)p * n + i;
         const PairIn<T> cur = nx;
@@ -549,7 +571,7 @@ __device__ __forceinline__ void pairgrad_slice(const EvalCtx<T>& a, int i, int s
         T f[G::NMU_], df[G::NMU_];
         radial<T, true>(r, cs + (zi * a.S + cur.zj) * csz, a.NQ, a.rmin, a.rcut, a.inv_span, f, df);
         T s = T(0), gx = T(0), gy = T(0), gz = T(0);
-        SL::template grad<T>(x, y, z, f, df, adjs, s, gx, gy, gz);
+        SliceSel<T, S>::type::template grad<T>(x, y, z, f, df, adj, s, gx, gy, gz);
         const T sr = s / r;
         gx += sr * x;
         gy += sr * y;
@@ -563,24 +585,61 @@ __device__ __forceinline__ void pairgrad_slice(const EvalCtx<T>& a, int i, int s
     }
 }
 
+template <class T, int S, int TPA>
+__device__ __forceinline__ void pairgrad_slice(const EvalCtx<T>& a, int i, int sub, bool active, int zi, int cnt,
+                                               const T* cs, T* sadj) {
+    using SL = typename SliceSel<T, S>::type;
+#if MTPGEN_HAS_PARTS
+    if constexpr (PairgradShared<T>::value) {
+        // dV/dM straight from the contraction parts' slots, summed in slot order, written once per
+        // atom (its lanes share the work) and read by all of them
+        constexpr int NSA = 128 / TPA;
+        T* mine = sadj + 4 * (threadIdx.x / TPA);
+        __syncwarp();  // the atom's lanes are done with the previous slice or atom
+        if (active) SL::template adj_to_shared<T, TPA, NSA>(a.aslots + (size_t)(i >> 5) * G::NSLOT_ * 32 + (i & 31),
+                                                            mine, sub);
+        __syncwarp();
+        pairgrad_pairs<T, S, TPA>(a, i, sub, zi, cnt, cs,
+                                  SharedAdj<T, NSA>{reinterpret_cast<const Vec4<T>*>(mine)});
+        return;
+    }
+#endif
+    // (an inactive lane's atom index stays within the last tile, which is allocated in full)
+    T adjs[SL::SIZE];
+    const T* src = a.adjm + (size_t)(i >> 5) * G::C_ * 32 + (i & 31);
+#pragma unroll
+    for (int t = 0; t < SL::SIZE; ++t) adjs[t] = src[(size_t)(SL::BEGIN + t) * 32];
+    pairgrad_pairs<T, S, TPA>(a, i, sub, zi, cnt, cs, adjs);
+}
+
 template <class T, int S, int NS, int TPA>
-__device__ __forceinline__ void pairgrad_all(const EvalCtx<T>& a, int i, int sub, int zi, int cnt, const T* cs) {
+__device__ __forceinline__ void pairgrad_all(const EvalCtx<T>& a, int i, int sub, bool active, int zi, int cnt,
+                                             const T* cs, T* sadj) {
     if constexpr (S < NS) {
-        pairgrad_slice<T, S, TPA>(a, i, sub, zi, cnt, cs);
-        pairgrad_all<T, S + 1, NS, TPA>(a, i, sub, zi, cnt, cs);
+        pairgrad_slice<T, S, TPA>(a, i, sub, active, zi, cnt, cs, sadj);
+        pairgrad_all<T, S + 1, NS, TPA>(a, i, sub, active, zi, cnt, cs, sadj);
     }
 }
 
 template <class T, int TPA>
 __global__ void __launch_bounds__(128) k_pairgrad(const EvalCtx<T> a) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* cs = reinterpret_cast<T*>(smem_raw);
+    T* sadj = reinterpret_cast<T*>(smem_raw + ((coef_bytes(a) + 15) & ~(size_t)15));
     load_c(a, cs);
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
-    for (int g = gtid; g < a.n_atoms * TPA; g += stride) {
+    const int n_groups = ((a.n_atoms + 31) / 32) * 32;  // whole warps stay converged for __syncwarp
+    for (int g = gtid; g < n_groups * TPA; g += stride) {
         const int i = g / TPA, sub = g % TPA;
-        pairgrad_all<T, 0, NumSlices<T>::value, TPA>(a, i, sub, clamp_species(a.types[i], a.S), a.count[i], cs);
+        const bool active = i < a.n_atoms;
+        int zi = 0, cnt = 0;
+        if (active) {
+            zi = clamp_species(a.types[i], a.S);
+            cnt = a.count[i];
+        }
+        pairgrad_all<T, 0, NumSlices<T>::value, TPA>(a, i, sub, active, zi, cnt, cs, sadj);
     }
 }
 
@@ -608,6 +667,7 @@ struct GatherIn {
 
 template <class T, int TPA>
 __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<T> a) {
+    pdl_enter();
     // float path with contraction parts: the site energies are the sums of the parts' shares
 #if MTPGEN_HAS_PARTS
     constexpr bool kE = sizeof(T) == 4;
@@ -803,16 +863,25 @@ int launch_pairs(const EvalCtx<T>& a, cudaStream_t st, int n_sm, bool moments) {
     const int max_blocks = n_sm * 16;
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
-    if (moments)
-        k_moments<T, TPA><<<blocks, threads, cbytes, st>>>(a);
-    else
-        k_pairgrad<T, TPA><<<blocks, threads, cbytes, st>>>(a);
+    if (moments) {
+        launch_pdl(k_moments<T, TPA>, blocks, threads, cbytes, st, a);
+    } else {
+        const size_t smem = ((cbytes + 15) & ~(size_t)15) + pairgrad_adj_bytes<T, TPA>();
+        static bool attr_set = false;
+        if (!attr_set && smem > 48 * 1024) {
+            cudaFuncSetAttribute(k_pairgrad<T, TPA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            attr_set = true;
+        }
+        launch_pdl(k_pairgrad<T, TPA>, blocks, threads, smem, st, a);
+    }
     return 1;
 }
 
 template <class T>
 int launch_pairs_tpa(const EvalCtx<T>& a, cudaStream_t st, int n_sm, bool moments) {
-    switch (a.tpa_m) {
+    // the moment accumulation holds its sums in registers and takes tpa_m lanes per atom; the pair
+    // gradients read dV/dM from shared memory and take the gather's tpa
+    switch (moments ? a.tpa_m : a.tpa) {
         case 8: return launch_pairs<T, 8>(a, st, n_sm, moments);
         case 4: return launch_pairs<T, 4>(a, st, n_sm, moments);
         case 2: return launch_pairs<T, 2>(a, st, n_sm, moments);
@@ -833,10 +902,10 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks,
         const long warps = (long)((a.n_atoms + 31) / 32) * G::NPART_;
         int blocks = (int)((warps + 3) / 4);
         if (blocks > n_sm * 16) blocks = n_sm * 16;
-        k_contract_parts<<<blocks, threads, 0, st>>>(a);
+        launch_pdl(k_contract_parts, blocks, threads, 0, st, a);
         ++launches;
         if (a.b_rows) {  // the caller provides per-atom rows whenever b rows are requested
-            k_brows<T><<<a.n_cfg, 128, 0, st>>>(a, a.cfg_off);
+            launch_pdl(k_brows<T>, a.n_cfg, 128, 0, st, a, a.cfg_off);
             ++launches;
         }
     } else
@@ -860,7 +929,7 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks,
         if (per_sm > 8) per_sm = 8;
         int blocks = (a.n_atoms + wpb * A - 1) / (wpb * A);
         if (blocks > n_sm * per_sm) blocks = n_sm * per_sm;
-        k_contract<T, A><<<blocks, threads, smem, st>>>(a);
+        launch_pdl(k_contract<T, A>, blocks, threads, smem, st, a);
         ++launches;
     }
     if (marks) record_mark(marks[kPhasePairgrad], st);
@@ -872,11 +941,18 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks,
         const long work = (long)(((a.n_atoms + 31) / 32) * 32) * a.tpa;
         int blocks = (int)((work + threads - 1) / threads);
         if (blocks > n_sm * 8) blocks = n_sm * 8;
+        // after a wait on another stream's event the launch is an ordinary one
+        auto go = [&](void (*k)(const EvalCtx<T>)) {
+            if (gather_after)
+                k<<<blocks, threads, 0, st>>>(a);
+            else
+                launch_pdl(k, blocks, threads, 0, st, a);
+        };
         switch (a.tpa) {
-            case 8: k_gather<T, 8><<<blocks, threads, 0, st>>>(a); break;
-            case 4: k_gather<T, 4><<<blocks, threads, 0, st>>>(a); break;
-            case 2: k_gather<T, 2><<<blocks, threads, 0, st>>>(a); break;
-            default: k_gather<T, 1><<<blocks, threads, 0, st>>>(a); break;
+            case 8: go(k_gather<T, 8>); break;
+            case 4: go(k_gather<T, 4>); break;
+            case 2: go(k_gather<T, 2>); break;
+            default: go(k_gather<T, 1>); break;
         }
         ++launches;
     }

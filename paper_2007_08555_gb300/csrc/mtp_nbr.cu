@@ -42,6 +42,7 @@ __device__ __forceinline__ int find_cfg(const int* cfg_off, int K, int i) {
 // Per-configuration geometry: inverse cell, perpendicular widths, bin counts and reach.
 __global__ void k_cells(int K, const double* cells, const int* cfg_off, double rsearch, CellDesc* d,
                         int* bin_total, int* err, int* zero_a, int* zero_b, int n_zero) {
+    pdl_enter();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     // the launch also clears the per-bin counters for k_bin_atoms and k_bin_scatter
     for (int t = k; t < n_zero; t += gridDim.x * blockDim.x) zero_a[t] = zero_b[t] = 0;
@@ -113,6 +114,7 @@ __global__ void k_cells(int K, const double* cells, const int* cfg_off, double r
 __global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, int S, const int* cfg_off,
                             const CellDesc* d, int* cfg_of, int* atom_bin, int* atom_wrap, float4* local,
                             float4* wp, int* bin_count, int* err) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int k = find_cfg(cfg_off, K, i);
@@ -153,6 +155,7 @@ __global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, i
 // Start of every non-empty bin in bin_atoms: one atomic per warp on the running total (the
 // placement order is irrelevant downstream, see k_cells).
 __global__ void k_alloc_bins(int nbins, const int* bin_count, int* bin_start, int* atom_total) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     for (int b0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; b0 < nbins; b0 += gridDim.x * blockDim.x) {
         const int b = b0 + lane;
@@ -171,6 +174,7 @@ __global__ void k_alloc_bins(int nbins, const int* bin_count, int* bin_start, in
 }
 
 __global__ void k_bin_scatter(int n, const int* atom_bin, const int* bin_start, int* bin_fill, int* bin_atoms) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int bin = atom_bin[i];
@@ -272,6 +276,7 @@ size_t build_smem(int cap, size_t realsz) { return kSmWarp + (size_t)kBuildWarps
 // whose candidates exceed one staging round are re-staged for every group of four atoms.
 template <class T>
 __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* cpos = reinterpret_cast<float4*>(smem_raw + kSmCpos);
     int* cshift = reinterpret_cast<int*>(smem_raw + kSmCshift);
@@ -710,19 +715,19 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
                                         nb.bin_fill.as<int>(), nz);
     }
     ++launches;
-    k_bin_atoms<<<(n + 63) / 64, 64, 0, st>>>(n, K, pos, types, S, cfg_off, desc, nb.cfg_of.as<int>(),
-                                                nb.atom_bin.as<int>(), nb.atom_wrap.as<int>(),
-                                                nb.atom_local.as<float4>(), nb.atom_wp.as<float4>(), bin_count,
-                                                nb.err.as<int>());
+    launch_pdl(k_bin_atoms, (n + 63) / 64, 64, 0, st, n, K, pos, types, S, cfg_off, (const CellDesc*)desc,
+               nb.cfg_of.as<int>(), nb.atom_bin.as<int>(), nb.atom_wrap.as<int>(), nb.atom_local.as<float4>(),
+               nb.atom_wp.as<float4>(), bin_count, nb.err.as<int>());
     ++launches;
     {
         int blocks = (total_bins_upper + 255) / 256;
         if (blocks > 152 * 8) blocks = 152 * 8;
-        k_alloc_bins<<<blocks, 256, 0, st>>>(total_bins_upper, bin_count, bin_start, counters + 1);
+        launch_pdl(k_alloc_bins, blocks, 256, 0, st, total_bins_upper, (const int*)bin_count, bin_start,
+                   counters + 1);
         ++launches;
     }
-    k_bin_scatter<<<(n + 63) / 64, 64, 0, st>>>(n, nb.atom_bin.as<int>(), bin_start, nb.bin_fill.as<int>(),
-                                                  nb.bin_atoms.as<int>());
+    launch_pdl(k_bin_scatter, (n + 63) / 64, 64, 0, st, n, (const int*)nb.atom_bin.as<int>(),
+               (const int*)bin_start, nb.bin_fill.as<int>(), nb.bin_atoms.as<int>());
     ++launches;
     BuildArgs a;
     a.n = n;
@@ -765,7 +770,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
                                  cudaSharedmemCarveoutMaxShared);
             attr64 = (int)smem;
         }
-        k_build<double><<<blocks, threads, smem, st>>>(a);
+        launch_pdl(k_build<double>, blocks, threads, smem, st, (const BuildArgs)a);
     } else {
         if ((int)smem > attr32) {
             cudaFuncSetAttribute(k_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -773,7 +778,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
                                  cudaSharedmemCarveoutMaxShared);
             attr32 = (int)smem;
         }
-        k_build<float><<<blocks, threads, smem, st>>>(a);
+        launch_pdl(k_build<float>, blocks, threads, smem, st, (const BuildArgs)a);
     }
     ++launches;
     {

@@ -12,7 +12,7 @@ per neighbour pair, forward (moments kernel):
 per neighbour pair, adjoint (pair-gradient kernel):
   the geometry and radial terms again, with derivatives: + (N_Q - 2) * 5 + 2 N_mu N_Q + 4 N_mu
   monomials of the value and its gradient
-  alpha_m = sum adj f, beta_m = sum adj df: 4 C; value term 2 per monomial; gradient terms
+  P_mu = sum adj mono, alpha_m = sum adj f: 4 C; s = sum df P: 2 N_mu; gradient terms
   2 per non-zero exponent; final r-hat scaling 7
 per atom (contraction kernel): forward program 2 flops per op, adjoint 4 flops per op, site energy 2 m
 per pair (gather kernel): force 6, virial 18
@@ -41,7 +41,7 @@ def counts(lev_max: int, n_radial: int):
     radial_fd = radial_f + max(NQ - 2, 0) * 5 + 2 * nmu * NQ + 4 * nmu
     n_grad_terms = sum(sum(1 for k in range(3) if m[k] > 0) for m in monos)
     pair_fwd = 5 + radial_f + len(monos) + 2 * C
-    pair_adj = 5 + radial_fd + len(grad_monos) + 4 * C + 2 * (len(monos) + 1) + 2 * n_grad_terms + 7
+    pair_adj = 5 + radial_fd + len(grad_monos) + 4 * C + 2 * nmu + 2 * n_grad_terms + 7
     ops = len(prog.ops)
     atom_contract = 2 * ops + 4 * ops + 2 * prog.basis.m
     pair_gather = 6 + 18
