@@ -610,6 +610,10 @@ def emit_slice_functions(prog: Program, slc, tag, slot_begin=None):
             for t, ci in enumerate(comps):
                 terms = [f"sl[{s * 32}]" for s in range(slot_begin[ci], slot_begin[ci + 1])] or ["T(0)"]
                 out.append(f"    if ({t} % TPA == sub) dst[{(t // 4) * 4} * NS + {t % 4}] = " + " + ".join(terms) + ";")
+                # a compiler fence after every 16 components of this lane: the loads of one group
+                # are in flight together, not all of them (their registers would set the kernel's
+                # count); with four or more lanes per atom a lane's share is small and needs none
+                out.append(f'    if (TPA <= 2 && {t + 1} % (16 * TPA) == 0) asm volatile("" ::: "memory");')
             out.append("  }")
         need = _closure(monos)
         out.append("  template <class T> static __device__ __forceinline__ void mom(const T x, const T y, const T z, "

@@ -216,14 +216,23 @@ __device__ __forceinline__ void radial(const T r, const T* __restrict__ cz, cons
     }
 }
 
+// Elements between the coefficient rows of two species pairs: one 16-byte vector more than the row,
+// so that lanes reading the same Chebyshev order for different species pairs hit different banks.
+template <class T>
+__host__ __device__ inline int coef_row(const EvalCtx<T>& a) {
+    return CoefPad<T>::value * a.NQ + 16 / (int)sizeof(T);
+}
+
 template <class T>
 __device__ __forceinline__ void load_c(const EvalCtx<T>& a, T* cs) {
-    // global c[z_i][z_j][mu][b] -> shared [z_i][z_j][b][mu padded]
+    // global c[z_i][z_j][mu][b] -> shared [z_i][z_j][b][mu padded], rows coef_row apart
     constexpr int P = CoefPad<T>::value;
-    const int nc = a.S * a.S * a.NQ * P;
+    const int row = coef_row(a);
+    const int nc = a.S * a.S * row;
     for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-        const int mu = k % P, b = (k / P) % a.NQ, pair = k / (P * a.NQ);
-        cs[k] = mu < G::NMU_ ? a.c[((size_t)pair * G::NMU_ + mu) * a.NQ + b] : T(0);
+        const int pair = k / row, e = k % row;
+        const int mu = e % P, b = e / P;
+        cs[k] = (mu < G::NMU_ && b < a.NQ) ? a.c[((size_t)pair * G::NMU_ + mu) * a.NQ + b] : T(0);
     }
     __syncthreads();
 }
@@ -231,7 +240,7 @@ __device__ __forceinline__ void load_c(const EvalCtx<T>& a, T* cs) {
 // bytes of the shared coefficient table
 template <class T>
 __host__ __device__ inline size_t coef_bytes(const EvalCtx<T>& a) {
-    return sizeof(T) * (size_t)a.S * a.S * a.NQ * CoefPad<T>::value;
+    return sizeof(T) * (size_t)a.S * a.S * coef_row(a);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -257,7 +266,7 @@ __device__ __forceinline__ void moments_slice(const EvalCtx<T>& a, int i, int su
     for (int t = 0; t < SL::SIZE; ++t) acc[t] = T(0);
     const size_t n = (size_t)a.n_atoms;
     if (active) {
-        const int csz = CoefPad<T>::value * a.NQ;
+        const int csz = coef_row(a);
         // the next pair's loads are issued before this pair's arithmetic (their latency overlaps it)
         PairIn<T> nx = load_pair(a, sub < cnt ? (size_t)sub * n + i : (size_t)i);
         for (int p = sub; p < cnt; p += TPA) {
@@ -558,10 +567,11 @@ template <class T, int S, int TPA, class A>
 __device__ __forceinline__ void pairgrad_pairs(const EvalCtx<T>& a, int i, int sub, int zi, int cnt, const T* cs,
                                                const A adj) {
     const size_t n = (size_t)a.n_atoms;
-    const int csz = CoefPad<T>::value * a.NQ;
+    const int csz = coef_row(a);
     // the next pair's loads are issued before this pair's arithmetic (their latency overlaps it)
     PairIn<T> nx{};
     if (sub < cnt) nx = load_pair(a, (size_t)sub * n + i);
+#pragma unroll 1
     for (int p = sub; p < cnt; p += TPA) {
         const size_t idx = (size_t)p * n + i;
         const PairIn<T> cur = nx;
@@ -647,8 +657,9 @@ __global__ void __launch_bounds__(128) k_pairgrad(const EvalCtx<T> a) {
 // k_gather: forces and virial
 // ----------------------------------------------------------------------------------------------
 // running per-configuration sums of the gather: the virial in the working precision T (its
-// per-pair terms are T already), the energy in double (so that E equals the double sum of the site
-// energies, Eq. 2, to double rounding); both reach the double outputs by atomics
+// per-pair terms are T already), the energy as a float pair in double-float arithmetic (about 44
+// significant bits, so that E equals the double sum of the site energies, Eq. 2, to ~1e-13
+// relative, with no double-precision arithmetic per atom); both reach the double outputs by atomics
 template <class T>
 __device__ __forceinline__ void flush_run(const EvalCtx<T>& a, int cfg, const T* run, double erun, bool want_e) {
     if (a.virial) {
@@ -683,7 +694,7 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
     const int stride = gridDim.x * blockDim.x;
     const int n_groups = ((a.n_atoms + 31) / 32) * 32;  // whole warps stay converged for the shuffles
     T Wrun[9];
-    double Erun = 0.0;
+    Df Erun = {0.f, 0.f};  // energy: an unevaluated float pair (error-free sums, no FP64 work)
 #pragma unroll
     for (int k = 0; k < 9; ++k) Wrun[k] = T(0);
     int wcfg = -1;
@@ -789,15 +800,15 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
         }
         if (active && (a.virial || want_e)) {
             if (cfg != wcfg) {
-                if (wcfg >= 0) flush_run(a, wcfg, Wrun, Erun, want_e);
+                if (wcfg >= 0) flush_run(a, wcfg, Wrun, (double)Erun.hi + (double)Erun.lo, want_e);
 #pragma unroll
                 for (int k = 0; k < 9; ++k) Wrun[k] = T(0);
-                Erun = 0.0;
+                Erun = {0.f, 0.f};
                 wcfg = cfg;
             }
 #pragma unroll
             for (int k = 0; k < 9; ++k) Wrun[k] += W[k];
-            if (want_e) Erun += (double)e_i;
+            if (want_e) Erun = df_add(Erun, {e_i, 0.f});
         }
     }
     if (!a.virial && !want_e) return;
@@ -817,7 +828,10 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
         }
         if (want_e) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) Erun += __shfl_xor_sync(0xffffffffu, Erun, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                const Df other = {__shfl_xor_sync(0xffffffffu, Erun.hi, o), __shfl_xor_sync(0xffffffffu, Erun.lo, o)};
+                Erun = df_add(Erun, other);
+            }
         }
         if (lane < 9) {
             T v = Wrun[0];
@@ -825,9 +839,9 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
             for (int k = 1; k < 9; ++k) v = lane == k ? Wrun[k] : v;
             s_w[warp][lane] = v;
         }
-        if (lane == 9) s_e[warp] = Erun;
+        if (lane == 9) s_e[warp] = (double)Erun.hi + (double)Erun.lo;
     } else if (wcfg >= 0) {
-        flush_run(a, wcfg, Wrun, Erun, want_e);
+        flush_run(a, wcfg, Wrun, (double)Erun.hi + (double)Erun.lo, want_e);
     }
     if (lane == 0) s_cfg[warp] = wuni ? cmax : -1;  // -1: nothing left to add
     __syncthreads();
@@ -864,6 +878,11 @@ int launch_pairs(const EvalCtx<T>& a, cudaStream_t st, int n_sm, bool moments) {
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
     if (moments) {
+        static bool attr_m = false;
+        if (!attr_m && cbytes > 48 * 1024) {  // 8 species with 16 radial functions in double
+            cudaFuncSetAttribute(k_moments<T, TPA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            attr_m = true;
+        }
         launch_pdl(k_moments<T, TPA>, blocks, threads, cbytes, st, a);
     } else {
         const size_t smem = ((cbytes + 15) & ~(size_t)15) + pairgrad_adj_bytes<T, TPA>();
@@ -1046,7 +1065,7 @@ __device__ __forceinline__ void tmom_slice(const EvalCtx<T>& a, int i, int sub, 
     for (int t = 0; t < SL::SIZE; ++t) acc[t] = T(0);
     const size_t n = (size_t)a.n_atoms;
     if (active) {
-        const int csz = CoefPad<T>::value * a.NQ;
+        const int csz = coef_row(a);
         for (int p = sub; p < cnt; p += TPA) {
             const size_t idx = (size_t)p * n + i;
             const int jz = a.jz[idx];
@@ -1376,6 +1395,11 @@ int launch_grad_pairs(EvalCtx<T>& a, cudaStream_t st, int n_sm) {
     if (blocks > n_sm * 16) blocks = n_sm * 16;
     if (blocks < 1) blocks = 1;
     const size_t cbytes = coef_bytes(a);
+    static bool attr_t = false;
+    if (!attr_t && cbytes > 48 * 1024) {
+        cudaFuncSetAttribute(k_tmom<T, TPA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr_t = true;
+    }
     k_tmom<T, TPA><<<blocks, threads, cbytes, st>>>(a);
     return 1;
 }
