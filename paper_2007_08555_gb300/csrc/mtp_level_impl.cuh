@@ -7,10 +7,13 @@
 //               accumulated in registers slice by slice (the slices are generated, unrolled code);
 //   k_contract  warp per atom: the generated contraction program (every basis function B_alpha),
 //               the site energy V_i = sum xi_alpha B_alpha (Eq. 2), then the adjoint program
-//               dV_i/dM, all in shared memory;
-//   k_pairgrad  thread group per atom: dV_i/dr_ij = sum adj * d(f_mu(r) mono(r))/dr per pair;
-//   k_gather    thread per atom: F_i = sum_p (g_ip - g_{j_p, reverse}) and the virial
-//               W = -sum g_ij (x) r_ij, reduced per configuration in double precision.
+//               dV_i/dM, all in shared memory (FP64 path); the float path runs the program in
+//               parts instead (k_contract_parts: one warp per part and 32 atoms);
+//   k_pairgrad  thread group per atom: dV_i/dr_ij = sum adj * d(f_mu(r) mono(r))/dr per pair, with
+//               dV_i/dM staged in shared memory on the float path;
+//   k_gather    thread group per atom: F_i = sum_p (g_ip - g_{j_p, reverse}) and the virial
+//               W = -sum g_ij (x) r_ij, summed per warp and added per configuration in double.
+// The kernels of one evaluation are chained by programmatic dependent launch (launch_pdl).
 #include "mtp_common.cuh"
 #include "mtp_level.h"
 
