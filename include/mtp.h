@@ -200,6 +200,25 @@ mtp_status mtp_set_active_set(mtp_model* model, const double* A);
  * directly; may be NULL).  MTP_ENOACTIVESET without an active set. */
 mtp_status mtp_get_active_set(const mtp_model* model, double* A, double* A_inv, int32_t* rows);
 
+/*
+ * Write the model to a text file (the paper has no counterpart: a library service; the MLIP
+ * package's own .mtp format is not used): lev_max, S, N_Q, R_min, R_cut, precision, skin,
+ * neighbour-list capacity, threads per atom, theta = {xi, c} and, when one is installed, the active
+ * set (A, A^-1 and its row indices).  Doubles are written with 17 significant digits, so every value
+ * reads back to the same bits.  Synchronous (reads A from the device).  MTP_EINVAL if the file cannot
+ * be written.
+ */
+mtp_status mtp_save(const mtp_model* model, const char* path);
+
+/*
+ * Create a model from a file written by mtp_save() on the current CUDA device.  The whole file is
+ * read and checked before any device work: a missing or malformed file, a wrong format version,
+ * counts that do not match lev_max / S / N_Q, or non-finite values give MTP_EINVAL and *out = NULL.
+ * The active set is installed as saved (A^-1 is not recomputed), so grades match the saved model bit
+ * for bit.
+ */
+mtp_status mtp_load(const char* path, mtp_model** out);
+
 /* Extrapolation grade of arbitrary rows (Sec. 2.3): gamma[r] = max_j |(b_r A^-1)_j| for b_rows
  * [n_rows][m] (double), in double precision.  Device arrays unless MTP_HOST_MEMORY. */
 mtp_status mtp_grade(mtp_model* model, int n_rows, const double* b_rows, double* gamma, int flags, void* stream);

@@ -1,9 +1,14 @@
 // C ABI of the MTP library (declared in include/mtp.h).
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <cerrno>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/mtp.h"
@@ -876,6 +881,186 @@ mtp_status mtp_get_active_set(const mtp_model* M, double* A, double* A_inv, int3
     if (A && cudaMemcpy(A, M->d_A.p, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
     if (A_inv && cudaMemcpy(A_inv, M->d_Ai.p, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
     if (rows) std::memcpy(rows, M->active_rows.data(), sizeof(int) * M->m);
+    return MTP_OK;
+}
+
+// ---- model files -------------------------------------------------------------------------------
+// Text, one "key value(s)" record after another in a fixed order; doubles with 17 significant
+// digits, so that every value reads back to the same bits.
+namespace {
+
+constexpr const char* kFileMagic = "mtp-gb300-potential";
+constexpr int kFileVersion = 1;
+
+struct ModelFile {
+    int L = 0, S = 0, NQ = 0, cap = 128, tpa_m = 0, tpa_p = 0;
+    double rmin = 0, rcut = 0, skin = 0;
+    mtp_precision prec = MTP_FP64;
+    std::vector<double> xi, c, A, Ai;
+    std::vector<int> rows;
+    bool active = false;
+};
+
+class Tokens {
+  public:
+    explicit Tokens(std::ifstream& f) : f_(f) {}
+    bool word(std::string& w) { return static_cast<bool>(f_ >> w); }
+    bool key(const char* k) {
+        std::string w;
+        return word(w) && w == k;
+    }
+    bool integer(long lo, long hi, long& v) {
+        std::string w;
+        if (!word(w)) return false;
+        errno = 0;
+        char* end = nullptr;
+        v = std::strtol(w.c_str(), &end, 10);
+        return errno == 0 && end && *end == '\0' && !w.empty() && v >= lo && v <= hi;
+    }
+    bool real(double& v) {
+        std::string w;
+        if (!word(w)) return false;
+        errno = 0;
+        char* end = nullptr;
+        v = std::strtod(w.c_str(), &end);
+        return errno == 0 && end && *end == '\0' && !w.empty() && std::isfinite(v);
+    }
+    // "<key> <count>" with the expected count, then the values
+    bool reals(const char* k, size_t count, std::vector<double>& out) {
+        long n = 0;
+        if (!key(k) || !integer(0, 1L << 30, n) || (size_t)n != count) return false;
+        out.resize(count);
+        for (size_t i = 0; i < count; ++i)
+            if (!real(out[i])) return false;
+        return true;
+    }
+
+  private:
+    std::ifstream& f_;
+};
+
+// Parse and check a model file completely (no CUDA call); false on any mismatch.
+bool parse_model_file(const char* path, ModelFile& mf) {
+    std::ifstream f(path);
+    if (!f) return false;
+    Tokens t(f);
+    long v = 0;
+    if (!t.key(kFileMagic) || !t.integer(kFileVersion, kFileVersion, v)) return false;
+    if (!t.key("lev_max") || !t.integer(2, 20, v) || v % 2) return false;
+    mf.L = (int)v;
+    if (!t.key("n_species") || !t.integer(1, mtp::kMaxSpecies, v)) return false;
+    mf.S = (int)v;
+    if (!t.key("n_radial") || !t.integer(1, mtp::kMaxRadial, v)) return false;
+    mf.NQ = (int)v;
+    if (!t.key("r_min") || !t.real(mf.rmin) || !t.key("r_cut") || !t.real(mf.rcut)) return false;
+    if (!(mf.rmin >= 0.0) || !(mf.rcut > mf.rmin)) return false;
+    std::string w;
+    if (!t.key("precision") || !t.word(w)) return false;
+    if (w == "fp64")
+        mf.prec = MTP_FP64;
+    else if (w == "fp32")
+        mf.prec = MTP_FP32;
+    else
+        return false;
+    if (!t.key("skin") || !t.real(mf.skin) || !(mf.skin >= 0.0) || mf.skin > 10.0) return false;
+    if (!t.key("neighbor_capacity") || !t.integer(1, 1024, v)) return false;
+    mf.cap = (int)v;
+    long tm = 0, tp = 0;
+    auto lanes_ok = [](long x) { return x == 0 || x == 1 || x == 2 || x == 4 || x == 8; };
+    if (!t.key("threads_per_atom") || !t.integer(0, 8, tm) || !t.integer(0, 8, tp) || !lanes_ok(tm) ||
+        !lanes_ok(tp))
+        return false;
+    mf.tpa_m = (int)tm;
+    mf.tpa_p = (int)tp;
+    const mtp::LevelOps* ops = mtp::level_ops(mf.L);
+    if (!ops) return false;
+    const size_t m = (size_t)ops->M;
+    const size_t nc = (size_t)mf.S * mf.S * ops->NMU * mf.NQ;
+    if (!t.reals("xi", m, mf.xi) || !t.reals("c", nc, mf.c)) return false;
+    if (!t.key("active_set") || !t.integer(0, 1, v)) return false;
+    mf.active = v == 1;
+    if (mf.active) {
+        if (!t.reals("A", m * m, mf.A) || !t.reals("A_inv", m * m, mf.Ai)) return false;
+        long n = 0;
+        if (!t.key("rows") || !t.integer(0, 1L << 30, n) || (size_t)n != m) return false;
+        mf.rows.resize(m);
+        for (size_t i = 0; i < m; ++i) {
+            long r = 0;
+            if (!t.integer(-1, 0x7fffffffL, r)) return false;
+            mf.rows[i] = (int)r;
+        }
+    }
+    return t.key("end") && !t.word(w);
+}
+
+void write_reals(std::FILE* f, const char* key, const double* v, size_t n) {
+    std::fprintf(f, "%s %zu\n", key, n);
+    for (size_t i = 0; i < n; ++i) std::fprintf(f, "%.17g%c", v[i], (i + 1) % 4 == 0 || i + 1 == n ? '\n' : ' ');
+}
+
+}  // namespace
+
+mtp_status mtp_save(const mtp_model* M, const char* path) {
+    if (!M || !path) return MTP_EINVAL;
+    const size_t m = (size_t)M->m;
+    std::vector<double> A, Ai;
+    if (M->has_active) {
+        A.resize(m * m);
+        Ai.resize(m * m);
+        if (cudaMemcpy(A.data(), M->d_A.p, sizeof(double) * m * m, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(Ai.data(), M->d_Ai.p, sizeof(double) * m * m, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return MTP_ECUDA;
+    }
+    std::FILE* f = std::fopen(path, "w");
+    if (!f) return MTP_EINVAL;
+    std::fprintf(f, "%s %d\n", kFileMagic, kFileVersion);
+    std::fprintf(f, "lev_max %d\nn_species %d\nn_radial %d\n", M->L, M->S, M->NQ);
+    std::fprintf(f, "r_min %.17g\nr_cut %.17g\n", M->rmin, M->rcut);
+    std::fprintf(f, "precision %s\nskin %.17g\n", M->prec == MTP_FP64 ? "fp64" : "fp32", M->skin);
+    std::fprintf(f, "neighbor_capacity %d\nthreads_per_atom %d %d\n", M->cap, M->tpa_moments, M->tpa_pairs);
+    write_reals(f, "xi", M->xi.data(), M->xi.size());
+    write_reals(f, "c", M->c.data(), M->c.size());
+    std::fprintf(f, "active_set %d\n", M->has_active ? 1 : 0);
+    if (M->has_active) {
+        write_reals(f, "A", A.data(), A.size());
+        write_reals(f, "A_inv", Ai.data(), Ai.size());
+        std::fprintf(f, "rows %zu\n", m);
+        for (size_t i = 0; i < m; ++i) std::fprintf(f, "%d%c", M->active_rows[i], (i + 1) % 16 == 0 || i + 1 == m ? '\n' : ' ');
+    }
+    std::fprintf(f, "end\n");
+    const bool ok = std::ferror(f) == 0;
+    return (std::fclose(f) == 0 && ok) ? MTP_OK : MTP_EINVAL;
+}
+
+mtp_status mtp_load(const char* path, mtp_model** out) {
+    if (!path || !out) return MTP_EINVAL;
+    *out = nullptr;
+    ModelFile mf;
+    if (!parse_model_file(path, mf)) return MTP_EINVAL;
+    mtp_model* M = nullptr;
+    mtp_status st = mtp_create(mf.L, mf.S, mf.NQ, mf.rmin, mf.rcut, mf.xi.data(), mf.c.data(), mf.prec, &M);
+    if (st) return st;
+    if (!st) st = mtp_set_skin(M, mf.skin);
+    if (!st) st = mtp_set_neighbor_capacity(M, mf.cap);
+    if (!st) st = mtp_set_threads_per_atom(M, mf.tpa_m, mf.tpa_p);
+    if (!st && mf.active) {
+        // A and A^-1 as saved (not recomputed), so that grades read back bit for bit
+        const size_t bytes = sizeof(double) * mf.A.size();
+        if (M->d_A.reserve(bytes) || M->d_Ai.reserve(bytes)) {
+            st = MTP_ENOMEM;
+        } else if (cudaMemcpy(M->d_A.p, mf.A.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+                   cudaMemcpy(M->d_Ai.p, mf.Ai.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            st = MTP_ECUDA;
+        } else {
+            M->active_rows = mf.rows;
+            M->has_active = true;
+        }
+    }
+    if (st) {
+        mtp_destroy(M);
+        return st;
+    }
+    *out = M;
     return MTP_OK;
 }
 

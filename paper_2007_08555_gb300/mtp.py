@@ -73,6 +73,8 @@ _SIGS = {
     "mtp_md_run": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _I, _P, _P, ctypes.POINTER(_I), _I, _P]),
     "mtp_select_active_set_noalloc": (_I, [_I, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
     "mtp_profile_read": (_I, [_P, _P, _I, ctypes.POINTER(_L)]),
+    "mtp_save": (_I, [_P, ctypes.c_char_p]),
+    "mtp_load": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
 }
 
 PHASES = ("neighbors", "moments", "contract", "pairgrad", "gather")
@@ -221,6 +223,16 @@ def mtp_select_active_set_noalloc(n_rows, m, b_rows, selected, a_inv=None, strea
     return int(sw.value)
 
 
+def mtp_save(h, path):
+    _check(load().mtp_save(h, os.fsencode(path)), "mtp_save")
+
+
+def mtp_load(path):
+    h = ctypes.c_void_p()
+    _check(load().mtp_load(os.fsencode(path), ctypes.byref(h)), "mtp_load")
+    return h
+
+
 def mtp_set_active_set(h, A):
     _check(load().mtp_set_active_set(h, _ptr(np.ascontiguousarray(A, dtype=np.float64))), "mtp_set_active_set")
 
@@ -268,6 +280,33 @@ class Model:
     @classmethod
     def from_params(cls, p, precision="fp64"):
         return cls(p.lev_max, p.n_species, p.n_radial, p.r_min, p.r_cut, p.xi, p.c, precision)
+
+    @classmethod
+    def load(cls, path):
+        """A model from a file written by save() (mtp_load)."""
+        h = mtp_load(path)
+        self = cls.__new__(cls)
+        self.h = h
+        lib = load()
+        self.m = lib.mtp_basis_count(h)
+        self.n_mu = lib.mtp_radial_count(h)
+        self.n_components = lib.mtp_moment_count(h)
+        # the file's header records the sizes that the handle does not expose
+        head = {}
+        with open(path) as f:
+            for line in f:
+                key, _, val = line.partition(" ")
+                if key in ("n_species", "n_radial", "precision"):
+                    head[key] = val.strip()
+                if key == "xi":
+                    break
+        self.n_species = int(head["n_species"])
+        self.n_radial = int(head["n_radial"])
+        self.precision = FP64 if head["precision"] == "fp64" else FP32
+        return self
+
+    def save(self, path):
+        mtp_save(self.h, path)
 
     def close(self):
         if getattr(self, "h", None):
