@@ -1,5 +1,6 @@
 """The generated per-pair code compiled for the host (g++): for every slice, the adjoint (`grad`)
-is the gradient of the moment accumulation (`mom`) contracted with dV/dM.
+is the gradient of the moment accumulation (`mom`) contracted with dV/dM, and the tangent
+functions of the loss gradient (`tmom`, `pdot`) are the directional derivatives they stand for.
 
 For a pair r = (x, y, z) with radial values f_mu(|r|), `mom` accumulates the slice's moment
 components M_t = f_mu(t) x^a y^b z^c (Eq. 5 for one neighbour); `grad` returns s and (gx, gy, gz)
@@ -43,6 +44,21 @@ def _build(L, tmp_path):
     src.append("  }")
     src.append("  out[0] = s; out[1] = gx; out[2] = gy; out[3] = gz;")
     src.append("}")
+    src.append('extern "C" void tmom(int k, double x, double y, double z, const double* f, const double* df, '
+               "double rdu, double ux, double uy, double uz, double* acc) {")
+    src.append("  switch (k) {")
+    for k in range(n):
+        src.append(f"    case {k}: gen::SliceF<{k}>::tmom<double>(x, y, z, f, df, rdu, ux, uy, uz, acc); break;")
+    src.append("  }")
+    src.append("}")
+    # pdot reads dV/dM and its tangent with the tile stride (32) from the slice's first component
+    src.append('extern "C" void pdot(int k, double x, double y, double z, const double* adjp, const double* adjtp, '
+               "double ux, double uy, double uz, double* P, double* Pd) {")
+    src.append("  switch (k) {")
+    for k in range(n):
+        src.append(f"    case {k}: gen::SliceF<{k}>::pdot<double>(x, y, z, adjp, adjtp, ux, uy, uz, P, Pd); break;")
+    src.append("  }")
+    src.append("}")
     cpp = tmp_path / f"slices_L{L}.cpp"
     so = tmp_path / f"slices_L{L}.so"
     cpp.write_text("\n".join(src) + "\n")
@@ -52,6 +68,8 @@ def _build(L, tmp_path):
     p = ctypes.POINTER(ctypes.c_double)
     lib.mom.argtypes = [ctypes.c_int, d, d, d, p, p]
     lib.grad.argtypes = [ctypes.c_int, d, d, d, p, p, p, p]
+    lib.tmom.argtypes = [ctypes.c_int, d, d, d, p, p, d, d, d, d, p]
+    lib.pdot.argtypes = [ctypes.c_int, d, d, d, p, p, d, d, d, p, p]
     return prog, lib
 
 
@@ -123,3 +141,73 @@ def test_planted_sign_error_is_caught(tmp_path):
     num = np.array([(value(v + h * e) - value(v - h * e)) / (2 * h) for e in np.eye(3)])
     assert np.abs(good - num).max() <= 1e-6 * np.abs(num).max()
     assert np.abs(bad - num).max() > 1e-3 * np.abs(num).max()
+
+
+@pytest.mark.parametrize("L", [10, 16, 20])
+def test_tangent_moments_are_directional_derivatives(L, tmp_path):
+    """tmom: the derivative of the slice's moment contributions along a pair displacement u."""
+    prog, lib = _build(L, tmp_path)
+    nmu = prog.n_mu
+    rng = np.random.default_rng(100 + L)
+    a_mu = rng.uniform(0.5, 1.5, nmu)
+
+    def radial(r):
+        return np.ascontiguousarray(np.cos(a_mu * r)), np.ascontiguousarray(-a_mu * np.sin(a_mu * r))
+
+    for k in range(lib.n_slices()):
+        size = lib.slice_size(k)
+
+        def mom(v):
+            acc = np.zeros(size)
+            f, _ = radial(float(np.linalg.norm(v)))
+            lib.mom(k, v[0], v[1], v[2], _ptr(f), _ptr(acc))
+            return acc
+
+        v = rng.standard_normal(3)
+        v *= 3.0 / np.linalg.norm(v)
+        u = rng.standard_normal(3)
+        r = float(np.linalg.norm(v))
+        f, df = radial(r)
+        acc = np.zeros(size)
+        lib.tmom(k, v[0], v[1], v[2], _ptr(f), _ptr(df), float(v @ u) / r, u[0], u[1], u[2], _ptr(acc))
+        h = 1e-5
+        num = (mom(v + h * u) - mom(v - h * u)) / (2 * h)
+        assert np.abs(acc - num).max() <= 1e-6 * max(np.abs(num).max(), 1e-300), (L, k)
+
+
+@pytest.mark.parametrize("L", [10, 16, 20])
+def test_pdot_is_the_monomial_sum_and_its_tangent(L, tmp_path):
+    """pdot: P_mu = sum_t adj_t mono_t over the components of radial index mu, and
+    Pd_mu = sum_t adjt_t mono_t + d/de P_mu(r + e u)."""
+    prog, lib = _build(L, tmp_path)
+    nmu = prog.n_mu
+    rng = np.random.default_rng(200 + L)
+    for k in range(lib.n_slices()):
+        size = lib.slice_size(k)
+
+        def P_of(v, adj):
+            # mom with f = e_mu picks out the components of radial index mu: P_mu = adj . acc
+            out = np.zeros(nmu)
+            for mu in range(nmu):
+                e = np.zeros(nmu)
+                e[mu] = 1.0
+                acc = np.zeros(size)
+                lib.mom(k, v[0], v[1], v[2], _ptr(e), _ptr(acc))
+                out[mu] = adj @ acc
+            return out
+
+        adj = rng.standard_normal(size)
+        adjt = rng.standard_normal(size)
+        tile = np.zeros(size * 32)
+        tile_t = np.zeros(size * 32)
+        tile[::32] = adj
+        tile_t[::32] = adjt
+        v = rng.standard_normal(3) * 1.7
+        u = rng.standard_normal(3)
+        P = np.zeros(nmu)
+        Pd = np.zeros(nmu)
+        lib.pdot(k, v[0], v[1], v[2], _ptr(tile), _ptr(tile_t), u[0], u[1], u[2], _ptr(P), _ptr(Pd))
+        np.testing.assert_allclose(P, P_of(v, adj), rtol=1e-12, atol=1e-12 * np.abs(P).max())
+        h = 1e-5
+        num = P_of(v, adjt) + (P_of(v + h * u, adj) - P_of(v - h * u, adj)) / (2 * h)
+        assert np.abs(Pd - num).max() <= 1e-6 * max(np.abs(num).max(), 1e-300), (L, k)
