@@ -5,11 +5,13 @@ For random moment values of a synthetic neighbourhood, for every partition into 
 * the basis values B_alpha the parts write equal an independent full-Cartesian numpy.einsum
   contraction of the moment tensors for each graph of the oracle's level table (Sec. 2.1);
 * the site-energy shares add up to V = sum_alpha xi_alpha B_alpha (Eq. 2);
-* the dV/dM slots of each component add up to the derivative of V, checked by central differences.
-No GPU.
+* the dV/dM slots of each component add up to the derivative of V, checked by central differences;
+and for the tangent parts of the loss gradient, the per-basis terms ek B - dB/de along a moment
+tangent T and the tangent dV/dM slots, against central differences.  No GPU.
 """
 
 import ctypes
+import itertools
 import shutil
 import string
 import subprocess
@@ -130,3 +132,90 @@ def test_parts_evaluate_the_basis_and_its_adjoint(L, parts, tmp_path):
         em = _run(lib, prog, parts, sm, xi)[0]
         num = (ep - em) / (2 * h)
         assert adj[c] == pytest.approx(num, rel=1e-6, abs=1e-7 * max(abs(e) / scale, 1e-12)), (L, parts, c)
+
+
+def _build_dual(L, parts, tmp_path):
+    prog = codegen.build_program(L)
+    lines = codegen.emit_dual_parts(prog, parts)
+    C = len(prog.comp_list)
+    # one lane: the warp sum of a lane's term is the term itself (the other lanes add zeros)
+    src = ["#include <cstddef>", "#define __device__", "#define __forceinline__ inline", "#define float double",
+           "inline double __shfl_xor_sync(unsigned, double, int) { return 0.0; }", "namespace gen {"] + lines + ["}"]
+    src.append('extern "C" void run_dual(int g, const double* m, const double* mt, double* adj, double* adt, '
+               "const double* xi, double ek, double* dxt) {")
+    src.append("  gen::dual_part(g, m, mt, adj, adt, xi, ek, true, true, dxt);")
+    src.append("}")
+    src.append(f'extern "C" int dslot_begin_at(int c) {{ return c <= {C} ? gen::dslot_begin[c] : -1; }}')
+    src.append('extern "C" int n_dslots() { return gen::NDSLOT; }')
+    cpp = tmp_path / f"dual_L{L}_{parts}.cpp"
+    so = tmp_path / f"dual_L{L}_{parts}.so"
+    cpp.write_text("\n".join(src) + "\n")
+    subprocess.run(["g++", "-O1", "-shared", "-fPIC", "-o", str(so), str(cpp)], check=True)
+    lib = ctypes.CDLL(str(so))
+    p = ctypes.POINTER(ctypes.c_double)
+    lib.run_dual.restype = None
+    lib.run_dual.argtypes = [ctypes.c_int, p, p, p, p, p, ctypes.c_double, p]
+    return prog, lib
+
+
+def _run_dual(lib, prog, parts, m_tile, t_tile, xi, ek):
+    nd = lib.n_dslots()
+    adj, adt = np.zeros(nd * 32), np.zeros(nd * 32)
+    dxt = np.full(len(xi), np.nan)
+    for g in range(parts):
+        lib.run_dual(g, _ptr(m_tile), _ptr(t_tile), _ptr(adj), _ptr(adt), _ptr(xi), ek, _ptr(dxt))
+    C = len(prog.comp_list)
+
+    def per_comp(a):
+        return np.array([a[[s * 32 for s in range(lib.dslot_begin_at(c), lib.dslot_begin_at(c + 1))]].sum()
+                         for c in range(C)])
+
+    return per_comp(adj), per_comp(adt), dxt
+
+
+@pytest.mark.parametrize("L,parts", [(10, 1), (12, 2), (16, 8)])
+def test_dual_parts_are_the_tangent_contraction(L, parts, tmp_path):
+    """dxt_alpha = ek B_alpha - dB_alpha/de (M + e T); the dV/dM slots add up to dV/dM and the tangent
+    slots to its directional derivative along T (central differences of the value and adjoint)."""
+    prog, lib = _build_dual(L, parts, tmp_path)
+    rng = np.random.default_rng(L * 100 + parts)
+    M = _neighbourhood(L, rng)
+    m_tile = _tile(prog, M)
+    C = len(prog.comp_list)
+    t_tile = np.zeros_like(m_tile)
+    t_tile[::32] = rng.normal(size=C) * np.abs(m_tile[::32]).mean()
+    m = len(levels.basis(L))
+    xi = rng.normal(size=m)
+    ek = 0.37
+    adj, adt, dxt = _run_dual(lib, prog, parts, m_tile, t_tile, xi, ek)
+    assert not np.isnan(dxt).any(), "every basis function is written by exactly one part"
+
+    def comps_to_cart(tile):
+        # moment tensors from tile values: the symmetric tensor with the given components
+        out = {}
+        for c, (mu, (a, b, cc)) in enumerate(prog.comp_list):
+            nu = a + b + cc
+            key = (mu, nu)
+            if key not in out:
+                out[key] = np.zeros((3,) * nu)
+            for idx in set(itertools.permutations((0,) * a + (1,) * b + (2,) * cc)):
+                out[key][idx] = tile[c * 32]
+        for key, val in M.items():
+            out.setdefault(key, val)
+        return out
+
+    h = 1e-6
+    Bp = _einsum_basis(comps_to_cart(m_tile + h * t_tile), L)
+    Bm = _einsum_basis(comps_to_cart(m_tile - h * t_tile), L)
+    B0 = _einsum_basis(comps_to_cart(m_tile), L)
+    np.testing.assert_allclose(B0, _einsum_basis(M, L), rtol=1e-12, atol=1e-14 * np.abs(B0).max())
+    ref = ek * B0 - (Bp - Bm) / (2 * h)
+    np.testing.assert_allclose(dxt, ref, rtol=1e-6, atol=1e-7 * np.abs(ref).max())
+    # tangent slots: the directional derivative of the dV/dM slots computed by the same code
+    ap = _run_dual(lib, prog, parts, m_tile + h * t_tile, t_tile, xi, ek)[0]
+    am = _run_dual(lib, prog, parts, m_tile - h * t_tile, t_tile, xi, ek)[0]
+    np.testing.assert_allclose(adt, (ap - am) / (2 * h), rtol=1e-6, atol=1e-7 * np.abs(adt).max())
+    # and the dV/dM slots equal those of the forward parts (which are pinned above)
+    _, fl = _build(L, codegen.CONTRACT_PARTS[L], tmp_path)
+    _, _, adj_f = _run(fl, prog, codegen.CONTRACT_PARTS[L], m_tile, xi)
+    np.testing.assert_allclose(adj, adj_f, rtol=1e-12, atol=1e-12 * np.abs(adj_f).max())
