@@ -595,15 +595,9 @@ def emit_slice_functions(prog: Program, slc, tag, slot_begin=None):
         out.append(f"template <> struct {name}<{si}> {{")
         out.append(f"  static constexpr int BEGIN = {min(comps)}, SIZE = {len(comps)};")
         if slot_begin is not None:
-            # dV/dM of this slice's components from the contraction parts' slots (slot order)
-            out.append("  template <class T> static __device__ __forceinline__ void adj_from_slots("
-                       "const T* __restrict__ sl, T* __restrict__ adj) {")
-            for t, ci in enumerate(comps):
-                terms = [f"sl[{s * 32}]" for s in range(slot_begin[ci], slot_begin[ci + 1])] or ["T(0)"]
-                out.append(f"    adj[{t}] = " + " + ".join(terms) + ";")
-            out.append("  }")
-            # the same sums written to shared memory in groups of four components (one 16-byte
-            # vector per group and atom, groups NS vectors apart), component t by the lane with
+            # dV/dM of this slice's components: the contraction parts' slots summed in slot
+            # order, written to shared memory in groups of four components (one 16-byte vector
+            # per group and atom, groups NS vectors apart), component t by the lane with
             # t % TPA == sub of the atom's TPA lanes
             out.append("  template <class T, int TPA, int NS> static __device__ __forceinline__ void adj_to_shared("
                        "const T* __restrict__ sl, T* __restrict__ dst, const int sub) {")
