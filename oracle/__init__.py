@@ -156,13 +156,16 @@ class Potential:
         return q, dq
 
     def eval_sampled(self, cfg, which, threads=0):
-        """Site energies, basis rows and forces of the listed atoms only (for large cells)."""
+        """Site energies, basis rows and forces of the listed atoms only (for large cells): V_i, B(n_i)
+        and F_i = -dE/dx_i, with the neighbour lists searched among the atoms within 2 R_cut."""
         which = _i32(which)
         pos, types, cell = _f64(cfg.pos), _i32(cfg.types), _f64(cfg.cell)
         k = which.shape[0]
         site = np.zeros(k)
         b = np.zeros((k, self.m))
         f = np.zeros((k, 3))
-        lib().oracle_eval_sampled(self.h, _d(_f64(self.p.xi)), _d(_f64(self.p.c)), pos.shape[0], _d(pos),
-                                  _i(types), _d(cell), _i(which), k, _d(site), _d(b), _d(f), int(threads))
+        rc = lib().oracle_eval_sampled(self.h, _d(_f64(self.p.xi)), _d(_f64(self.p.c)), pos.shape[0], _d(pos),
+                                       _i(types), _d(cell), _i(which), k, _d(site), _d(b), _d(f), int(threads))
+        if rc != 0:
+            raise ValueError("oracle_eval_sampled: atom or species index out of range")
         return {"site": site, "b_atoms": b, "forces": f}

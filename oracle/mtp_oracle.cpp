@@ -118,13 +118,18 @@ void widths(const double* H, double* w) {
 // Brute force over every atom j and every image shift that could lie within R_cut:
 // |(f_j - f_i + s)_k| * width_k <= |r| bounds each shift component from the fractional
 // displacement f, so the finite range below (rounded outwards) contains every solution.
-std::vector<Pair> neighbours_of(int i, int n, const double* pos, const double* H, double rcut) {
+// With `cand` (ascending atom indices) only those atoms are tried as j: the result is the full
+// list whenever every neighbour of i is among them.
+std::vector<Pair> neighbours_of(int i, int n, const double* pos, const double* H, double rcut,
+                                const std::vector<int>* cand = nullptr) {
     double Hi[9], vol, w[3];
     inverse3(H, Hi, &vol);
     widths(H, w);
     const double rc2 = rcut * rcut;
     std::vector<Pair> out;
-    for (int j = 0; j < n; ++j) {
+    const int count = cand ? (int)cand->size() : n;
+    for (int t = 0; t < count; ++t) {
+        const int j = cand ? (*cand)[t] : t;
         double dx[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1], pos[3 * j + 2] - pos[3 * i + 2]};
         int lo[3], hi[3];
         for (int k = 0; k < 3; ++k) {
@@ -490,13 +495,21 @@ int oracle_eval(void* model, const double* xi_, const double* c_, int n, const d
 
 // Site energies, basis rows and forces restricted to a sample of atoms of a large
 // configuration: V_i and B(n_i) for i in `which`, and the force on each sampled atom k,
-// assembled from V_k and the site energies of k's neighbours (every i with k in n_i is a
-// neighbour of k, because the neighbour relation is symmetric under r_ij -> -r_ij).
+//   F_k = -dE/dx_k = sum over pairs (k, j, s) of n_k with j != k of dV_k/dr_kj
+//                    - sum over atoms i != k of sum over pairs (i, k, s) of n_i of dV_i/dr_ik.
+// A self-image pair (k, k, s != 0) has r = s H, which does not move with x_k, so it gives no
+// force (in the full evaluation its two terms cancel).  Every i with k in n_i is within R_cut of
+// k, and each of i's neighbours is within 2 R_cut of k, so the neighbour lists are searched only
+// among the atoms that have an image within 2 R_cut of k (the same lists as a search over all atoms).
 int oracle_eval_sampled(void* model, const double* xi_, const double* c_, int n, const double* pos,
                         const int* types, const double* cell, const int* which, int count, double* site,
                         double* batoms, double* forces, int nthreads) {
     const Model& M = *(Model*)model;
     const int nc = M.S * M.S * M.Nmu * M.NQ;
+    for (int t = 0; t < count; ++t)
+        if (which[t] < 0 || which[t] >= n) return 1;
+    for (int i = 0; i < n; ++i)
+        if (types[i] < 0 || types[i] >= M.S) return 1;
     std::vector<double> xi(xi_, xi_ + M.m), c(c_, c_ + nc);
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -504,7 +517,12 @@ int oracle_eval_sampled(void* model, const double* xi_, const double* c_, int n,
 #pragma omp parallel for schedule(dynamic, 1)
     for (int t = 0; t < count; ++t) {
         const int k = which[t];
-        std::vector<Pair> nk = neighbours_of(k, n, pos, cell, M.rcut);
+        std::vector<int> cand;
+        for (const Pair& p : neighbours_of(k, n, pos, cell, 2.0 * M.rcut)) cand.push_back(p.j);
+        cand.push_back(k);
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        std::vector<Pair> nk = neighbours_of(k, n, pos, cell, M.rcut, &cand);
         Site<double> sk = eval_site(M, xi, c, types[k], nk, types);
         if (site) site[t] = sk.V;
         if (batoms)
@@ -512,7 +530,8 @@ int oracle_eval_sampled(void* model, const double* xi_, const double* c_, int n,
         if (!forces) continue;
         double F[3] = {0, 0, 0};
         for (size_t p = 0; p < nk.size(); ++p)
-            for (int a = 0; a < 3; ++a) F[a] += sk.g[p][a];
+            if (nk[p].j != k)
+                for (int a = 0; a < 3; ++a) F[a] += sk.g[p][a];
         // contributions of V_i for each distinct neighbour atom i != k
         std::vector<int> others;
         for (const Pair& p : nk)
@@ -520,7 +539,7 @@ int oracle_eval_sampled(void* model, const double* xi_, const double* c_, int n,
         std::sort(others.begin(), others.end());
         others.erase(std::unique(others.begin(), others.end()), others.end());
         for (int i : others) {
-            std::vector<Pair> ni = neighbours_of(i, n, pos, cell, M.rcut);
+            std::vector<Pair> ni = neighbours_of(i, n, pos, cell, M.rcut, &cand);
             Site<double> si = eval_site(M, xi, c, types[i], ni, types);
             for (size_t p = 0; p < ni.size(); ++p)
                 if (ni[p].j == k)

@@ -257,3 +257,53 @@ def test_neighbours_equal_independent_brute_force():
                     if np.dot(dd, dd) < 25.0:
                         want.add((i, jj, sv))
         assert got == want
+
+
+def _sampled_cases():
+    rng = np.random.default_rng(31)
+    one = synth.Config(np.array([[0.3, 0.2, 0.1]]), np.zeros(1, np.int32), np.diag([2.6, 2.9, 3.1]))
+    cases = [("one atom, self images", one)]
+    for kind, reps, label in (("bcc", (1, 1, 1), "2 atoms, self images"), ("fcc", (1, 1, 2), "8 atoms, self images"),
+                              ("hcp", (2, 2, 2), "16 atoms, self images along c"),
+                              ("fcc", (2, 2, 2), "32 atoms, no self images")):
+        cfg = synth.perturbed(kind, reps, 0.1, rng, n_species=3)
+        cases.append((label, cfg))
+    return cases
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_sampled_evaluation_equals_full_evaluation(case):
+    """The sampled evaluation (used for cells too large for the full oracle) gives the site energies,
+    basis rows and forces of the full evaluation, on cells whose atoms see their own periodic images
+    (a self-image pair r = s H does not move with the atom and must give no force) and on one
+    without."""
+    label, cfg = _sampled_cases()[case]
+    p = _params(12, S=3, seed=5)
+    pot = oracle.Potential(p)
+    full = pot.eval(cfg, want_b=True)
+    which = np.arange(cfg.n, dtype=np.int32)[::-1].copy()
+    smp = pot.eval_sampled(cfg, which)
+    scale_f = max(np.abs(full["forces"]).max(), 1e-300)
+    np.testing.assert_allclose(smp["site"], full["site"][which], rtol=1e-12, atol=1e-12 * np.abs(full["site"]).max())
+    np.testing.assert_allclose(smp["b_atoms"], full["b_atoms"][which], rtol=1e-12,
+                               atol=1e-12 * np.abs(full["b_atoms"]).max())
+    np.testing.assert_allclose(smp["forces"], full["forces"][which], rtol=0, atol=1e-12 * scale_f, err_msg=label)
+    if cfg.n == 1:  # moving the only atom moves every image with it: no force at all
+        np.testing.assert_allclose(smp["forces"], 0.0, atol=1e-12 * np.abs(full["site"]).max())
+
+
+def test_sampled_forces_are_finite_differences():
+    """Sampled forces of a 2-atom cell (every neighbour pair of each atom includes images of itself)
+    equal central differences of the full energy."""
+    rng = np.random.default_rng(8)
+    cfg = synth.perturbed("bcc", (1, 1, 1), 0.1, rng, n_species=2)
+    pot = oracle.Potential(_params(10, S=2, seed=3))
+    smp = pot.eval_sampled(cfg, np.array([0, 1], dtype=np.int32))
+    h = 1e-5
+    for i in range(2):
+        for a in range(3):
+            cp, cm = synth.Config(cfg.pos.copy(), cfg.types, cfg.cell), synth.Config(cfg.pos.copy(), cfg.types, cfg.cell)
+            cp.pos[i, a] += h
+            cm.pos[i, a] -= h
+            fd = -(pot.eval(cp)["energy"] - pot.eval(cm)["energy"]) / (2 * h)
+            assert abs(smp["forces"][i, a] - fd) <= 1e-6 * max(1.0, np.abs(smp["forces"]).max()), (i, a)
