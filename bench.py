@@ -5,6 +5,9 @@ occupancy, Gaussian displacements sigma = 0.15 Angstrom, lev_max = 16, N_Q = 8, 
 R_cut = 5 Angstrom, random parameters (synthetic stand-in for the paper's DFT datasets).
 One step = neighbour search + energy, forces and virial (every kernel of the path), FP32 path.
 Metric: atoms/s (higher is better).  L2 is flushed (a 512 MiB write) between timed steps.
+The same line carries sub-records of the other two stated evaluation workloads: 4096 cells of
+8-256 atoms at lev_max 16 with the grade of every cell (batched), and the 1,048,576-atom ternary
+fcc cell at lev_max 20, each with its FP64-path figure.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
 workload (an 8x8x8 cell cut with the same recipe), as the reference arm.
@@ -45,11 +48,37 @@ def parse():
     ap.add_argument("--md-steps", type=int, default=100)
     ap.add_argument("--profile-run", action="store_true",
                     help="only the timed FP32 steps (for ncu launch lists); prints the bench line without the "
-                         "FP64, end-to-end and CPU legs")
+                         "FP64, end-to-end, sub-workload and CPU legs")
+    ap.add_argument("--no-sub", action="store_true", help="skip the batched and lev_max-20 sub-records")
     return ap.parse_args()
 
 
-PAIRGRAD_DRAM_BYTES = 31057664 + 0  # dram__bytes_read.sum + dram__bytes_write.sum, one launch
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a kernel on the headline
+# workload, from one ncu capture of the current kernel (profiles/); None when not captured since the
+# kernel last changed
+TRAFFIC = {"k_build": None, "k_pairgrad": None, "k_moments": None, "k_contract_parts": None, "k_gather": None}
+PHASE_KERNEL = {"neighbors": "k_build", "moments": "k_moments", "contract": "k_contract_parts",
+                "pairgrad": "k_pairgrad", "gather": "k_gather"}
+
+
+def measured_peaks():
+    """HBM and bf16 peaks from the generated MEASURED_PEAKS.json (else the recipe's fallback) and the
+    FP32 FMA peak measured now by the library's microbenchmark."""
+    from paper_2007_08555_gb300 import mtp
+
+    out = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            m = json.load(open(path))
+            for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained"):
+                if m.get(k):
+                    out[k] = float(m[k])
+            out["source"] = "measured (MEASURED_PEAKS.json)"
+        except (OSError, ValueError):
+            pass
+    out["fp32_tflops"] = mtp.mtp_fp32_peak(9)
+    return out
 
 
 def dist_env():
@@ -228,25 +257,41 @@ def run_ours(args):
     h2d = h_pos.numel() * 8 + h_types.numel() * 4 + h_cells.numel() * 8 + h_off.numel() * 4
     d2h = h_e.numel() * 8 + h_f.numel() * 8 + h_w.numel() * 8
 
-    # roofline of the dominant kernel phase
+    # roofline of the dominant phase (every phase of the step, the neighbour search included)
     per_call = {k: v / max(calls, 1) for k, v in phase_ms.items()}
-    kern = {k: per_call[k] for k in ("moments", "contract", "pairgrad", "gather")}
-    dom = max(kern, key=kern.get)
-    peak = flops.fp32_peak_tflops()
-    achieved = fl[dom] / (kern[dom] * 1e-3) / 1e12
+    peaks = measured_peaks()
+    peak = peaks["fp32_tflops"]
+    dom = max(per_call, key=per_call.get)
+    headline_cfg = args.lev == 16 and args.reps == 16
+    traffic = TRAFFIC.get(PHASE_KERNEL[dom]) if headline_cfg else None
     total_flops = sum(fl.values())
-    # DRAM bytes (read + write) of one k_pairgrad launch on this workload, from the ncu capture in
-    # profiles/kernels_fcc16_lev16.md; valid while that kernel is unchanged
-    traffic = PAIRGRAD_DRAM_BYTES if (dom == "pairgrad" and args.lev == 16 and args.reps == 16) else None
-    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_note": "FP32 FMA peak derived: 152 SM x 128 lanes x 2 flop x 2.07 GHz",
-                "path_frac": round(total_flops / (ms * 1e-3) / 1e12 / peak, 4)}
+    path_frac = round(total_flops / (ms * 1e-3) / 1e12 / peak, 4)
+    if dom == "neighbors":
+        nbytes = flops.neighbor_bytes(n, n_pairs, 4)
+        achieved = nbytes / (per_call[dom] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_build (neighbour phase, binning kernels included)",
+                    "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                    "algorithmic_bytes": nbytes, "peak_note": peaks["source"] + ", copy bandwidth",
+                    "path_frac": path_frac}
+    else:
+        achieved = fl[dom] / (per_call[dom] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": PHASE_KERNEL[dom], "achieved": round(achieved, 3),
+                    "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "peak_note": "FP32 FMA peak measured by mtp_fp32_peak (median of 9 launches)",
+                    "path_frac": path_frac}
+    roofline["peak_fp32_measured_tflops"] = round(peak, 2)
+    roofline["peak_fp32_from_units_tflops"] = round(flops.fp32_peak_tflops(
+        torch.cuda.get_device_properties(local).multi_processor_count, clk.get("sm_mhz") or 2070.0), 2)
     out = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(args.lev)
+        sub = {}
+        if not args.no_sub and world == 1:
+            sub["batch4096_lev16"] = batch_record(args, peaks)
+            sub["eval1m_lev20"] = eval1m_record(args, peaks)
         out = {
             "metric": METRIC, "value": round(value, 1), "unit": "atoms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max, 5), "higher_is_better": True, "scaling": "weak",
@@ -262,6 +307,8 @@ def run_ours(args):
             "roofline": roofline,
             "phases_ms": {k: round(v, 5) for k, v in per_call.items()},
             "fp64_path": {"value": round(fp64_value, 1), "unit": "atoms/s", "speedup_fp32_over_fp64": round(value / world / fp64_value, 2)},
+            "tensor": (sub.get("batch4096_lev16") or {}).get("tensor"),
+            "sub": sub,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out))
@@ -339,6 +386,81 @@ def _line(args, metric_note, value, ms, config, extra, dtype="f32", unit="atoms/
            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config, "note": metric_note}
     out.update(extra)
     print(json.dumps(out))
+
+
+def batch_record(args, peaks):
+    """4096 cells of 8-256 atoms, lev_max 16: E+F+W with the grade of every cell (Sec. 2.3), in one call
+    per step replayed as a CUDA graph; evaluation only, per-atom grades and the FP64 path beside it."""
+    import torch
+
+    from paper_2007_08555_gb300 import codegen, mtp, synth
+
+    b = synth.small_cells(n_cfg=4096, seed=3)
+    m = codegen.build_basis(16).m
+    p = synth.random_params(16, 3, 8, 2.0, 5.0, m, seed=3)
+    d = lambda a, t=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device="cuda")
+    pos, types, cells, off = d(b.pos), d(b.types, torch.int32), d(b.cells), d(b.cfg_off, torch.int32)
+    stream = torch.cuda.current_stream()
+    m64 = mtp.Model.from_params(p, "fp64")
+    rows = m64.eval_batch(pos, types, cells, off, b_rows=True)["b_rows"]
+    sel, swaps, _ = m64.select_active_set(rows[:2 * m].contiguous())
+    A, _, _ = mtp.mtp_get_active_set(m64.h, m)
+    model = mtp.Model.from_params(p, "fp32")
+    mtp.mtp_set_active_set(model.h, A)
+    outs = {}
+
+    def call(mod, key, **kw):  # the same output tensors every call: the library replays its CUDA graph
+        outs[key] = mod.eval_batch(pos, types, cells, off, out=outs.get(key), **kw)
+
+    steps = max(5, args.steps // 2)
+    ms = _timed(lambda: call(model, "cfg", grade_cfg=True), steps, 3, stream)
+    ms_eval = _timed(lambda: call(model, "eval"), steps, 3, stream)
+    ms_atom = _timed(lambda: call(model, "atom", grade_cfg=True, grade_atom=True), steps, 3, stream)
+    ms64 = _timed(lambda: call(m64, "fp64"), 3, 1, stream)
+    n = b.n_atoms
+    return {"workload": f"4096 strained fcc/bcc/hcp cells of 8-256 atoms ({n} atoms), 1-3 species, lev_max=16, "
+                        "E+F+W and the grade of every cell", "value": round(n / (ms * 1e-3), 1), "unit": "atoms/s",
+            "ms_per_step": round(ms, 4), "eval_only_atoms_per_s": round(n / (ms_eval * 1e-3), 1),
+            "with_atom_grades_atoms_per_s": round(n / (ms_atom * 1e-3), 1),
+            "fp64_path_atoms_per_s": round(n / (ms64 * 1e-3), 1),
+            "maxvol": {"rows": 2 * m, "m": m, "swaps": swaps}, "tensor": None, "l2": "inputs ~12 MB, not flushed"}
+
+
+def eval1m_record(args, peaks):
+    """One evaluation (neighbour build + E/F/W) of the 1,048,576-atom ternary fcc cell at lev_max 20 on
+    the stated recipe (R_min 2, c ~ N(0, 0.1), xi scaled per basis function)."""
+    import torch
+
+    from paper_2007_08555_gb300 import codegen, flops, mtp, synth
+
+    cfg = synth.fcc_ternary()
+    labels = synth.labels_from_level_table(codegen.level_table(codegen.build_basis(20)))
+    p = synth.scaled_params(20, 3, 8, 2.0, 5.0, labels, seed=5)
+    d = lambda a, t=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device="cuda")
+    pos, types = d(cfg.pos), d(cfg.types, torch.int32)
+    cells, off = d(cfg.cell.reshape(1, 3, 3)), d(np.array([0, cfg.n]), torch.int32)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for prec, steps in (("fp32", max(5, args.steps // 2)), ("fp64", 2)):
+        model = mtp.Model.from_params(p, prec)
+        out = {}
+        step = lambda: out.update(model.eval_batch(pos, types, cells, off, out=out or None))
+        mtp.mtp_profile(model.h, True)
+        res[prec] = (_timed(step, steps, 2, stream), mtp.mtp_profile_read(model.h), model)
+    ms, (phase, calls), model = res["fp32"]
+    counts, _, _, _ = model.neighbors(pos, cells, off)
+    n_pairs = int(counts.sum().item())
+    fl = flops.per_evaluation(20, 8, cfg.n, n_pairs)
+    per = {k: v / max(calls, 1) for k, v in phase.items()}
+    peak = peaks["fp32_tflops"]
+    return {"workload": f"fcc 64^3 ternary alloy, {cfg.n} atoms, lev_max=20, one E+F+W evaluation incl. neighbour build",
+            "value": round(cfg.n / (ms * 1e-3), 1), "unit": "atoms/s", "ms_per_step": round(ms, 4),
+            "n_pairs": n_pairs, "phases_ms": {k: round(v, 4) for k, v in per.items()},
+            "tflops_per_phase": {k: round(fl[k] / (per[k] * 1e-3) / 1e12, 2) for k in fl if per.get(k)},
+            "path_tflops": round(sum(fl.values()) / (ms * 1e-3) / 1e12, 2),
+            "path_frac": round(sum(fl.values()) / (ms * 1e-3) / 1e12 / peak, 4),
+            "fp64_path_atoms_per_s": round(cfg.n / (res["fp64"][0] * 1e-3), 1),
+            "speedup_fp32_over_fp64": round(res["fp64"][0] / ms, 2)}
 
 
 def run_batch(args):

@@ -180,8 +180,11 @@ mtp_status mtp_select_active_set(mtp_model* model, int n_rows, const double* b_r
  * cudaMalloc could synchronise the device and stall other work, or an application whose device
  * memory is entirely owned by its own pool -- it runs the algorithm of mtp_select_active_set() with
  * all scratch in one fixed array built into the library (4 MiB, held on every GPU that loads the
- * library until the process exits).  Limit: the scratch layout for n_rows x m must fit that array
- * (about n_rows * m <= 100,000 for m near 100); larger sizes return MTP_EINVAL before any work.
+ * library until the process exits).  Limit: the scratch layout must fit that array of 524,288
+ * doubles, i.e.  2 n m + max(n m, 2 m^2) + 2 m^2 + 3 m + n + ceil((n + m + 2) / 2) + 1 <= 524,288
+ * with n = n_rows (n <= 1421 at m = 116, n <= 1671 at m = 100; n = 2 m fits up to m = 255, so the
+ * lev_max-20 basis, m = 460, does not fit);
+ * larger sizes return MTP_EINVAL before any work.
  * Inputs and outputs are the caller's device arrays: b_rows [n_rows][m] (double), selected [m]
  * (int32, the chosen row of each position), a_inv [m][m] (double, may be NULL); n_swaps is a host
  * pointer (may be NULL).  It needs no model and keeps no active set.  The first call on each device
@@ -230,7 +233,7 @@ mtp_status mtp_grade(mtp_model* model, int n_rows, const double* b_rows, double*
  * 1 "structures" (Eq. 11: 1/N^2, 1/N, 1/N^2), 2 "vibrations" (Eq. 12: 1/N, 1, 1/N); the stress
  * term uses the virial W (eV, extensive).  The batch layout is that of mtp_eval_batch; e_ref [n_cfg],
  * f_ref [n_atoms][3], w_ref [n_cfg][9].  Outputs: loss [1], d_xi [m], d_c [S][S][N_mu][N_Q] (each may
- * be NULL).  The force and stress terms are obtained as the derivative of the pair gradients along
+ * be NULL; with both d_xi and d_c NULL only the evaluation and the loss run).  The force and stress terms are obtained as the derivative of the pair gradients along
  * the residual displacements (the mixed second derivative), recomputed rather than stored.
  * Device arrays unless MTP_HOST_MEMORY.  Gradient sums are accumulated in double precision.
  */
@@ -266,6 +269,11 @@ int64_t mtp_launch_count(const mtp_model* model);
  * milliseconds, in that order, and the number of evaluations accumulated. */
 mtp_status mtp_profile(mtp_model* model, int enable);
 mtp_status mtp_profile_read(const mtp_model* model, double* ms, int n, int64_t* calls);
+
+/* Measured FP32 fused-multiply-add throughput of the current device in TFLOP/s (median of `repeats`
+ * timed launches of a kernel of independent FMA chains that fills every SM; instrumentation for the
+ * roofline of the float kernels, no counterpart in the paper).  Synchronous; allocates 4 bytes. */
+mtp_status mtp_fp32_peak(int repeats, double* tflops);
 
 #ifdef __cplusplus
 }

@@ -131,6 +131,7 @@ mtp_status status_from_err(int err) {
     if (err & mtp::kErrSpecies) return MTP_EINVAL;
     if (err & mtp::kErrShift) return MTP_EINVAL;
     if (err & mtp::kErrCellThin) return MTP_EINVAL;
+    if (err & (mtp::kErrNonFinite | mtp::kErrCell)) return MTP_EINVAL;
     if (err & mtp::kErrOverflow) return MTP_EOVERFLOW;
     if (err & mtp::kErrSingular) return MTP_ESINGULAR;
     if (err & mtp::kErrTimeout) return MTP_ETIMEOUT;
@@ -466,6 +467,33 @@ static mtp_status check_batch(mtp_model* M, int K, int n, const int32_t* off, co
     return MTP_OK;
 }
 
+// Checks of host-memory inputs before anything is copied: CSR offsets, finite positions, finite
+// cells of non-zero volume (the test of the neighbour build's cell kernel), species in [0, S).
+// Device-memory inputs get the same checks inside the first kernels of the neighbour build.
+static mtp_status check_host_inputs(const mtp_model* M, int K, int n, const int32_t* off, const double* pos,
+                                    const int32_t* types, const double* cells) {
+    if (off[0] != 0 || off[K] != n) return MTP_EINVAL;
+    for (int k = 0; k < K; ++k)
+        if (off[k + 1] < off[k]) return MTP_EINVAL;
+    for (size_t q = 0; q < 3 * (size_t)n; ++q)
+        if (!std::isfinite(pos[q])) return MTP_EINVAL;
+    if (types)
+        for (int i = 0; i < n; ++i)
+            if (types[i] < 0 || types[i] >= M->S) return MTP_EINVAL;
+    for (int k = 0; k < K; ++k) {
+        const double* H = cells + 9 * (size_t)k;
+        for (int q = 0; q < 9; ++q)
+            if (!std::isfinite(H[q])) return MTP_EINVAL;
+        const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                           H[2] * (H[3] * H[7] - H[4] * H[6]);
+        const double l0 = std::sqrt(H[0] * H[0] + H[1] * H[1] + H[2] * H[2]);
+        const double l1 = std::sqrt(H[3] * H[3] + H[4] * H[4] + H[5] * H[5]);
+        const double l2 = std::sqrt(H[6] * H[6] + H[7] * H[7] + H[8] * H[8]);
+        if (!(std::fabs(det) > 1e-9 * l0 * l1 * l2)) return MTP_EINVAL;
+    }
+    return MTP_OK;
+}
+
 static mtp_status prepare_neighbors(mtp_model* M, int K, int n, const int* off, const double* pos,
                                     const int* types, const double* cells, double skin, cudaStream_t st) {
     cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
@@ -523,7 +551,7 @@ namespace {
 template <class T>
 mtp_status run_param_grad(mtp_model* M, int K, int n, const int* off, const int* types, const double* e_ref,
                           const double* f_ref, const double* w_ref, double we, double wf, double ws, int scaling,
-                          double* out, cudaStream_t st) {
+                          double* out, bool loss_only, cudaStream_t st) {
     const size_t N = (size_t)n;
     const int nc = (int)M->c.size();
     if (M->g_energy.reserve(8 * (size_t)K + 8) || M->g_forces.reserve(24 * N + 8) ||
@@ -568,6 +596,7 @@ mtp_status run_param_grad(mtp_model* M, int K, int n, const int* off, const int*
     L.w_ref = w_ref;
     L.loss = out;
     L.gew = M->g_ew.as<double>();
+    L.loss_only = loss_only ? 1 : 0;
     int l;
     if constexpr (sizeof(T) == 8)
         l = M->ops->grad_f64(a, L, st, M->n_sm);
@@ -592,6 +621,8 @@ extern "C" mtp_status mtp_param_grad(mtp_model* M, int K, int n, const int32_t* 
     const bool host = flags & MTP_HOST_MEMORY;
     const int nc = (int)M->c.size();
     if (host) {
+        mtp_status v = check_host_inputs(M, K, n, cfg_off, pos, types, cells);
+        if (v) return v;
         bool ok = true;
         cfg_off = stage_in(M->s_off, cfg_off, K + 1, st, &ok);
         pos = stage_in(M->s_pos, pos, 3 * (size_t)n, st, &ok);
@@ -610,10 +641,13 @@ extern "C" mtp_status mtp_param_grad(mtp_model* M, int K, int n, const int32_t* 
     mtp_status s = prepare_neighbors(M, K, n, cfg_off, pos, types, cells, M->skin, st);
     if (s) return s;
     double* out = M->g_out.as<double>();
+    const bool loss_only = !d_xi && !d_c;  // the gradient kernels run only when a gradient is asked for
     if (is_fp64(M))
-        s = run_param_grad<double>(M, K, n, cfg_off, types, e_ref, f_ref, w_ref, w_e, w_f, w_s, scaling, out, st);
+        s = run_param_grad<double>(M, K, n, cfg_off, types, e_ref, f_ref, w_ref, w_e, w_f, w_s, scaling, out,
+                                   loss_only, st);
     else
-        s = run_param_grad<float>(M, K, n, cfg_off, types, e_ref, f_ref, w_ref, w_e, w_f, w_s, scaling, out, st);
+        s = run_param_grad<float>(M, K, n, cfg_off, types, e_ref, f_ref, w_ref, w_e, w_f, w_s, scaling, out,
+                                  loss_only, st);
     if (s) return s;
     const cudaMemcpyKind kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (loss) cudaMemcpyAsync(loss, out, sizeof(double), kind, st);
@@ -643,10 +677,7 @@ mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, co
     double *h_energy = energy, *h_forces = forces, *h_virial = virial, *h_site = site, *h_brows = b_rows,
            *h_batoms = b_atoms;
     if (host) {
-        std::vector<int> offs(cfg_off, cfg_off + K + 1);
-        if (offs[0] != 0 || offs[K] != n) return MTP_EINVAL;
-        for (int k = 0; k < K; ++k)
-            if (offs[k + 1] < offs[k]) return MTP_EINVAL;
+        if ((s = check_host_inputs(M, K, n, cfg_off, pos, types, cells))) return s;
         bool ok = true;
         cfg_off = stage_in(M->s_off, cfg_off, K + 1, st, &ok);
         pos = stage_in(M->s_pos, pos, 3 * (size_t)n, st, &ok);
@@ -822,10 +853,15 @@ mtp_status mtp_select_active_set(mtp_model* M, int n_rows, const double* b_rows,
         B = M->s_rows.as<double>();
     }
     cudaMemsetAsync(M->mv_status.p, 0, sizeof(int), st);
-    M->launches += mtp::launch_maxvol(n, m, B, M->mv_Bs.as<double>(), M->mv_D.as<double>(), M->mv_W.as<double>(),
+    const int lm = mtp::launch_maxvol(n, m, B, M->mv_Bs.as<double>(), M->mv_D.as<double>(), M->mv_W.as<double>(),
                                       M->mv_perm.as<int>(), M->mv_sel.as<int>(), M->d_A.as<double>(),
                                       M->d_Ai.as<double>(), M->mv_C.as<double>(), 1e-3, 100 * m,
                                       M->mv_status.as<int>(), M->mv_swaps.as<int>(), M->mv_gmax.as<double>(), st);
+    if (lm < 0) {
+        M->has_active = false;
+        return MTP_ECUDA;
+    }
+    M->launches += lm;
     int status = 0, swaps = 0;
     double g = 0.0;
     std::vector<int> sel(m);
@@ -865,8 +901,13 @@ mtp_status mtp_set_active_set(mtp_model* M, const double* A) {
         return MTP_ENOMEM;
     if (cudaMemcpy(M->d_A.p, A, sizeof(double) * m * m, cudaMemcpyHostToDevice) != cudaSuccess) return MTP_ECUDA;
     cudaMemset(M->mv_status.p, 0, sizeof(int));
-    M->launches += mtp::launch_invert(m, M->d_A.as<double>(), M->d_Ai.as<double>(), M->mv_W.as<double>(),
+    const int li = mtp::launch_invert(m, M->d_A.as<double>(), M->d_Ai.as<double>(), M->mv_W.as<double>(),
                                       M->mv_status.as<int>(), 0);
+    if (li < 0) {
+        M->has_active = false;
+        return MTP_ECUDA;
+    }
+    M->launches += li;
     int status = 0;
     if (cudaMemcpy(&status, M->mv_status.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
     M->active_rows.assign(m, -1);

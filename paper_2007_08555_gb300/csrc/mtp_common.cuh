@@ -17,7 +17,9 @@ enum : int {
     kErrShift = 4,      // |image shift| beyond the packed range
     kErrCellThin = 8,   // cell thinner than the cutoff allows with the supported image range
     kErrTimeout = 16,   // an iteration limit was reached
-    kErrSingular = 32   // singular matrix in the active-set LU
+    kErrSingular = 32,  // singular matrix in the active-set LU
+    kErrNonFinite = 64, // a position or cell entry is NaN or infinite
+    kErrCell = 128      // a cell with (numerically) zero volume
 };
 
 // Inputs and outputs of one evaluation; every array is device memory.
@@ -95,6 +97,7 @@ struct LossArgs {
     const double* w_ref;
     double* loss;           // [1] accumulated
     double* gew;            // [K]
+    int loss_only;          // 1: residuals and loss only, no gradient kernels
 };
 
 __host__ __device__ inline void loss_scales(int kind, double n, double* se, double* sf, double* ss) {

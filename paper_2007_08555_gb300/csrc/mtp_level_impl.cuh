@@ -1415,7 +1415,7 @@ int grad_all(EvalCtx<T>& a, const LossArgs& L, cudaStream_t st, int n_sm) {
     k_resid_atoms<T><<<min((a.n_atoms + 127) / 128 + 1, n_sm * 8), 128, 0, st>>>(a, L, D);
     k_resid_cfgs<T><<<min((a.n_cfg + 127) / 128 + 1, n_sm * 8), 128, 0, st>>>(L, eps);
     launches += 2;
-    if (a.n_atoms == 0) return launches;
+    if (a.n_atoms == 0 || L.loss_only) return launches;
     switch (a.tpa) {
         case 8: launches += launch_grad_pairs<T, 8>(a, st, n_sm); break;
         case 4: launches += launch_grad_pairs<T, 4>(a, st, n_sm); break;

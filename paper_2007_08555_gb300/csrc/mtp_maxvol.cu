@@ -12,7 +12,8 @@
 //      by the rank-one (Sherman-Morrison) update  C <- C - C[:,j] (C[k,:] - e_j) / C_kj.
 //   A^-1 is recomputed from scratch at the end.
 // k_grade: gamma_r = max_j |(b_r A^-1)_j| for many rows; 64x64 output tiles through shared memory,
-//   the row maxima are combined with an atomic max on the bit pattern (gamma >= 0).
+//   the row maxima are combined with an atomic max on the bit pattern (gamma >= 0); a NaN in a row
+//   of b A^-1 gives gamma = +inf, so a broken configuration reads as extrapolating.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <mutex>
@@ -283,7 +284,12 @@ __global__ void __launch_bounds__(256) k_grade(int n, int m, const T* __restrict
         double mx = 0.0;
 #pragma unroll
         for (int b = 0; b < 4; ++b)
-            if (col0 + tx * 4 + b < m) mx = fmax(mx, fabs((double)acc[a][b]));
+            if (col0 + tx * 4 + b < m) {
+                // a NaN entry counts as an infinite grade (fmax would drop it and report a row
+                // of NaN as interpolating)
+                const double v = fabs((double)acc[a][b]);
+                mx = fmax(mx, v != v ? (double)INFINITY : v);
+            }
         // combine the 16 threads that share this row (consecutive lanes)
         for (int o = 8; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o, 16));
         const int r = row0 + ty * 4 + a;
@@ -299,16 +305,18 @@ __global__ void __launch_bounds__(kMvThreads) k_invert(int m, const double* A, d
 
 }  // namespace
 
+// The launchers return the number of kernels launched, or -1 if the launch itself failed (the
+// error is taken off cudaGetLastError, so the caller reports it instead of reading stale results).
 int launch_invert(int m, const double* A, double* Ai, double* W, int* status, cudaStream_t st) {
     k_invert<<<1, kMvThreads, 0, st>>>(m, A, Ai, W, status);
-    return 1;
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_maxvol(int n, int m, const double* B, double* Bs, double* D, double* W, int* perm, int* sel, double* A,
                   double* Ai, double* C, double tol, int max_iter, int* status, int* swaps, double* gmax,
                   cudaStream_t st) {
     k_maxvol<<<1, kMvThreads, 0, st>>>(n, m, B, Bs, D, W, perm, sel, A, Ai, C, tol, max_iter, status, swaps, gmax);
-    return 1;
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 template <class T>
@@ -393,7 +401,8 @@ extern "C" mtp_status mtp_select_active_set_noalloc(int n_rows, int m, const dou
     double* gmax = reinterpret_cast<double*>(base + (need - 1));
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(status, 0, 2 * sizeof(int), st) != cudaSuccess) return MTP_ECUDA;
-    launch_maxvol(n_rows, m, b_rows, Bs, D, W, perm, sel, A, Ai, C, 1e-3, 100 * m, status, swaps, gmax, st);
+    if (launch_maxvol(n_rows, m, b_rows, Bs, D, W, perm, sel, A, Ai, C, 1e-3, 100 * m, status, swaps, gmax, st) < 0)
+        return MTP_ECUDA;
     int h[2] = {0, 0};
     if (cudaMemcpyAsync(h, status, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MTP_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return MTP_ECUDA;

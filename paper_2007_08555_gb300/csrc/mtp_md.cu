@@ -8,6 +8,7 @@
 // amu; 1 amu Angstrom^2 / fs^2 = 103.6427 eV.
 #include <cuda_runtime.h>
 #include "mtp_internal.h"
+#include "mtp_common.cuh"
 
 namespace mtp {
 
@@ -17,12 +18,13 @@ constexpr double kMvv2eV = 103.642696;  // amu Angstrom^2 fs^-2 in eV
 
 template <class T>
 __global__ void k_update_pairs(int n, const int* count, const int* jz, const T* r0x, const T* r0y, const T* r0z,
-                               const double* x, const double* x0, T* rx, T* ry, T* rz) {
+                               const double* x, const double* x0, T* rx, T* ry, T* rz, int* err) {
     const size_t N = (size_t)n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double ui0 = x[3 * (size_t)i] - x0[3 * (size_t)i];
         const double ui1 = x[3 * (size_t)i + 1] - x0[3 * (size_t)i + 1];
         const double ui2 = x[3 * (size_t)i + 2] - x0[3 * (size_t)i + 2];
+        if (!(isfinite(ui0) && isfinite(ui1) && isfinite(ui2))) atomicOr(err, kErrNonFinite);
         const T fi0 = (T)ui0, fi1 = (T)ui1, fi2 = (T)ui2;
         const int cnt = count[i];
         for (int p = 0; p < cnt; ++p) {
@@ -62,7 +64,7 @@ __global__ void k_drift(int n, double* x, const double* v, const double* x0, dou
             const double u = xn - x0[3 * (size_t)i + c];
             d2 += u * u;
         }
-        far = far || d2 > lim2;
+        far = far || !(d2 <= lim2);  // a NaN displacement forces a rebuild, whose checks report it
     }
     if (__syncthreads_or(far) && threadIdx.x == 0) atomicOr(flag, 1);
 }
@@ -97,11 +99,11 @@ int launch_update_pairs(const NbrState& nb, const double* x, cudaStream_t st, in
     if (nb.fp64)
         k_update_pairs<double><<<grid_for(n, 128, n_sm), 128, 0, st>>>(
             n, nb.count.as<int>(), nb.jz.as<int>(), nb.rx.as<double>(), nb.ry.as<double>(), nb.rz.as<double>(), x,
-            nb.x0.as<double>(), nb.cx.as<double>(), nb.cy.as<double>(), nb.cz.as<double>());
+            nb.x0.as<double>(), nb.cx.as<double>(), nb.cy.as<double>(), nb.cz.as<double>(), nb.err.as<int>());
     else
         k_update_pairs<float><<<grid_for(n, 128, n_sm), 128, 0, st>>>(
             n, nb.count.as<int>(), nb.jz.as<int>(), nb.rx.as<float>(), nb.ry.as<float>(), nb.rz.as<float>(), x,
-            nb.x0.as<double>(), nb.cx.as<float>(), nb.cy.as<float>(), nb.cz.as<float>());
+            nb.x0.as<double>(), nb.cx.as<float>(), nb.cy.as<float>(), nb.cz.as<float>(), nb.err.as<int>());
     return 1;
 }
 

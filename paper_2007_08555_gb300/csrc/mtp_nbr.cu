@@ -49,7 +49,14 @@ __global__ void k_cells(int K, const double* cells, const int* cfg_off, double r
     if (k >= K) return;
     CellDesc D;
     const double* H = cells + 9 * (size_t)k;
-    for (int q = 0; q < 9; ++q) D.H[q] = H[q];
+    bool finite = true;
+    for (int q = 0; q < 9; ++q) {
+        D.H[q] = H[q];
+        finite = finite && isfinite(H[q]);
+    }
+    // input checks: every geometry below stays finite-indexed for any input (a NaN converts to a
+    // zero bin count, clamped to one bin), so bad cells are only reported here
+    if (!finite) atomicOr(err, kErrNonFinite);
     // The inverse cell in double (fractional coordinates of atoms far from the origin need it),
     // with a single reciprocal; the bin geometry below in float: this thread's chain is serial,
     // and a double-precision division or square root costs many float operations here.  Float is
@@ -58,6 +65,9 @@ __global__ void k_cells(int K, const double* cells, const int* cfg_off, double r
     {
         const double a = H[0], b = H[1], c = H[2], e = H[3], f = H[4], g = H[5], h = H[6], ii = H[7], jj = H[8];
         const double det = a * (f * jj - g * ii) - b * (e * jj - g * h) + c * (e * ii - f * h);
+        const double l0 = sqrt(a * a + b * b + c * c), l1 = sqrt(e * e + f * f + g * g),
+                     l2 = sqrt(h * h + ii * ii + jj * jj);
+        if (finite && !(fabs(det) > 1e-9 * l0 * l1 * l2)) atomicOr(err, kErrCell);  // flat or degenerate cell
         const double id = 1.0 / det;
         D.Hi[0] = (f * jj - g * ii) * id; D.Hi[1] = (c * ii - b * jj) * id; D.Hi[2] = (b * g - c * f) * id;
         D.Hi[3] = (g * h - e * jj) * id; D.Hi[4] = (a * jj - c * h) * id; D.Hi[5] = (c * e - a * g) * id;
@@ -122,6 +132,9 @@ __global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, i
     if (types[i] < 0 || types[i] >= S) atomicOr(err, kErrSpecies);
     const CellDesc& D = d[k];
     const double x[3] = {pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2]};
+    // a non-finite position is reported; its bin and wrap below are clamped, and its pairs fail
+    // every distance test, so no index is derived from it
+    if (!(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]))) atomicOr(err, kErrNonFinite);
     int w[3], b[3];
     double frac[3];
     for (int q = 0; q < 3; ++q) {

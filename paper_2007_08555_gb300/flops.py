@@ -56,8 +56,16 @@ def per_evaluation(lev_max: int, n_radial: int, n_atoms: int, n_pairs: int):
             "pairgrad": c["pair_adjoint"] * n_pairs, "gather": c["pair_gather"] * n_pairs}
 
 
-def fp32_peak_tflops(n_sm: int = 152, clock_mhz: float = 2070.0) -> float:
-    """FP32 FMA peak: 128 lanes per SM, 2 flops per FMA, at the given SM clock."""
+def neighbor_bytes(n_atoms: int, n_pairs: int, real_bytes: int = 4) -> int:
+    """Algorithmic DRAM bytes of one neighbour search (Eq. 1): per atom its position (3 doubles) and
+    species read and its neighbour count written (32 B); per pair the neighbour index and r_ij in the
+    path's precision written (4 + 3 real_bytes: 16 B on the float path)."""
+    return 32 * n_atoms + (4 + 3 * real_bytes) * n_pairs
+
+
+def fp32_peak_tflops(n_sm: int, clock_mhz: float) -> float:
+    """FP32 FMA peak from unit counts: 128 lanes per SM, 2 flops per FMA, at the given SM clock
+    (context for the measured figure of mtp_fp32_peak)."""
     return n_sm * 128 * 2 * clock_mhz * 1e6 / 1e12
 
 

@@ -75,6 +75,7 @@ _SIGS = {
     "mtp_profile_read": (_I, [_P, _P, _I, ctypes.POINTER(_L)]),
     "mtp_save": (_I, [_P, ctypes.c_char_p]),
     "mtp_load": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
+    "mtp_fp32_peak": (_I, [_I, ctypes.POINTER(_D)]),
 }
 
 PHASES = ("neighbors", "moments", "contract", "pairgrad", "gather")
@@ -221,6 +222,13 @@ def mtp_select_active_set_noalloc(n_rows, m, b_rows, selected, a_inv=None, strea
     _check(load().mtp_select_active_set_noalloc(int(n_rows), int(m), _ptr(b_rows), _ptr(selected), _ptr(a_inv),
                                                 ctypes.byref(sw), _stream(stream)), "mtp_select_active_set_noalloc")
     return int(sw.value)
+
+
+def mtp_fp32_peak(repeats=9):
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(load().mtp_fp32_peak(int(repeats), ctypes.byref(t)), "mtp_fp32_peak")
+    return float(t.value)
 
 
 def mtp_save(h, path):
@@ -383,6 +391,17 @@ class Model:
                        weights[0], weights[1], weights[2], kind, loss, dxi, dc)
         return loss, dxi, dc
 
+    def loss(self, pos, types, cells, cfg_off, e_ref, f_ref, w_ref, weights=(1.0, 0.01, 0.001),
+             scaling="vibrations"):
+        """The training loss alone (Sec. 2.2): the evaluation and the residuals, no gradient kernels."""
+        import torch
+
+        kind = {"molecules": 0, "structures": 1, "vibrations": 2}[scaling] if isinstance(scaling, str) else scaling
+        loss = torch.empty(1, dtype=torch.float64, device=pos.device)
+        mtp_param_grad(self.h, cells.shape[0], pos.shape[0], cfg_off, pos, types, cells, e_ref, f_ref, w_ref,
+                       weights[0], weights[1], weights[2], kind, loss, None, None)
+        return loss
+
     def set_skin(self, skin):
         mtp_set_skin(self.h, skin)
 
@@ -434,3 +453,50 @@ class Model:
         r = torch.empty((max(P, 1), 3), dtype=torch.float64, device=pos.device)
         mtp_neighbors(self.h, K, N, cfg_off, pos, cells, skin, counts, j, s, r, P)
         return counts, j[:P], s[:P], r[:P]
+
+
+# -- autograd ---------------------------------------------------------------------------------------
+def _training_loss_function():
+    import torch
+
+    class TrainingLoss(torch.autograd.Function):
+        """L(xi, c) of Sec. 2.2 (Eqs. 7, 11, 12) as a differentiable function of the parameters.
+
+        forward: the library's evaluation and loss (mtp_param_grad without gradient outputs).
+        backward: mtp_param_grad again, which re-evaluates energies, forces and virials (nothing of
+        the forward pass is stored) and returns dL/dxi and dL/dc from the library's adjoint kernels,
+        including the mixed second derivative of the force and stress terms.  xi [m] and c
+        [S, S, N_mu, N_Q] are float64 tensors; they are copied into the model before each call."""
+
+        @staticmethod
+        def forward(ctx, xi, c, model, batch, refs, weights, scaling):
+            model.set_params(xi.detach().double().cpu().numpy(), c.detach().double().cpu().numpy())
+            loss = model.loss(*batch, *refs, weights=weights, scaling=scaling)
+            ctx.save_for_backward(xi, c)
+            ctx.model, ctx.batch, ctx.refs, ctx.weights, ctx.scaling = model, batch, refs, weights, scaling
+            return loss[0].to(xi.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            xi, c = ctx.saved_tensors
+            model = ctx.model
+            model.set_params(xi.detach().double().cpu().numpy(), c.detach().double().cpu().numpy())
+            _, dxi, dc = model.param_grad(*ctx.batch, *ctx.refs, weights=ctx.weights, scaling=ctx.scaling)
+            g = grad_out.to(dxi.device)
+            return (g * dxi).to(xi.device), (g * dc).to(c.device), None, None, None, None, None
+
+    return TrainingLoss
+
+
+_TrainingLoss = None
+
+
+def training_loss(model, xi, c, pos, types, cells, cfg_off, e_ref, f_ref, w_ref, weights=(1.0, 0.01, 0.001),
+                  scaling="vibrations"):
+    """Differentiable training loss: torch.autograd sees L(xi, c); backward runs the library's adjoint.
+    Batch tensors as for Model.eval_batch, e_ref [K], f_ref [N, 3], w_ref [K, 9] (float64, device)."""
+    global _TrainingLoss
+    if _TrainingLoss is None:
+        _TrainingLoss = _training_loss_function()
+    return _TrainingLoss.apply(xi, c, model, (pos, types, cells, cfg_off), (e_ref, f_ref, w_ref), tuple(weights),
+                               scaling)

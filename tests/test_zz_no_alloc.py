@@ -42,3 +42,26 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(gpu_lib):
     with pytest.raises(mtp.MTPError) as ei:
         mtp.mtp_select_active_set_noalloc(6000, m, B, sel)
     assert ei.value.code == 1
+
+
+def _scratch_doubles(n, m):
+    """Doubles of the fixed scratch array used for n rows of m columns (the layout stated in mtp.h)."""
+    nm, mm = n * m, m * m
+    return 2 * nm + max(nm, 2 * mm) + 2 * mm + 3 * m + n + (n + m + 3) // 2 + 1
+
+
+def test_noalloc_accepts_the_largest_size_that_fits_and_rejects_one_more_row(gpu_lib):
+    m = 116
+    n = m
+    while _scratch_doubles(n + 1, m) <= 1 << 19:
+        n += 1
+    assert n == 1421  # the figure stated in mtp.h
+    model = mtp.Model.from_params(synth.random_params(16, 1, 4, 2.0, 5.0, m, 0))
+    B = torch.as_tensor(_matrix(n + 1, m, 21), dtype=torch.float64, device="cuda")
+    sel = torch.full((m,), -1, dtype=torch.int32, device="cuda")
+    swaps = mtp.mtp_select_active_set_noalloc(n, m, B[:n].contiguous(), sel)
+    sel_ref, swaps_ref, _ = model.select_active_set(B[:n].contiguous())
+    assert sel.cpu().tolist() == sel_ref.cpu().tolist() and swaps == swaps_ref
+    with pytest.raises(mtp.MTPError) as ei:
+        mtp.mtp_select_active_set_noalloc(n + 1, m, B, sel)
+    assert ei.value.code == 1
