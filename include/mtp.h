@@ -48,9 +48,12 @@ typedef enum {
 } mtp_status;
 
 typedef enum {
-    MTP_FP64 = 0,  /* every step in double precision */
-    MTP_FP32 = 1   /* pair geometry, radial basis, moments, contractions and adjoint in float;
-                      per-configuration energy and virial sums in double */
+    MTP_FP64 = 0,    /* every step in double precision */
+    MTP_FP32 = 1,    /* pair geometry, radial basis, moments, contractions and adjoint in float;
+                        per-configuration energy and virial sums in double */
+    MTP_FP32_TC = 2  /* MTP_FP32, and the grade product b A^-1 (Sec. 2.3) on the tensor cores: BF16
+                        digit products accumulated in FP32 (exact group sums), combined exactly;
+                        error comparable to a double-precision product (see mtp_grade) */
 } mtp_precision;
 
 enum {
@@ -74,7 +77,7 @@ const char* mtp_status_str(mtp_status s);
  *               mtp_level_table(), or NULL for zeros.
  *   c           host array [S][S][N_mu][N_Q] of the radial coefficients c_{mu,z_i,z_j}^{(b)} of
  *               Eq. 3, first index z_i (the central atom), or NULL for zeros.
- *   prec        MTP_FP64 or MTP_FP32.
+ *   prec        MTP_FP64, MTP_FP32 or MTP_FP32_TC.
  *   out         receives the model; release it with mtp_destroy().
  * Uses the current CUDA device.  Returns MTP_EINVAL for out-of-range arguments.
  */
@@ -223,7 +226,13 @@ mtp_status mtp_save(const mtp_model* model, const char* path);
 mtp_status mtp_load(const char* path, mtp_model** out);
 
 /* Extrapolation grade of arbitrary rows (Sec. 2.3): gamma[r] = max_j |(b_r A^-1)_j| for b_rows
- * [n_rows][m] (double), in double precision.  Device arrays unless MTP_HOST_MEMORY. */
+ * [n_rows][m] (double).  Device arrays unless MTP_HOST_MEMORY.  MTP_FP64 and MTP_FP32 models form
+ * the product in double precision; MTP_FP32_TC models on the tensor cores: with column scaling
+ * D = 2^e (A D columns of maximum in [1/2, 1)), rows of b D and columns of G = (A D)^-1 rounded to
+ * 56-bit grids relative to their largest entries 2^E_r and 2^F_j, split into 8 base-128 BF16
+ * digits, digit products summed exactly in FP32 and combined exactly in integers; the error of
+ * c_rj is about 1e-15 2^(E_r + F_j) and gamma is rounded to float (2^-24 relative).  A row holding
+ * NaN or inf has gamma = +inf in every precision.  m <= 480 for MTP_FP32_TC. */
 mtp_status mtp_grade(mtp_model* model, int n_rows, const double* b_rows, double* gamma, int flags, void* stream);
 
 /*

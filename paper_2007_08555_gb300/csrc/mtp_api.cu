@@ -68,6 +68,9 @@ struct mtp_model {
     int64_t launches = 0;
     // active set (Sec. 2.3): rows of the last selection, A and A^-1 in double precision
     bool has_active = false;
+    // tensor-core grades (MTP_FP32_TC): digits of (A D)^-1, prepared once per active set
+    DevBuf tc_digits, tc_ecol, tc_scale;
+    bool tc_ready = false;
     std::vector<int> active_rows;
     DevBuf g_energy, g_forces, g_virial, g_D, g_eps, g_ew, g_momt, g_adjmt, g_out, g_refs;
     DevBuf d_A, d_Ai, mv_Bs, mv_D, mv_W, mv_perm, mv_sel, mv_C, mv_status, mv_swaps, mv_gmax, s_rows, s_gamma, g_brows, g_batoms;
@@ -125,6 +128,33 @@ mtp_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return MTP_OK;
     if (e == cudaErrorMemoryAllocation) return MTP_ENOMEM;
     return MTP_ECUDA;
+}
+
+// Grades of n rows against the installed active set: tensor cores for MTP_FP32_TC (the digits of
+// (A D)^-1 are prepared on first use after the active set changed), double precision otherwise.
+// Returns the number of launches, or -1.
+int launch_grades(mtp_model* M, int n, const double* B, double* gamma, cudaStream_t st) {
+    auto* g = reinterpret_cast<unsigned long long*>(gamma);
+    if (M->prec != MTP_FP32_TC) return mtp::launch_grade<double>(n, M->m, B, M->m, M->d_Ai.as<double>(), g, st);
+    int l = 0;
+    if (!M->tc_ready) {
+        const int mp = ((M->m + 63) / 64) * 64;
+        if (M->tc_digits.reserve(mtp::grade_tc_digit_bytes(M->m)) || M->tc_ecol.reserve(sizeof(int) * mp) ||
+            M->tc_scale.reserve(sizeof(float) * mp))
+            return -1;
+        const int p = mtp::launch_grade_tc_prep(M->m, M->d_A.as<double>(), M->d_Ai.as<double>(), M->tc_digits.p,
+                                                M->tc_ecol.as<int>(), M->tc_scale.as<float>(), st);
+        if (p < 0) return -1;
+        l += p;
+        M->tc_ready = true;
+    }
+    if (!M->nb.err.p) {  // the error word (bounded waits of the kernel)
+        if (M->nb.err.reserve(4) || M->nb.counters.reserve(16)) return -1;
+        if (cudaMemset(M->nb.err.p, 0, M->nb.err.bytes) != cudaSuccess) return -1;
+    }
+    const int k = mtp::launch_grade_tc(n, M->m, B, M->m, M->tc_digits.p, M->tc_ecol.as<int>(), M->tc_scale.as<float>(),
+                                       g, M->nb.err.as<int>(), st, M->n_sm);
+    return k < 0 ? -1 : l + k;
 }
 
 mtp_status status_from_err(int err) {
@@ -317,7 +347,7 @@ mtp_status mtp_create(int lev_max, int n_species, int n_radial, double r_min, do
     lev_max -= lev_max % 2;
     const mtp::LevelOps* ops = mtp::level_ops(lev_max);
     if (!ops || n_species < 1 || n_species > mtp::kMaxSpecies || n_radial < 1 || n_radial > mtp::kMaxRadial ||
-        !(r_min >= 0.0) || !(r_cut > r_min) || (prec != MTP_FP64 && prec != MTP_FP32))
+        !(r_min >= 0.0) || !(r_cut > r_min) || (prec != MTP_FP64 && prec != MTP_FP32 && prec != MTP_FP32_TC))
         return MTP_EINVAL;
     mtp_model* M = new (std::nothrow) mtp_model;
     if (!M) return MTP_ENOMEM;
@@ -377,6 +407,9 @@ void mtp_destroy(mtp_model* M) {
     M->g_dslots.release();
     M->g_dxt.release();
     M->epart.release();
+    M->tc_digits.release();
+    M->tc_ecol.release();
+    M->tc_scale.release();
     if (M->h_flags) cudaFreeHost(M->h_flags);
     if (M->g_exec) cudaGraphExecDestroy(M->g_exec);
     if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
@@ -714,14 +747,25 @@ mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, co
         else
             e = run_eval<float>(M, K, n, cfg_off, types, energy, forces, virial, site, b_rows, b_atoms, q);
         if (e) return e;
-        if (grade_cfg)
-            M->launches += mtp::launch_grade<double>(K, M->m, b_rows, M->m, M->d_Ai.as<double>(),
-                                                     reinterpret_cast<unsigned long long*>(grade_cfg), q);
-        if (grade_atom)
-            M->launches += mtp::launch_grade<double>(n, M->m, b_atoms, M->m, M->d_Ai.as<double>(),
-                                                     reinterpret_cast<unsigned long long*>(grade_atom), q);
+        if (grade_cfg) {
+            const int l = launch_grades(M, K, b_rows, grade_cfg, q);
+            if (l < 0) return MTP_ECUDA;
+            M->launches += l;
+        }
+        if (grade_atom) {
+            const int l = launch_grades(M, n, b_atoms, grade_atom, q);
+            if (l < 0) return MTP_ECUDA;
+            M->launches += l;
+        }
         return MTP_OK;
     };
+    if ((grade_cfg || grade_atom) && M->prec == MTP_FP32_TC && !M->tc_ready) {
+        // digits of (A D)^-1 once per active set, outside any captured graph
+        const int l = launch_grades(M, 0, nullptr, nullptr, st);
+        if (l < 0) return MTP_ECUDA;
+        M->launches += l;
+        M->g_sig.clear();
+    }
     // Repeated identical device-memory calls replay a CUDA graph of the whole evaluation: the first
     // call runs eagerly (sizing every buffer), the second identical call captures, later ones replay.
     std::vector<uintptr_t> sig;
@@ -881,6 +925,7 @@ mtp_status mtp_select_active_set(mtp_model* M, int n_rows, const double* b_rows,
     }
     M->active_rows = sel;
     M->has_active = true;
+    M->tc_ready = false;
     if (n_swaps) *n_swaps = swaps;
     if (max_grade) *max_grade = g;
     if (selected) {
@@ -912,6 +957,7 @@ mtp_status mtp_set_active_set(mtp_model* M, const double* A) {
     if (cudaMemcpy(&status, M->mv_status.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
     M->active_rows.assign(m, -1);
     M->has_active = !(status & mtp::kErrSingular);
+    M->tc_ready = false;
     return M->has_active ? MTP_OK : MTP_ESINGULAR;
 }
 
@@ -1001,6 +1047,8 @@ bool parse_model_file(const char* path, ModelFile& mf) {
         mf.prec = MTP_FP64;
     else if (w == "fp32")
         mf.prec = MTP_FP32;
+    else if (w == "fp32_tc")
+        mf.prec = MTP_FP32_TC;
     else
         return false;
     if (!t.key("skin") || !t.real(mf.skin) || !(mf.skin >= 0.0) || mf.skin > 10.0) return false;
@@ -1057,7 +1105,8 @@ mtp_status mtp_save(const mtp_model* M, const char* path) {
     std::fprintf(f, "%s %d\n", kFileMagic, kFileVersion);
     std::fprintf(f, "lev_max %d\nn_species %d\nn_radial %d\n", M->L, M->S, M->NQ);
     std::fprintf(f, "r_min %.17g\nr_cut %.17g\n", M->rmin, M->rcut);
-    std::fprintf(f, "precision %s\nskin %.17g\n", M->prec == MTP_FP64 ? "fp64" : "fp32", M->skin);
+    std::fprintf(f, "precision %s\nskin %.17g\n",
+                 M->prec == MTP_FP64 ? "fp64" : (M->prec == MTP_FP32 ? "fp32" : "fp32_tc"), M->skin);
     std::fprintf(f, "neighbor_capacity %d\nthreads_per_atom %d %d\n", M->cap, M->tpa_moments, M->tpa_pairs);
     write_reals(f, "xi", M->xi.data(), M->xi.size());
     write_reals(f, "c", M->c.data(), M->c.size());
@@ -1095,6 +1144,7 @@ mtp_status mtp_load(const char* path, mtp_model** out) {
         } else {
             M->active_rows = mf.rows;
             M->has_active = true;
+            M->tc_ready = false;
         }
     }
     if (st) {
@@ -1120,12 +1170,13 @@ mtp_status mtp_grade(mtp_model* M, int n_rows, const double* b_rows, double* gam
         B = M->s_rows.as<double>();
         g = M->s_gamma.as<double>();
     }
-    M->launches += mtp::launch_grade<double>(n_rows, m, B, m, M->d_Ai.as<double>(),
-                                             reinterpret_cast<unsigned long long*>(g), st);
+    const int l = launch_grades(M, n_rows, B, g, st);
+    if (l < 0) return MTP_ECUDA;
+    M->launches += l;
     if (flags & MTP_HOST_MEMORY)
         cudaMemcpyAsync(gamma, g, sizeof(double) * n_rows, cudaMemcpyDeviceToHost, st);
     if (flags & MTP_ASYNC) return cuda_status(cudaGetLastError());
-    return cuda_status(cudaStreamSynchronize(st));
+    return M->prec == MTP_FP32_TC ? finish(M, st) : cuda_status(cudaStreamSynchronize(st));
 }
 
 mtp_status mtp_md_run(mtp_model* M, int n, double* pos, double* vel, const int32_t* types, const double* cell,

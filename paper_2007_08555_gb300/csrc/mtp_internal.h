@@ -74,6 +74,14 @@ int launch_invert(int m, const double* A, double* Ai, double* W, int* status, cu
 template <class T>
 int launch_grade(int n, int m, const T* B, int ldb, const T* Ai, unsigned long long* gbits, cudaStream_t st);
 
+// Tensor-core grade (mtp_grade_tc.cu): digits of (A D)^-1 prepared once per active set (m <= 480),
+// then gamma of n rows (gbits cleared by the launcher); return launches or -1.
+size_t grade_tc_digit_bytes(int m);
+int launch_grade_tc_prep(int m, const double* A, const double* Ai, void* digits, int* ecol, float* cscale,
+                         cudaStream_t st);
+int launch_grade_tc(int n, int m, const double* B, int ldb, const void* digits, const int* ecol, const float* cscale,
+                    unsigned long long* gbits, int* err, cudaStream_t st, int n_sm);
+
 // Molecular dynamics helpers (mtp_md.cu).  The refreshed r_ij go to nb.cx/cy/cz.
 int launch_update_pairs(const NbrState& nb, const double* x, cudaStream_t st, int n_sm);
 int launch_kick(int n, int S, double* v, const double* F, const int* types, const double* masses, double half_dt,

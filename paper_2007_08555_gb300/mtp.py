@@ -19,7 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libmtp.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "mtp.h")
 
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_TC = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_tc": FP32_TC}
 HOST_MEMORY, ASYNC, REUSE_NEIGHBORS = 1, 2, 4
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EOVERFLOW", 5: "ESINGULAR", 6: "ETIMEOUT",
           7: "ENOACTIVESET", 8: "EUNSUPPORTED"}
@@ -275,7 +276,7 @@ class Model:
     """One potential on the current CUDA device (theta = {xi, c}, Sec. 2.1)."""
 
     def __init__(self, lev_max, n_species, n_radial, r_min, r_cut, xi=None, c=None, precision="fp64"):
-        prec = {"fp64": FP64, "fp32": FP32}[precision] if isinstance(precision, str) else int(precision)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.precision = prec
         self.n_species = int(n_species)
         self.n_radial = int(n_radial)
@@ -310,7 +311,7 @@ class Model:
                     break
         self.n_species = int(head["n_species"])
         self.n_radial = int(head["n_radial"])
-        self.precision = FP64 if head["precision"] == "fp64" else FP32
+        self.precision = PRECISIONS[head["precision"]]
         return self
 
     def save(self, path):

@@ -47,17 +47,19 @@ def test_gradcheck_double_precision(gpu_lib):
     xi = dev(p0.xi).requires_grad_(True)
     c = dev(p0.c).requires_grad_(True)
     fn = lambda x, cc: mtp.training_loss(model, x, cc, *batch, e_ref, f_ref, w_ref)
-    assert torch.autograd.gradcheck(fn, (xi, c), eps=1e-6, atol=1e-7, rtol=1e-5)
+    # dL/dc is summed with double-precision atomics: repeated backward passes agree to rounding only
+    assert torch.autograd.gradcheck(fn, (xi, c), eps=1e-6, atol=1e-7, rtol=1e-5, nondet_tol=1e-9)
     loss = fn(xi, c)
     loss.backward()
     _, gxi, gc = model.param_grad(*batch, e_ref, f_ref, w_ref)
-    np.testing.assert_array_equal(xi.grad.cpu().numpy(), gxi.cpu().numpy())
-    np.testing.assert_array_equal(c.grad.cpu().numpy(), gc.cpu().numpy())
+    np.testing.assert_allclose(xi.grad.cpu().numpy(), gxi.cpu().numpy(), rtol=1e-12)
+    np.testing.assert_allclose(c.grad.cpu().numpy(), gc.cpu().numpy(), rtol=1e-12,
+                               atol=1e-14 * np.abs(gc.cpu().numpy()).max())
 
 
 def test_float_gradient_through_autograd_matches_oracle_entrywise(gpu_lib):
-    pstar, p0, b, cells = make_grad_lev20.workload()
-    cells_g, _, grad_o, scale_o = make_grad_lev20.read()
+    pstar, p0, b, cells = make_grad_lev20.workload("smooth")  # within float range (see test_gpu_full_size)
+    cells_g, _, grad_o, scale_o = make_grad_lev20.read("smooth")
     assert cells_g.tolist() == cells.tolist()
     sub = synth.pack([b.config(int(k)) for k in cells])
     e_ref, f_ref, w_ref = _refs(oracle.Potential(pstar), sub)

@@ -4,9 +4,11 @@
   every cell against the oracle at the FP64 and FP32 bars; b rows; the active set chosen by MaxVol
   over the first 2m cells equals the oracle's; the grade of every cell (Sec. 2.3) within the
   first-order bound that the accuracy of its inputs allows (below).
-* the lev_max-20 training loss (Sec. 2.2, Eq. 12) on the stated recipe (R_min 2, c ~ N(0, 0.1),
-  scaled xi): the full 820-entry gradient on four cells against the oracle's stored gradient,
-  entry by entry; four random projections of the gradient on all 2048 cells.
+* the lev_max-20 training loss (Sec. 2.2, Eq. 12): the full 820-entry gradient on four cells against
+  the oracle's stored gradient, entry by entry; four random projections of the gradient on all 2048
+  cells.  The double path on the stated recipe (R_min 2, c ~ N(0, 0.1), scaled xi) and on the smooth
+  one (R_min 1, c damped by 0.5^b); the float path on the smooth one, since on the stated recipe the
+  gradient leaves the float range (1e57 in double precision over the 2048 cells).
 * the 1,048,576-atom ternary fcc cell at lev_max 20 on the stated recipe: site energies, basis rows
   and forces of 256 sampled atoms against the oracle's sampled evaluation; E = sum of site
   energies; forces sum to zero.
@@ -70,16 +72,18 @@ def batch4096():
     pot = oracle.Potential(p)
     E, W, B = np.zeros(b.n_cfg), np.zeros((b.n_cfg, 9)), np.zeros((b.n_cfg, m))
     F = np.zeros((b.n_atoms, 3))
+    sabs = np.zeros(b.n_cfg)  # sum of |site energies|: the size of the terms each E sums
     for k in range(b.n_cfg):
         r = pot.eval(b.config(k), want_b=True)
         a0, a1 = b.cfg_off[k], b.cfg_off[k + 1]
         E[k], W[k], B[k], F[a0:a1] = r["energy"], r["virial"].reshape(9), r["b_atoms"].sum(0), r["forces"]
-    return b, p, m, E, F, W, B
+        sabs[k] = np.abs(r["site"]).sum()
+    return b, p, m, E, F, W, B, sabs
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_config3_batch4096_lev16(gpu_lib, batch4096, precision):
-    b, p, m, E, F, W, B = batch4096
+    b, p, m, E, F, W, B, sabs = batch4096
     assert b.n_cfg == 4096 and b.n_atoms > 250_000
     pos, types, cells, off = dev(b.pos), dev(b.types, torch.int32), dev(b.cells), dev(b.cfg_off, torch.int32)
     model = mtp.Model.from_params(p, precision)
@@ -88,15 +92,21 @@ def test_config3_batch4096_lev16(gpu_lib, batch4096, precision):
     w, br = out["virial"].cpu().numpy().reshape(-1, 9), out["b_rows"].cpu().numpy()
     tol = TOL[precision]
     n = np.diff(b.cfg_off)
-    assert np.all(np.abs(e - E) / n <= tol["e"] * np.maximum(np.abs(E) / n, 1e-12))
-    bad = []
+    re = np.abs(e - E) / np.maximum(np.abs(E), 1e-300)
+    rf, rw, rb = np.zeros(b.n_cfg), np.zeros(b.n_cfg), np.zeros(b.n_cfg)
     for k in range(b.n_cfg):
         a0, a1 = b.cfg_off[k], b.cfg_off[k + 1]
         rms = np.sqrt(np.mean(F[a0:a1] ** 2))
-        if np.sqrt(np.mean((f[a0:a1] - F[a0:a1]) ** 2)) > tol["f"] * rms or rel(w[k], W[k]) > tol["w"] \
-                or rel(br[k], B[k]) > tol["b"]:
-            bad.append(k)
-    assert not bad, f"{len(bad)} cells outside the bars, first {bad[:5]}"
+        rf[k] = np.sqrt(np.mean((f[a0:a1] - F[a0:a1]) ** 2)) / max(rms, 1e-300)
+        rw[k], rb[k] = rel(w[k], W[k]), rel(br[k], B[k])
+    bad = np.nonzero((re > tol["e"]) | (rf > tol["f"]) | (rw > tol["w"]) | (rb > tol["b"]))[0]
+    rmin = [float(np.linalg.norm(oracle.neighbors(b.config(int(k)).pos, b.config(int(k)).cell, 5.0)[3], axis=1).min())
+            for k in bad[:8]]
+    assert len(bad) == 0, (f"{len(bad)} cells outside the bars; worst rel E {re.max():.2e} F {rf.max():.2e} "
+                           f"W {rw.max():.2e} b {rb.max():.2e}; first: " +
+                           "; ".join(f"cfg {k}: n {n[k]} E/n {E[k] / n[k]:.3e} sum|V|/|E| {sabs[k] / abs(E[k]):.2e} "
+                                     f"relE {re[k]:.2e} relF {rf[k]:.2e} relW {rw[k]:.2e} relb {rb[k]:.2e} "
+                                     f"r_min {rm:.3f}" for k, rm in zip(bad[:8], rmin)))
     # active set over the first 2m cells (the oracle's MaxVol on the oracle's rows)
     sel_o, _, _ = maxvol.maxvol(B[:2 * m])
     A = B[sel_o]
@@ -131,10 +141,12 @@ def _targets(pot, cfgs):
             np.array([r["virial"].reshape(9) for r in refs]))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_config4_gradient_entrywise_four_cells(gpu_lib, precision):
-    pstar, p0, b, cells = make_grad_lev20.workload()
-    cells_g, loss_o, grad_o, scale_o = make_grad_lev20.read()
+# The float path runs on the smooth recipe: on the stated one the lev_max-20 gradient leaves the float
+# range (1e57 over the 2048 cells in double precision), so only the double path is checked there.
+@pytest.mark.parametrize("precision,recipe", [("fp64", "stated"), ("fp64", "smooth"), ("fp32", "smooth")])
+def test_config4_gradient_entrywise_four_cells(gpu_lib, precision, recipe):
+    pstar, p0, b, cells = make_grad_lev20.workload(recipe)
+    cells_g, loss_o, grad_o, scale_o = make_grad_lev20.read(recipe)
     assert cells_g.tolist() == cells.tolist()
     cfgs = [b.config(int(k)) for k in cells]
     sub = synth.pack(cfgs)
@@ -161,9 +173,9 @@ def test_config4_gradient_entrywise_four_cells(gpu_lib, precision):
         assert worst <= 1e-4, worst
 
 
-@pytest.fixture(scope="module")
-def grad2048():
-    pstar, p0, b, _ = make_grad_lev20.workload()
+@pytest.fixture(scope="module", params=["stated", "smooth"])
+def grad2048(request):
+    pstar, p0, b, _ = make_grad_lev20.workload(request.param)
     cfgs = [b.config(k) for k in range(b.n_cfg)]
     refs, e_ref, f_ref, w_ref = _targets(oracle.Potential(pstar), cfgs)
     rng = np.random.default_rng(2048)
@@ -173,14 +185,14 @@ def grad2048():
         vxi, vc = rng.normal(size=p0.xi.shape), rng.normal(size=p0.c.shape)
         L0, dL = oloss.loss_and_directional(pot, cfgs, refs, W8, "vibrations", p0.xi, p0.c, vxi, vc)
         dirs.append((vxi, vc, L0, dL))
-    return p0, b, e_ref, f_ref, w_ref, dirs
+    return request.param, p0, b, e_ref, f_ref, w_ref, dirs
 
 
 def test_config4_gradient_projections_all_2048_cells(gpu_lib, grad2048):
-    p0, b, e_ref, f_ref, w_ref, dirs = grad2048
+    recipe, p0, b, e_ref, f_ref, w_ref, dirs = grad2048
     assert b.n_cfg == 2048
     res = {}
-    for precision in ("fp64", "fp32"):
+    for precision in ("fp64", "fp32") if recipe == "smooth" else ("fp64",):
         model = mtp.Model.from_params(p0, precision)
         res[precision] = [t.cpu().numpy() for t in model.param_grad(*_batch_tensors(b), dev(e_ref), dev(f_ref),
                                                                        dev(w_ref), W8, "vibrations")]
@@ -190,6 +202,8 @@ def test_config4_gradient_projections_all_2048_cells(gpu_lib, grad2048):
         got = float(dxi @ vxi + np.sum(dc * vc))
         size = float(np.abs(dxi) @ np.abs(vxi) + np.sum(np.abs(dc * vc)))
         assert abs(got - dL) <= 1e-8 * size
+        if "fp32" not in res:
+            continue
         # float path: the gradient vector within 1e-4 of its norm (normwise float bar), hence by
         # Cauchy-Schwarz a projection within 1e-4 |g| |v|; |g| from the double path, whose
         # projections match the oracle's above
