@@ -122,6 +122,21 @@ mtp_status mtp_set_skin(mtp_model* model, double skin);
  * rounding whatever the choice (summation order changes).  Other values are MTP_EINVAL. */
 mtp_status mtp_set_threads_per_atom(mtp_model* model, int moments, int pairs);
 
+/*
+ * Autotuner of the batched launch (no counterpart in the paper): times the evaluation (neighbour
+ * search + E, F, W) of this batch for every lanes-per-atom choice of the moment kernel and of the
+ * pair-gradient, gather and loss-gradient kernels ({1, 2, 4, 8} each; median of five graph
+ * replays after three untimed calls) and records the fastest for the size class of the batch:
+ * (lev_max, S, N_Q, precision, floor(log2 n_atoms), SM count), shared by every model of the process.
+ * Models whose mtp_set_threads_per_atom() setting is 0 (the default) use the recorded choice for
+ * batches of that class, and the built-in heuristic for others.  Device arrays (batch layout of
+ * mtp_eval_batch); best_moments, best_pairs and times_ms ([16] in ms, index 4 * log2(moments) +
+ * log2(pairs)) are host pointers and may be NULL.  Synchronous; the model's own setting is kept.
+ */
+mtp_status mtp_autotune(mtp_model* model, int n_cfg, int n_atoms, const int32_t* cfg_off, const double* pos,
+                        const int32_t* types, const double* cells, int* best_moments, int* best_pairs,
+                        double* times_ms, void* stream);
+
 /* Capacity of the per-atom neighbour list (default 128).  MTP_EOVERFLOW reports the largest
  * count seen through *max_seen of mtp_last_neighbor_max(). */
 mtp_status mtp_set_neighbor_capacity(mtp_model* model, int cap);

@@ -7,6 +7,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -149,7 +151,7 @@ int launch_grades(mtp_model* M, int n, const double* B, double* gamma, cudaStrea
         M->tc_ready = true;
     }
     if (!M->nb.err.p) {  // the error word (bounded waits of the kernel)
-        if (M->nb.err.reserve(4) || M->nb.counters.reserve(16)) return -1;
+        if (M->nb.err.reserve(4) || M->nb.counters.reserve(64)) return -1;
         if (cudaMemset(M->nb.err.p, 0, M->nb.err.bytes) != cudaSuccess) return -1;
     }
     const int k = mtp::launch_grade_tc(n, M->m, B, M->m, M->tc_digits.p, M->tc_ecol.as<int>(), M->tc_scale.as<float>(),
@@ -166,6 +168,23 @@ mtp_status status_from_err(int err) {
     if (err & mtp::kErrSingular) return MTP_ESINGULAR;
     if (err & mtp::kErrTimeout) return MTP_ETIMEOUT;
     return MTP_OK;
+}
+
+// Lanes per atom chosen by mtp_autotune, per (lev_max, S, N_Q, precision, size class = floor(log2 of
+// the atom count), SM count), shared by every model of the process.
+std::mutex g_tune_mutex;
+std::map<std::vector<int>, std::pair<int, int>> g_tune;
+
+std::vector<int> tune_key(const mtp_model* M, int n) {
+    int cls = 0;
+    while (cls < 30 && (2 << cls) <= n) ++cls;
+    return {M->L, M->S, M->NQ, (int)M->prec, cls, M->n_sm};
+}
+
+std::pair<int, int> tuned(const mtp_model* M, int n) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune.find(tune_key(M, n));
+    return it == g_tune.end() ? std::pair<int, int>{0, 0} : it->second;
 }
 
 // Threads per atom: enough threads for the whole GPU (want per SM), as few lanes per atom as that
@@ -228,8 +247,10 @@ mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     a.adj_layers = M->ops->adj_layers;
     a.weights = M->d_weights.as<float>();
     a.n_weights = M->ops->n_weights;
-    a.tpa = M->tpa_pairs ? M->tpa_pairs : choose_tpa(n, M->n_sm, 512);
-    a.tpa_m = M->tpa_moments ? M->tpa_moments : choose_tpa(n, M->n_sm, 128);
+    // explicit setting, else the autotuned choice of this size class, else the heuristic
+    const std::pair<int, int> t = (M->tpa_pairs && M->tpa_moments) ? std::pair<int, int>{0, 0} : tuned(M, n);
+    a.tpa = M->tpa_pairs ? M->tpa_pairs : (t.second ? t.second : choose_tpa(n, M->n_sm, 512));
+    a.tpa_m = M->tpa_moments ? M->tpa_moments : (t.first ? t.first : choose_tpa(n, M->n_sm, 128));
     a.mom = M->mom.as<T>();
     a.adjm = M->adjm.as<T>();
     a.aslots = parts ? M->aslots.as<T>() : nullptr;
@@ -242,6 +263,7 @@ mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     a.forces = forces;
     a.virial = virial;
     a.err = M->nb.err.as<int>();
+    a.queue = M->nb.counters.as<int>() + 4;
     return MTP_OK;
 }
 
@@ -533,7 +555,7 @@ static mtp_status prepare_neighbors(mtp_model* M, int K, int n, const int* off, 
     cudaStreamIsCapturing(st, &cap_status);
     if (cap_status == cudaStreamCaptureStatusNone) M->g_sig.clear();  // scratch may be re-sized: no replay
     if (!M->nb.err.p) {  // the error word starts at zero and is cleared after every read
-        if (M->nb.err.reserve(4) || M->nb.counters.reserve(16)) return MTP_ENOMEM;
+        if (M->nb.err.reserve(4) || M->nb.counters.reserve(64)) return MTP_ENOMEM;
         if (cudaMemset(M->nb.err.p, 0, M->nb.err.bytes) != cudaSuccess) return MTP_ECUDA;
     }
     if (M->profiling) mtp::record_mark(M->ev_nbr[0], st);
@@ -847,6 +869,67 @@ mtp_status mtp_eval(mtp_model* M, int n, const double* pos, const int32_t* types
     }
     return mtp_eval_batch(M, 1, n, off, pos, types, cell, energy, forces, virial, site, nullptr, nullptr, grade_cfg,
                           grade_atom, flags, stream);
+}
+
+mtp_status mtp_autotune(mtp_model* M, int K, int n, const int32_t* cfg_off, const double* pos, const int32_t* types,
+                        const double* cells, int* best_moments, int* best_pairs, double* times_ms, void* stream) {
+    mtp_status s = check_batch(M, K, n, cfg_off, pos, cells);
+    if (s) return s;
+    if (n < 1 || !types) return MTP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (M->g_energy.reserve(8 * (size_t)K + 8) || M->g_forces.reserve(24 * (size_t)n + 8) ||
+        M->g_virial.reserve(72 * (size_t)K + 8))
+        return MTP_ENOMEM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return MTP_ECUDA;
+    }
+    const int saved_m = M->tpa_moments, saved_p = M->tpa_pairs;
+    const int opts[4] = {1, 2, 4, 8};
+    double best = 1e300;
+    int bm = 0, bp = 0;
+    for (int u = 0; u < 16 && !s; ++u) {
+        M->tpa_moments = opts[u / 4];
+        M->tpa_pairs = opts[u % 4];
+        M->g_sig.clear();
+        std::vector<float> ts;
+        // three untimed calls (eager, captured, first replay), then five timed graph replays
+        for (int r = 0; r < 8 && !s; ++r) {
+            if (r >= 3) cudaEventRecord(e0, st);
+            s = mtp_eval_batch(M, K, n, cfg_off, pos, types, cells, M->g_energy.as<double>(), M->g_forces.as<double>(),
+                               M->g_virial.as<double>(), nullptr, nullptr, nullptr, nullptr, nullptr, 0, stream);
+            if (r >= 3) {
+                cudaEventRecord(e1, st);
+                float ms = 0.f;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                    s = MTP_ECUDA;
+                ts.push_back(ms);
+            }
+        }
+        if (s) break;
+        std::sort(ts.begin(), ts.end());
+        const double med = ts[ts.size() / 2];
+        if (times_ms) times_ms[u] = med;
+        if (med < best) {
+            best = med;
+            bm = opts[u / 4];
+            bp = opts[u % 4];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    M->tpa_moments = saved_m;
+    M->tpa_pairs = saved_p;
+    M->g_sig.clear();
+    if (s) return s;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune[tune_key(M, n)] = {bm, bp};
+    }
+    if (best_moments) *best_moments = bm;
+    if (best_pairs) *best_pairs = bp;
+    return MTP_OK;
 }
 
 mtp_status mtp_neighbors(mtp_model* M, int K, int n, const int32_t* cfg_off, const double* pos, const double* cells,

@@ -57,6 +57,7 @@ struct EvalCtx {
     int adj_layers;
     const float* weights;               // [n_weights] op weights
     int n_weights;
+    int* queue;           // [2] work-queue counters of k_moments and k_pairgrad (zero at the start of an evaluation)
     int tpa;              // threads per atom in the pair-gradient, gather and loss-gradient kernels (1, 2, 4 or 8)
     int tpa_m;            // threads per atom in the moments kernel
     T* mom;               // [ceil(n/32)][C][32] moment components (tile layout)

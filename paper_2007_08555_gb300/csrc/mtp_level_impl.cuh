@@ -324,8 +324,16 @@ __global__ void __launch_bounds__(128) k_moments(const EvalCtx<T> a) {
             a.virial[t - a.n_cfg] = 0.0;
         }
     }
-    const int n_groups = ((a.n_atoms + 31) / 32) * 32;  // whole warps stay converged for the shuffles
-    for (int g = gtid; g < n_groups * TPA; g += stride) {
+    // packed-atom work queue: every warp takes the next 32 (atom, lane) units of the batch (atoms of
+    // all configurations in one sequence) until none are left; whole warps stay converged
+    const int total = ((a.n_atoms + 31) / 32) * 32 * TPA;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(a.queue, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= total) break;
+        const int g = base + lane;
         const int i = g / TPA, sub = g % TPA;
         const bool active = i < a.n_atoms;
         int zi = 0, cnt = 0;
@@ -641,10 +649,15 @@ __global__ void __launch_bounds__(128) k_pairgrad(const EvalCtx<T> a) {
     T* cs = reinterpret_cast<T*>(smem_raw);
     T* sadj = reinterpret_cast<T*>(smem_raw + ((coef_bytes(a) + 15) & ~(size_t)15));
     load_c(a, cs);
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int stride = gridDim.x * blockDim.x;
-    const int n_groups = ((a.n_atoms + 31) / 32) * 32;  // whole warps stay converged for __syncwarp
-    for (int g = gtid; g < n_groups * TPA; g += stride) {
+    // the work queue of k_moments (a second counter): whole warps stay converged for __syncwarp
+    const int total = ((a.n_atoms + 31) / 32) * 32 * TPA;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(a.queue + 1, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= total) break;
+        const int g = base + lane;
         const int i = g / TPA, sub = g % TPA;
         const bool active = i < a.n_atoms;
         int zi = 0, cnt = 0;

@@ -96,6 +96,8 @@ int grid_for(int n, int threads, int n_sm) {
 
 int launch_update_pairs(const NbrState& nb, const double* x, cudaStream_t st, int n_sm) {
     const int n = nb.n_atoms;
+    // the evaluation kernels' work queues start at zero (the neighbour build clears them otherwise)
+    cudaMemsetAsync(nb.counters.as<int>() + 4, 0, 2 * sizeof(int), st);
     if (nb.fp64)
         k_update_pairs<double><<<grid_for(n, 128, n_sm), 128, 0, st>>>(
             n, nb.count.as<int>(), nb.jz.as<int>(), nb.rx.as<double>(), nb.ry.as<double>(), nb.rz.as<double>(), x,

@@ -704,7 +704,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
         nb.atom_bin.reserve(N * 4) || nb.atom_wrap.reserve(N * 4) || nb.atom_local.reserve(N * 16) || nb.atom_wp.reserve(N * 32) ||
         nb.bin_count.reserve(bins_max * 4) || nb.bin_start.reserve((bins_max + 1) * 4) ||
         nb.bin_fill.reserve(bins_max * 4) || nb.bin_atoms.reserve(N * 4 + 4) ||
-        nb.counters.reserve(16) ||
+        nb.counters.reserve(64) ||
         nb.err.reserve(4))
         return -1;
     nb.n_atoms = n;
@@ -716,9 +716,9 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     int* bin_count = nb.bin_count.as<int>();
     int* bin_start = nb.bin_start.as<int>();
     // counters: [0] bins handed out to configurations, [1] atoms handed out to bins, [2] largest
-    // neighbour count seen
+    // neighbour count seen, [4] and [5] the work queues of the moments and pair-gradient kernels
     int* counters = nb.counters.as<int>();
-    cudaMemsetAsync(counters, 0, 3 * sizeof(int), st);
+    cudaMemsetAsync(counters, 0, 8 * sizeof(int), st);
     const int total_bins_upper = n + K;  // every configuration has at most max(1, atoms) bins
     {
         const int nz = total_bins_upper + 1;

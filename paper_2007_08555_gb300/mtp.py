@@ -77,6 +77,7 @@ _SIGS = {
     "mtp_save": (_I, [_P, ctypes.c_char_p]),
     "mtp_load": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "mtp_fp32_peak": (_I, [_I, ctypes.POINTER(_D)]),
+    "mtp_autotune": (_I, [_P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _P]),
 }
 
 PHASES = ("neighbors", "moments", "contract", "pairgrad", "gather")
@@ -223,6 +224,15 @@ def mtp_select_active_set_noalloc(n_rows, m, b_rows, selected, a_inv=None, strea
     _check(load().mtp_select_active_set_noalloc(int(n_rows), int(m), _ptr(b_rows), _ptr(selected), _ptr(a_inv),
                                                 ctypes.byref(sw), _stream(stream)), "mtp_select_active_set_noalloc")
     return int(sw.value)
+
+
+def mtp_autotune(h, n_cfg, n_atoms, cfg_off, pos, types, cells, stream=None):
+    """Times every lanes-per-atom choice on this batch; returns (moments, pairs, times_ms [4, 4])."""
+    bm, bp = ctypes.c_int(), ctypes.c_int()
+    t = np.zeros(16)
+    _check(load().mtp_autotune(h, int(n_cfg), int(n_atoms), _ptr(cfg_off), _ptr(pos), _ptr(types), _ptr(cells),
+                               ctypes.byref(bm), ctypes.byref(bp), _ptr(t), _stream(stream)), "mtp_autotune")
+    return int(bm.value), int(bp.value), t.reshape(4, 4)
 
 
 def mtp_fp32_peak(repeats=9):
@@ -405,6 +415,10 @@ class Model:
 
     def set_skin(self, skin):
         mtp_set_skin(self.h, skin)
+
+    def autotune(self, pos, types, cells, cfg_off):
+        """Lanes per atom for batches of this size class (mtp_autotune); returns (moments, pairs, times_ms)."""
+        return mtp_autotune(self.h, cells.shape[0], pos.shape[0], cfg_off, pos, types, cells)
 
     def set_threads_per_atom(self, moments=0, pairs=0):
         mtp_set_threads_per_atom(self.h, moments, pairs)
