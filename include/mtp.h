@@ -213,7 +213,44 @@ mtp_status mtp_select_active_set(mtp_model* model, int n_rows, const double* b_r
 mtp_status mtp_select_active_set_noalloc(int n_rows, int m, const double* b_rows, int32_t* selected, double* a_inv,
                                          int* n_swaps, void* stream);
 
-/* Install an active set given its m x m matrix A (host, row-major; rows = b of the active configurations);
+/*
+ * Active-set update from candidate configurations (Sec. 2.3: the selected, extrapolative
+ * configurations enter the training set where they raise |det A|; at most m of them, however many
+ * were selected).  MaxVol on the stacked matrix [A; cand_rows] (cand_rows [n_cand][m] double, b rows
+ * of the candidates) starting from the current active set (rows 0 .. m-1), with the swap rule,
+ * tolerance and iteration limit of mtp_select_active_set(); the result replaces the model's A and
+ * A^-1.  Outputs (host, each may be NULL): entered [m] the candidate indices now in the active set
+ * (ascending, *n_entered of them), rows [m] the final active set as indices into the stacked matrix
+ * (position j = row j of the new A), n_swaps.  cand_rows is device memory unless MTP_HOST_MEMORY.
+ * Synchronous.  MTP_ENOACTIVESET without an active set; MTP_ESINGULAR / MTP_ETIMEOUT as for
+ * mtp_select_active_set() (the active set is then dropped).
+ */
+mtp_status mtp_select_add(mtp_model* model, int n_cand, const double* cand_rows, int32_t* entered, int* n_entered,
+                          int32_t* rows, int* n_swaps, int flags, void* stream);
+
+/*
+ * Kind of extrapolation grade (Sec. 2.3): 0 (default) the linear criterion, rows b(cfg) of width m;
+ * 1 the nonlinear criterion, where the rows are the Jacobian dE(cfg)/dtheta over every parameter
+ * theta = [xi (m), c (S, S, N_mu, N_Q) in C order], width m + S^2 N_mu N_Q (mtp_grade_width()).
+ * The active set (mtp_select_active_set, mtp_select_add, mtp_set_active_set, mtp_get_active_set,
+ * mtp_grade, model files) then has that width; changing the kind drops the installed active set.
+ * In the nonlinear kind, rows come from mtp_jacobian_rows() and are graded with mtp_grade();
+ * mtp_eval_batch's grades and mtp_md_select return MTP_EUNSUPPORTED.
+ */
+mtp_status mtp_set_grade_kind(mtp_model* model, int nonlinear);
+int mtp_grade_width(const mtp_model* model);
+
+/*
+ * Jacobian rows of the nonlinear criterion (Sec. 2.3) for a batch (layout of mtp_eval_batch, device
+ * arrays): rows [n_cfg][m + S^2 N_mu N_Q] (double, device), row k = [b(cfg_k), dE_k/dc] with
+ * b(cfg_k) = sum_i B(n_i) = dE_k/dxi (Eq. 2) and dE_k/dc from the adjoint kernels of mtp_param_grad,
+ * summed per configuration in double precision.  Flags: MTP_ASYNC.
+ */
+mtp_status mtp_jacobian_rows(mtp_model* model, int n_cfg, int n_atoms, const int32_t* cfg_off, const double* pos,
+                             const int32_t* types, const double* cells, double* rows, int flags, void* stream);
+
+/* Install an active set given its w x w matrix A (host, row-major; rows = b (or Jacobian rows) of the
+ * active configurations; w = mtp_grade_width());
  * A^-1 is computed on the device.  MTP_ESINGULAR if A is singular. */
 mtp_status mtp_set_active_set(mtp_model* model, const double* A);
 
@@ -278,6 +315,45 @@ mtp_status mtp_param_grad(mtp_model* model, int n_cfg, int n_atoms, const int32_
 mtp_status mtp_md_run(mtp_model* model, int n_atoms, double* pos, double* vel, const int32_t* types,
                       const double* cell, const double* masses, double dt, int n_steps, double* e_pot,
                       double* e_kin, int* n_rebuilds, int flags, void* stream);
+
+/*
+ * Velocity-Verlet MD with active selection (Sec. 2.3, the two-threshold scheme): mtp_md_run(), and
+ * the extrapolation grade gamma of the configuration at every step, the starting one included
+ * (gamma = max_j |(b A^-1)_j|, b = sum_i B(n_i), against the installed active set).  A step with
+ * gamma > gamma_select is selected: its positions are copied into the device ring buffer
+ * ring_pos [ring_capacity][n][3] (slot = count mod ring_capacity, so the latest frames are kept)
+ * and its step and grade into the host arrays ring_steps, ring_gamma [ring_capacity].  The run
+ * stops at the first step with gamma >= gamma_break (that step is selected too); pos and vel then
+ * hold that configuration.  n_selected (all selections, including overwritten ones), stop_step
+ * (-1 if the run completed), gammas [n_steps + 1], e_pot and e_kin ([n_steps + 1], filled up to
+ * the last step run) are host pointers and may be NULL.  Requires 0 <= gamma_select < gamma_break
+ * and an active set (MTP_ENOACTIVESET).
+ */
+mtp_status mtp_md_select(mtp_model* model, int n_atoms, double* pos, double* vel, const int32_t* types,
+                         const double* cell, const double* masses, double dt, int n_steps, double gamma_select,
+                         double gamma_break, int ring_capacity, double* ring_pos, int32_t* ring_steps,
+                         double* ring_gamma, int* n_selected, int* stop_step, double* gammas, double* e_pot,
+                         double* e_kin, int* n_rebuilds, int flags, void* stream);
+
+/*
+ * Batched relaxation (the relaxation of candidate structures, Sec. 5: energy minimisation over atomic
+ * positions and, with relax_cell = 1, the lattice vectors; each configuration ends relaxed or at
+ * its first extrapolative configuration).  The paper names no minimiser; this is FIRE (Bitzek et
+ * al. 2006: semi-implicit Euler, unit masses, N_min 5, f_inc 1.1, f_dec 0.5, a_start 0.1, f_a 0.99,
+ * starting step dt, largest dt_max) on the coordinates q = [u, D]: H = H0 D^T, x = u D^T with D the
+ * deformation gradient of the starting cell, forces F D on u and W D^-T / N on D (W the virial).
+ * A configuration is converged when max |F| <= fmax and (relaxing the cell) max |W| / volume <=
+ * smax; it stops when its grade (Sec. 2.3, the installed active set) reaches gamma_break (pass
+ * INFINITY for no grade checks); every configuration, the starting one included, is checked.
+ * Batch layout of mtp_eval_batch, device arrays; pos and cells are overwritten with the final
+ * coordinates; energy [n_cfg] (device, the energy at the final coordinates), steps and status
+ * ([n_cfg], host: 1 converged, 2 stopped by the grade, 3 step limit max_steps, 4 diverged) may be
+ * NULL.  Synchronous.
+ */
+mtp_status mtp_relax_batch(mtp_model* model, int n_cfg, int n_atoms, const int32_t* cfg_off, double* pos,
+                           const int32_t* types, double* cells, int relax_cell, double fmax, double smax,
+                           double gamma_break, int max_steps, double dt, double dt_max, double* energy, int32_t* steps,
+                           int32_t* status, void* stream);
 
 /* Wait for the model's work on `stream` and report errors detected on the device since the last
  * check (MTP_EOVERFLOW, MTP_EINVAL for bad species or shifts). */

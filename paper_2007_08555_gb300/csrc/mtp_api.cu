@@ -70,6 +70,14 @@ struct mtp_model {
     int64_t launches = 0;
     // active set (Sec. 2.3): rows of the last selection, A and A^-1 in double precision
     bool has_active = false;
+    // width of the active set and of graded rows: m (linear, b rows) or m + S^2 N_mu N_Q (nonlinear,
+    // Jacobian rows dE/dtheta)
+    int gw = 0;
+    bool nonlinear = false;
+    DevBuf j_rows;  // per-configuration dE/dc of the Jacobian rows
+    // batched relaxation state
+    DevBuf r_u, r_vu, r_D, r_vD, r_H0, r_H, r_x, r_dt, r_alpha, r_npos, r_status, r_steps, r_E, r_W, r_F, r_gamma,
+        r_efinal;
     // tensor-core grades (MTP_FP32_TC): digits of (A D)^-1, prepared once per active set
     DevBuf tc_digits, tc_ecol, tc_scale;
     bool tc_ready = false;
@@ -137,14 +145,16 @@ mtp_status cuda_status(cudaError_t e) {
 // Returns the number of launches, or -1.
 int launch_grades(mtp_model* M, int n, const double* B, double* gamma, cudaStream_t st) {
     auto* g = reinterpret_cast<unsigned long long*>(gamma);
-    if (M->prec != MTP_FP32_TC) return mtp::launch_grade<double>(n, M->m, B, M->m, M->d_Ai.as<double>(), g, st);
+    const int w = M->gw;
+    if (M->prec != MTP_FP32_TC || w > 480)  // the tensor-core product is exact up to 480 columns
+        return mtp::launch_grade<double>(n, w, B, w, M->d_Ai.as<double>(), g, st);
     int l = 0;
     if (!M->tc_ready) {
-        const int mp = ((M->m + 63) / 64) * 64;
-        if (M->tc_digits.reserve(mtp::grade_tc_digit_bytes(M->m)) || M->tc_ecol.reserve(sizeof(int) * mp) ||
+        const int mp = ((w + 63) / 64) * 64;
+        if (M->tc_digits.reserve(mtp::grade_tc_digit_bytes(w)) || M->tc_ecol.reserve(sizeof(int) * mp) ||
             M->tc_scale.reserve(sizeof(float) * mp))
             return -1;
-        const int p = mtp::launch_grade_tc_prep(M->m, M->d_A.as<double>(), M->d_Ai.as<double>(), M->tc_digits.p,
+        const int p = mtp::launch_grade_tc_prep(w, M->d_A.as<double>(), M->d_Ai.as<double>(), M->tc_digits.p,
                                                 M->tc_ecol.as<int>(), M->tc_scale.as<float>(), st);
         if (p < 0) return -1;
         l += p;
@@ -154,7 +164,7 @@ int launch_grades(mtp_model* M, int n, const double* B, double* gamma, cudaStrea
         if (M->nb.err.reserve(4) || M->nb.counters.reserve(64)) return -1;
         if (cudaMemset(M->nb.err.p, 0, M->nb.err.bytes) != cudaSuccess) return -1;
     }
-    const int k = mtp::launch_grade_tc(n, M->m, B, M->m, M->tc_digits.p, M->tc_ecol.as<int>(), M->tc_scale.as<float>(),
+    const int k = mtp::launch_grade_tc(n, w, B, w, M->tc_digits.p, M->tc_ecol.as<int>(), M->tc_scale.as<float>(),
                                        g, M->nb.err.as<int>(), st, M->n_sm);
     return k < 0 ? -1 : l + k;
 }
@@ -381,6 +391,7 @@ mtp_status mtp_create(int lev_max, int n_species, int n_radial, double r_min, do
     M->prec = prec;
     M->ops = ops;
     M->m = ops->M;
+    M->gw = ops->M;
     M->nmu = ops->NMU;
     M->C = ops->C;
     M->V = ops->V;
@@ -429,6 +440,10 @@ void mtp_destroy(mtp_model* M) {
     M->g_dslots.release();
     M->g_dxt.release();
     M->epart.release();
+    for (DevBuf* b : {&M->r_u, &M->r_vu, &M->r_D, &M->r_vD, &M->r_H0, &M->r_H, &M->r_x, &M->r_dt, &M->r_alpha,
+                      &M->r_npos, &M->r_status, &M->r_steps, &M->r_E, &M->r_W, &M->r_F, &M->r_gamma, &M->r_efinal,
+                      &M->j_rows})
+        b->release();
     M->tc_digits.release();
     M->tc_ecol.release();
     M->tc_scale.release();
@@ -634,7 +649,7 @@ mtp_status run_param_grad(mtp_model* M, int K, int n, const int* off, const int*
     a.dxt = dual_parts ? M->g_dxt.as<double>() : nullptr;
     a.dxi = out + 1;
     a.dc = out + 1 + M->m;
-    mtp::LossArgs L;
+    mtp::LossArgs L{};
     L.n_atoms = n;
     L.n_cfg = K;
     L.scaling = scaling;
@@ -713,9 +728,177 @@ extern "C" mtp_status mtp_param_grad(mtp_model* M, int K, int n, const int32_t* 
 }
 
 namespace {
+
+// Jacobian rows of the nonlinear criterion (Sec. 2.3): row k = [b(cfg_k), dE_k/dc].  The xi part is
+// the b row of the evaluation; the c part comes from the adjoint of the loss gradient with e_k = 1
+// and no force or stress direction (D = 0, eps = 0), so that its c-derivative term is
+// sum over the pairs of configuration k of Q_b(r) P_mu, P_mu = sum_m dV/dM[mu, m] mono_m, summed per
+// configuration.
+template <class T>
+mtp_status run_jacobian(mtp_model* M, int K, int n, const int* off, const int* types, double* rows, cudaStream_t st) {
+    const size_t N = (size_t)n;
+    const int nc = (int)M->c.size();
+    const int m = M->m;
+    if (M->g_energy.reserve(8 * (size_t)K + 8) || M->g_D.reserve(3 * N * sizeof(T) + 8) ||
+        M->g_eps.reserve(9 * (size_t)K * sizeof(T) + 8) || M->g_ew.reserve(8 * (size_t)K + 8) ||
+        M->g_momt.reserve(((N + 31) / 32) * M->C * 32 * sizeof(T)) ||
+        M->g_adjmt.reserve(((N + 31) / 32) * M->C * 32 * sizeof(T)) ||
+        M->g_brows.reserve(sizeof(double) * (size_t)K * m + 8) || M->g_batoms.reserve(sizeof(double) * N * m + 8) ||
+        M->j_rows.reserve(sizeof(double) * (size_t)K * nc + 8) || M->g_out.reserve(sizeof(double) * (1 + m + nc) + 64))
+        return MTP_ENOMEM;
+    const bool dual_parts = sizeof(T) == 4 && M->ops->contract_parts > 0;
+    if (dual_parts && (M->g_dslots.reserve(2 * ((N + 31) / 32) * M->ops->dual_slots * 32 * sizeof(T) + 16) ||
+                       M->g_dxt.reserve(((N + 31) / 32) * m * sizeof(double) + 16)))
+        return MTP_ENOMEM;
+    mtp::EvalCtx<T> a;
+    mtp_status s = run_eval<T>(M, K, n, off, types, M->g_energy.as<double>(), nullptr, nullptr, nullptr,
+                               M->g_brows.as<double>(), M->g_batoms.as<double>(), st, &a);
+    if (s) return s;
+    const std::vector<double> ones(K, 1.0);
+    cudaMemcpyAsync(M->g_ew.p, ones.data(), sizeof(double) * K, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(M->g_D.p, 0, 3 * N * sizeof(T), st);
+    cudaMemsetAsync(M->g_eps.p, 0, 9 * (size_t)K * sizeof(T), st);
+    cudaMemsetAsync(M->j_rows.p, 0, sizeof(double) * (size_t)K * nc, st);
+    double* out = M->g_out.as<double>();  // scratch for the unused batch sums of dL/dxi and dL/dc
+    cudaMemsetAsync(out, 0, sizeof(double) * (1 + m + nc), st);
+    a.gD = M->g_D.as<T>();
+    a.geps = M->g_eps.as<T>();
+    a.gew = M->g_ew.as<double>();
+    a.momt = M->g_momt.as<T>();
+    a.adjmt = M->g_adjmt.as<T>();
+    a.dslots = dual_parts ? M->g_dslots.as<T>() : nullptr;
+    a.dxt = dual_parts ? M->g_dxt.as<double>() : nullptr;
+    a.dxi = out + 1;
+    a.dc = out + 1 + m;
+    a.dc_rows = M->j_rows.as<double>();
+    mtp::LossArgs L{};
+    L.n_atoms = n;
+    L.n_cfg = K;
+    L.cfg_off = off;
+    L.cfg_of = M->nb.cfg_of.as<int>();
+    L.gew = M->g_ew.as<double>();
+    L.jacobian = 1;
+    int l;
+    if constexpr (sizeof(T) == 8)
+        l = M->ops->grad_f64(a, L, st, M->n_sm);
+    else
+        l = M->ops->grad_f32(a, L, st, M->n_sm);
+    if (l < 0) return MTP_EUNSUPPORTED;
+    M->launches += l;
+    // rows = [b (m) | dE/dc (nc)]
+    const size_t w = sizeof(double) * (size_t)(m + nc);
+    cudaMemcpy2DAsync(rows, w, M->g_brows.p, sizeof(double) * m, sizeof(double) * m, K, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpy2DAsync(rows + m, w, M->j_rows.p, sizeof(double) * nc, sizeof(double) * nc, K, cudaMemcpyDeviceToDevice,
+                      st);
+    return cuda_status(cudaGetLastError());
+}
+
 }  // namespace
 
 extern "C" {
+
+mtp_status mtp_relax_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, double* pos, const int32_t* types,
+                           double* cells, int relax_cell, double fmax, double smax, double gamma_break, int max_steps,
+                           double dt, double dt_max, double* energy, int32_t* steps, int32_t* status, void* stream) {
+    mtp_status s = check_batch(M, K, n, cfg_off, pos, cells);
+    if (s) return s;
+    if (n < 1 || !types || !(fmax > 0.0) || !(smax > 0.0) || max_steps < 0 || !(dt > 0.0) || !(dt_max >= dt) ||
+        (relax_cell != 0 && relax_cell != 1) || gamma_break != gamma_break)
+        return MTP_EINVAL;
+    const bool grading = std::isfinite(gamma_break);
+    if (grading && !M->has_active) return MTP_ENOACTIVESET;
+    if (grading && M->nonlinear) return MTP_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N3 = 3 * (size_t)n, K9 = 9 * (size_t)K, Kd = sizeof(double) * (size_t)K;
+    if (M->r_u.reserve(8 * N3) || M->r_vu.reserve(8 * N3) || M->r_x.reserve(8 * N3) || M->r_F.reserve(8 * N3) ||
+        M->r_D.reserve(8 * K9) || M->r_vD.reserve(8 * K9) || M->r_H0.reserve(8 * K9) || M->r_H.reserve(8 * K9) ||
+        M->r_W.reserve(8 * K9) || M->r_dt.reserve(Kd) || M->r_alpha.reserve(Kd) || M->r_E.reserve(Kd) ||
+        M->r_gamma.reserve(Kd) || M->r_efinal.reserve(Kd) || M->r_npos.reserve(4 * (size_t)K) ||
+        M->r_status.reserve(4 * (size_t)K) || M->r_steps.reserve(4 * (size_t)K))
+        return MTP_ENOMEM;
+    mtp::RelaxArgs a;
+    a.off = cfg_off;
+    a.relax_cell = relax_cell;
+    a.max_steps = max_steps;
+    a.fmax = fmax;
+    a.smax = smax;
+    a.gamma_break = gamma_break;
+    a.dt_max = dt_max;
+    a.F = M->r_F.as<double>();
+    a.W = M->r_W.as<double>();
+    a.E = M->r_E.as<double>();
+    a.H = M->r_H.as<double>();
+    a.gamma = grading ? M->r_gamma.as<double>() : nullptr;
+    a.u = M->r_u.as<double>();
+    a.vu = M->r_vu.as<double>();
+    a.D = M->r_D.as<double>();
+    a.vD = M->r_vD.as<double>();
+    a.dt = M->r_dt.as<double>();
+    a.alpha = M->r_alpha.as<double>();
+    a.e_final = M->r_efinal.as<double>();
+    a.npos = M->r_npos.as<int>();
+    a.status = M->r_status.as<int>();
+    a.steps = M->r_steps.as<int>();
+    cudaMemcpyAsync(M->r_H0.p, cells, 8 * K9, cudaMemcpyDeviceToDevice, st);
+    if (mtp::launch_relax_init(a, n, K, pos, dt, st) < 0) return MTP_ECUDA;
+    M->launches += 1;
+    std::vector<int> hs(K);
+    for (int step = 0; step <= max_steps; ++step) {
+        if (mtp::launch_relax_map(n, K, cfg_off, a.u, a.D, M->r_H0.as<double>(), M->r_x.as<double>(),
+                                  M->r_H.as<double>(), st) < 0)
+            return MTP_ECUDA;
+        // the same arguments every iteration: after the first two calls the evaluation is a graph replay
+        s = mtp_eval_batch(M, K, n, cfg_off, M->r_x.as<double>(), types, M->r_H.as<double>(), M->r_E.as<double>(),
+                           M->r_F.as<double>(), M->r_W.as<double>(), nullptr, nullptr, nullptr,
+                           grading ? M->r_gamma.as<double>() : nullptr, nullptr, MTP_ASYNC, stream);
+        if (s) return s;
+        if (mtp::launch_fire(a, K, step, st) < 0) return MTP_ECUDA;
+        M->launches += 2;
+        if (step % 4 == 3 || step == max_steps) {  // every few iterations: stop once every configuration is done
+            cudaMemcpyAsync(hs.data(), a.status, sizeof(int) * K, cudaMemcpyDeviceToHost, st);
+            if ((s = finish(M, st))) return s;
+            if (std::all_of(hs.begin(), hs.end(), [](int v) { return v != mtp::kRelaxRunning; })) break;
+        }
+    }
+    // final coordinates (each configuration frozen at its last state) back into pos and cells
+    if (mtp::launch_relax_map(n, K, cfg_off, a.u, a.D, M->r_H0.as<double>(), pos, cells, st) < 0) return MTP_ECUDA;
+    if (energy) cudaMemcpyAsync(energy, a.e_final, Kd, cudaMemcpyDeviceToDevice, st);
+    std::vector<int> hsteps(K);
+    cudaMemcpyAsync(hs.data(), a.status, sizeof(int) * K, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hsteps.data(), a.steps, sizeof(int) * K, cudaMemcpyDeviceToHost, st);
+    if ((s = finish(M, st))) return s;
+    if (status) std::copy(hs.begin(), hs.end(), status);
+    if (steps) std::copy(hsteps.begin(), hsteps.end(), steps);
+    return MTP_OK;
+}
+
+mtp_status mtp_set_grade_kind(mtp_model* M, int nonlinear) {
+    if (!M || (nonlinear != 0 && nonlinear != 1)) return MTP_EINVAL;
+    M->nonlinear = nonlinear == 1;
+    M->gw = M->m + (M->nonlinear ? (int)M->c.size() : 0);
+    M->has_active = false;  // an active set of the other kind has the wrong width
+    M->tc_ready = false;
+    M->active_rows.clear();
+    M->g_sig.clear();
+    return MTP_OK;
+}
+
+int mtp_grade_width(const mtp_model* M) { return M ? M->gw : 0; }
+
+mtp_status mtp_jacobian_rows(mtp_model* M, int K, int n, const int32_t* cfg_off, const double* pos,
+                             const int32_t* types, const double* cells, double* rows, int flags, void* stream) {
+    mtp_status s = check_batch(M, K, n, cfg_off, pos, cells);
+    if (s) return s;
+    if (n < 1 || !types || !rows) return MTP_EINVAL;
+    if (flags & (MTP_HOST_MEMORY | MTP_REUSE_NEIGHBORS)) return MTP_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = prepare_neighbors(M, K, n, cfg_off, pos, types, cells, M->skin, st))) return s;
+    s = is_fp64(M) ? run_jacobian<double>(M, K, n, cfg_off, types, rows, st)
+                   : run_jacobian<float>(M, K, n, cfg_off, types, rows, st);
+    if (s) return s;
+    if (flags & MTP_ASYNC) return cuda_status(cudaGetLastError());
+    return finish(M, st);
+}
 
 mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, const double* pos,
                           const int32_t* types, const double* cells, double* energy, double* forces, double* virial,
@@ -725,6 +908,7 @@ mtp_status mtp_eval_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, co
     if (s) return s;
     if (n > 0 && !types) return MTP_EINVAL;
     if ((grade_cfg || grade_atom) && !M->has_active) return MTP_ENOACTIVESET;
+    if ((grade_cfg || grade_atom) && M->nonlinear) return MTP_EUNSUPPORTED;  // mtp_jacobian_rows + mtp_grade
     const bool reuse = (flags & MTP_REUSE_NEIGHBORS) && M->nb.has_x0 && M->nb.n_atoms == n && M->nb.n_cfg == K;
     double *h_gcfg = grade_cfg, *h_gatom = grade_atom;
     cudaStream_t st = (cudaStream_t)stream;
@@ -962,10 +1146,10 @@ mtp_status mtp_neighbors(mtp_model* M, int K, int n, const int32_t* cfg_off, con
 
 mtp_status mtp_select_active_set(mtp_model* M, int n_rows, const double* b_rows, int32_t* selected, int* n_swaps,
                                  double* max_grade, int flags, void* stream) {
-    if (!M || !b_rows || n_rows < M->m) return MTP_EINVAL;
+    if (!M || !b_rows || n_rows < M->gw) return MTP_EINVAL;
     M->g_sig.clear();  // A^-1 may move: no replay of an older graph
     cudaStream_t st = (cudaStream_t)stream;
-    const int m = M->m, n = n_rows;
+    const int m = M->gw, n = n_rows;
     const size_t wsz = std::max((size_t)n * m, (size_t)2 * m * m) + 2 * (size_t)m + n + 16;
     if (M->mv_W.reserve(sizeof(double) * wsz) || M->mv_perm.reserve(sizeof(int) * n) ||
         M->mv_sel.reserve(sizeof(int) * m) || M->d_A.reserve(sizeof(double) * m * m) ||
@@ -1020,10 +1204,68 @@ mtp_status mtp_select_active_set(mtp_model* M, int n_rows, const double* b_rows,
     return MTP_OK;
 }
 
+mtp_status mtp_select_add(mtp_model* M, int n_cand, const double* cand_rows, int32_t* entered, int* n_entered,
+                          int32_t* rows, int* n_swaps, int flags, void* stream) {
+    if (!M || n_cand < 0 || (n_cand > 0 && !cand_rows)) return MTP_EINVAL;
+    if (!M->has_active) return MTP_ENOACTIVESET;
+    M->g_sig.clear();  // A^-1 moves: no replay of an older graph
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = M->gw, n = m + n_cand;
+    const size_t wsz = std::max((size_t)n * m, (size_t)2 * m * m) + 2 * (size_t)m + n + 16;
+    if (M->mv_W.reserve(sizeof(double) * wsz) || M->mv_perm.reserve(sizeof(int) * n) ||
+        M->mv_sel.reserve(sizeof(int) * m) || M->mv_C.reserve(sizeof(double) * (size_t)n * m) ||
+        M->mv_status.reserve(16) || M->mv_swaps.reserve(16) || M->mv_gmax.reserve(16) ||
+        M->mv_Bs.reserve(sizeof(double) * (size_t)n * m) || M->mv_D.reserve(sizeof(double) * m) ||
+        M->s_rows.reserve(sizeof(double) * (size_t)n * m))
+        return MTP_ENOMEM;
+    // the stacked matrix [A; candidates]: the current active set first, so that MaxVol starts from it
+    double* B = M->s_rows.as<double>();
+    const size_t mm = (size_t)m * m;
+    cudaMemcpyAsync(B, M->d_A.p, sizeof(double) * mm, cudaMemcpyDeviceToDevice, st);
+    if (n_cand)
+        cudaMemcpyAsync(B + mm, cand_rows, sizeof(double) * (size_t)n_cand * m,
+                        (flags & MTP_HOST_MEMORY) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(M->mv_status.p, 0, sizeof(int), st);
+    const int lm = mtp::launch_maxvol(n, m, B, M->mv_Bs.as<double>(), M->mv_D.as<double>(), M->mv_W.as<double>(),
+                                      M->mv_perm.as<int>(), M->mv_sel.as<int>(), M->d_A.as<double>(),
+                                      M->d_Ai.as<double>(), M->mv_C.as<double>(), 1e-3, 100 * m,
+                                      M->mv_status.as<int>(), M->mv_swaps.as<int>(), M->mv_gmax.as<double>(), st, 1);
+    if (lm < 0) {
+        M->has_active = false;
+        return MTP_ECUDA;
+    }
+    M->launches += lm;
+    int status = 0, swaps = 0;
+    std::vector<int> sel(m);
+    cudaMemcpyAsync(&status, M->mv_status.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&swaps, M->mv_swaps.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(sel.data(), M->mv_sel.p, sizeof(int) * m, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    M->tc_ready = false;
+    if (status & (mtp::kErrSingular | mtp::kErrTimeout)) {  // A and A^-1 were overwritten
+        M->has_active = false;
+        return (status & mtp::kErrSingular) ? MTP_ESINGULAR : MTP_ETIMEOUT;
+    }
+    std::vector<int> ent;
+    for (int j = 0; j < m; ++j)
+        if (sel[j] >= m) ent.push_back(sel[j] - m);
+    std::sort(ent.begin(), ent.end());
+    // rows of the new active set: earlier rows keep their indices, candidates are marked -1
+    std::vector<int> kept(m);
+    for (int j = 0; j < m; ++j) kept[j] = sel[j] < m ? M->active_rows[sel[j]] : -1;
+    M->active_rows = kept;
+    if (entered) std::copy(ent.begin(), ent.end(), entered);
+    if (n_entered) *n_entered = (int)ent.size();
+    if (rows) std::copy(sel.begin(), sel.end(), rows);
+    if (n_swaps) *n_swaps = swaps;
+    return MTP_OK;
+}
+
 mtp_status mtp_set_active_set(mtp_model* M, const double* A) {
     if (!M || !A) return MTP_EINVAL;
     M->g_sig.clear();
-    const int m = M->m;
+    const int m = M->gw;
     if (M->d_A.reserve(sizeof(double) * m * m) || M->d_Ai.reserve(sizeof(double) * m * m) ||
         M->mv_W.reserve(sizeof(double) * 2 * m * m + 16) || M->mv_status.reserve(16))
         return MTP_ENOMEM;
@@ -1047,10 +1289,10 @@ mtp_status mtp_set_active_set(mtp_model* M, const double* A) {
 mtp_status mtp_get_active_set(const mtp_model* M, double* A, double* A_inv, int32_t* rows) {
     if (!M) return MTP_EINVAL;
     if (!M->has_active) return MTP_ENOACTIVESET;
-    const size_t bytes = sizeof(double) * M->m * M->m;
+    const size_t bytes = sizeof(double) * M->gw * M->gw;
     if (A && cudaMemcpy(A, M->d_A.p, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
     if (A_inv && cudaMemcpy(A_inv, M->d_Ai.p, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
-    if (rows) std::memcpy(rows, M->active_rows.data(), sizeof(int) * M->m);
+    if (rows) std::memcpy(rows, M->active_rows.data(), sizeof(int) * M->gw);
     return MTP_OK;
 }
 
@@ -1069,6 +1311,7 @@ struct ModelFile {
     std::vector<double> xi, c, A, Ai;
     std::vector<int> rows;
     bool active = false;
+    bool nonlinear = false;
 };
 
 class Tokens {
@@ -1149,14 +1392,16 @@ bool parse_model_file(const char* path, ModelFile& mf) {
     const size_t m = (size_t)ops->M;
     const size_t nc = (size_t)mf.S * mf.S * ops->NMU * mf.NQ;
     if (!t.reals("xi", m, mf.xi) || !t.reals("c", nc, mf.c)) return false;
-    if (!t.key("active_set") || !t.integer(0, 1, v)) return false;
-    mf.active = v == 1;
+    if (!t.key("active_set") || !t.integer(0, 2, v)) return false;
+    mf.active = v >= 1;
+    mf.nonlinear = v == 2;
     if (mf.active) {
-        if (!t.reals("A", m * m, mf.A) || !t.reals("A_inv", m * m, mf.Ai)) return false;
+        const size_t w = mf.nonlinear ? m + nc : m;
+        if (!t.reals("A", w * w, mf.A) || !t.reals("A_inv", w * w, mf.Ai)) return false;
         long n = 0;
-        if (!t.key("rows") || !t.integer(0, 1L << 30, n) || (size_t)n != m) return false;
-        mf.rows.resize(m);
-        for (size_t i = 0; i < m; ++i) {
+        if (!t.key("rows") || !t.integer(0, 1L << 30, n) || (size_t)n != w) return false;
+        mf.rows.resize(w);
+        for (size_t i = 0; i < w; ++i) {
             long r = 0;
             if (!t.integer(-1, 0x7fffffffL, r)) return false;
             mf.rows[i] = (int)r;
@@ -1174,7 +1419,7 @@ void write_reals(std::FILE* f, const char* key, const double* v, size_t n) {
 
 mtp_status mtp_save(const mtp_model* M, const char* path) {
     if (!M || !path) return MTP_EINVAL;
-    const size_t m = (size_t)M->m;
+    const size_t m = (size_t)M->gw;
     std::vector<double> A, Ai;
     if (M->has_active) {
         A.resize(m * m);
@@ -1193,7 +1438,8 @@ mtp_status mtp_save(const mtp_model* M, const char* path) {
     std::fprintf(f, "neighbor_capacity %d\nthreads_per_atom %d %d\n", M->cap, M->tpa_moments, M->tpa_pairs);
     write_reals(f, "xi", M->xi.data(), M->xi.size());
     write_reals(f, "c", M->c.data(), M->c.size());
-    std::fprintf(f, "active_set %d\n", M->has_active ? 1 : 0);
+    // 0: none; 1: linear active set (m x m); 2: nonlinear (Jacobian rows, (m + #c) x (m + #c))
+    std::fprintf(f, "active_set %d\n", M->has_active ? (M->nonlinear ? 2 : 1) : 0);
     if (M->has_active) {
         write_reals(f, "A", A.data(), A.size());
         write_reals(f, "A_inv", Ai.data(), Ai.size());
@@ -1216,6 +1462,7 @@ mtp_status mtp_load(const char* path, mtp_model** out) {
     if (!st) st = mtp_set_skin(M, mf.skin);
     if (!st) st = mtp_set_neighbor_capacity(M, mf.cap);
     if (!st) st = mtp_set_threads_per_atom(M, mf.tpa_m, mf.tpa_p);
+    if (!st && mf.nonlinear) st = mtp_set_grade_kind(M, 1);
     if (!st && mf.active) {
         // A and A^-1 as saved (not recomputed), so that grades read back bit for bit
         const size_t bytes = sizeof(double) * mf.A.size();
@@ -1242,7 +1489,7 @@ mtp_status mtp_grade(mtp_model* M, int n_rows, const double* b_rows, double* gam
     if (!M || n_rows < 0 || (n_rows > 0 && (!b_rows || !gamma))) return MTP_EINVAL;
     if (!M->has_active) return MTP_ENOACTIVESET;
     cudaStream_t st = (cudaStream_t)stream;
-    const int m = M->m;
+    const int m = M->gw;
     const double* B = b_rows;
     double* g = gamma;
     if (flags & MTP_HOST_MEMORY) {
@@ -1262,9 +1509,62 @@ mtp_status mtp_grade(mtp_model* M, int n_rows, const double* b_rows, double* gam
     return M->prec == MTP_FP32_TC ? finish(M, st) : cuda_status(cudaStreamSynchronize(st));
 }
 
+}  // extern "C"
+
+namespace {
+
+// Active selection during MD (Sec. 2.3): thresholds, the device ring buffer of selected frames and
+// the host-side records.
+struct MdSelect {
+    double g_select, g_break;
+    int cap;              // ring slots
+    double* ring_pos;     // device [cap][n][3]
+    int32_t* ring_steps;  // host [cap]
+    double* ring_gamma;   // host [cap]
+    int n_selected = 0;
+    int stop_step = -1;
+    double* gammas;       // host [n_steps + 1] or NULL
+};
+
+mtp_status md_impl(mtp_model* M, int n, double* pos, double* vel, const int32_t* types, const double* cell,
+                   const double* masses, double dt, int n_steps, double* e_pot, double* e_kin, int* n_rebuilds,
+                   int flags, void* stream, MdSelect* sel);
+
+}  // namespace
+
+extern "C" {
+
 mtp_status mtp_md_run(mtp_model* M, int n, double* pos, double* vel, const int32_t* types, const double* cell,
                       const double* masses, double dt, int n_steps, double* e_pot, double* e_kin, int* n_rebuilds,
                       int flags, void* stream) {
+    return md_impl(M, n, pos, vel, types, cell, masses, dt, n_steps, e_pot, e_kin, n_rebuilds, flags, stream, nullptr);
+}
+
+mtp_status mtp_md_select(mtp_model* M, int n, double* pos, double* vel, const int32_t* types, const double* cell,
+                         const double* masses, double dt, int n_steps, double gamma_select, double gamma_break,
+                         int ring_capacity, double* ring_pos, int32_t* ring_steps, double* ring_gamma,
+                         int* n_selected, int* stop_step, double* gammas, double* e_pot, double* e_kin,
+                         int* n_rebuilds, int flags, void* stream) {
+    if (!M || !(gamma_select < gamma_break) || !(gamma_select >= 0.0) || ring_capacity < 0 ||
+        (ring_capacity > 0 && (!ring_pos || !ring_steps || !ring_gamma)))
+        return MTP_EINVAL;
+    if (!M->has_active) return MTP_ENOACTIVESET;
+    if (M->nonlinear) return MTP_EUNSUPPORTED;
+    MdSelect sel{gamma_select, gamma_break, ring_capacity, ring_pos, ring_steps, ring_gamma, 0, -1, gammas};
+    const mtp_status s =
+        md_impl(M, n, pos, vel, types, cell, masses, dt, n_steps, e_pot, e_kin, n_rebuilds, flags, stream, &sel);
+    if (n_selected) *n_selected = sel.n_selected;
+    if (stop_step) *stop_step = sel.stop_step;
+    return s;
+}
+
+}  // extern "C"
+
+namespace {
+
+mtp_status md_impl(mtp_model* M, int n, double* pos, double* vel, const int32_t* types, const double* cell,
+                   const double* masses, double dt, int n_steps, double* e_pot, double* e_kin, int* n_rebuilds,
+                   int flags, void* stream, MdSelect* sel) {
     if (!M || n < 1 || !pos || !vel || !types || !cell || !masses || !(dt > 0.0) || n_steps < 0) return MTP_EINVAL;
     if (flags & MTP_HOST_MEMORY) return MTP_EUNSUPPORTED;
     if (!(M->skin > 0.0)) return MTP_EINVAL;  // velocity Verlet reuses lists: needs a skin
@@ -1279,33 +1579,70 @@ mtp_status mtp_md_run(mtp_model* M, int n, double* pos, double* vel, const int32
     cudaMemcpyAsync(M->s_off.p, off_h, sizeof off_h, cudaMemcpyHostToDevice, st);
     const int* off = M->s_off.as<int>();
     double* F = M->md_F.as<double>();
-    double* sc = M->md_scalars.as<double>();  // [0] E_pot, [1] E_kin
+    double* sc = M->md_scalars.as<double>();  // [0] E_pot, [1] E_kin, [2] grade
     int* flag = M->md_flag.as<int>();
     const double* mass = M->md_masses.as<double>();
     const double lim2 = 0.25 * M->skin * M->skin;
     int rebuilds = 0;
     std::vector<double> ep(n_steps + 1), ek(n_steps + 1);
+    // with selection, every evaluation also forms the configuration's b row (Eq. 13) and its grade
+    double* brow = nullptr;
+    double* batoms = nullptr;
+    if (sel) {
+        if (M->g_brows.reserve(sizeof(double) * M->m + 8) || M->g_batoms.reserve(sizeof(double) * N * M->m + 8))
+            return MTP_ENOMEM;
+        brow = M->g_brows.as<double>();
+        batoms = M->g_batoms.as<double>();
+    }
     auto forces = [&](bool reuse) -> mtp_status {
         mtp_status s2 = reuse ? refresh_neighbors(M, 1, n, pos, st)
                               : prepare_neighbors(M, 1, n, off, pos, types, cell, M->skin, st);
         if (s2) return s2;
         if (is_fp64(M))
-            return run_eval<double>(M, 1, n, off, types, sc, F, nullptr, nullptr, nullptr, nullptr, st);
-        return run_eval<float>(M, 1, n, off, types, sc, F, nullptr, nullptr, nullptr, nullptr, st);
+            s2 = run_eval<double>(M, 1, n, off, types, sc, F, nullptr, nullptr, brow, batoms, st);
+        else
+            s2 = run_eval<float>(M, 1, n, off, types, sc, F, nullptr, nullptr, brow, batoms, st);
+        if (s2 || !sel) return s2;
+        const int l = launch_grades(M, 1, brow, sc + 2, st);
+        if (l < 0) return MTP_ECUDA;
+        M->launches += l;
+        return MTP_OK;
     };
+    bool stop = false;
     auto record = [&](int step) -> mtp_status {
         cudaMemsetAsync(sc + 1, 0, sizeof(double), st);
         M->launches += mtp::launch_kinetic(n, M->S, vel, types, mass, sc + 1, st, M->n_sm);
-        double h[2];
-        cudaMemcpyAsync(h, sc, sizeof h, cudaMemcpyDeviceToHost, st);
+        double h[3] = {0.0, 0.0, 0.0};
+        cudaMemcpyAsync(h, sc, sizeof(double) * (sel ? 3 : 2), cudaMemcpyDeviceToHost, st);
         mtp_status s2 = finish(M, st);
         ep[step] = h[0];
         ek[step] = h[1];
+        if (!s2 && sel) {  // the two-threshold scheme on this configuration
+            const double g = h[2];
+            if (sel->gammas) sel->gammas[step] = g;
+            if (g > sel->g_select) {
+                if (sel->cap > 0) {
+                    const int slot = sel->n_selected % sel->cap;  // the ring keeps the latest frames
+                    cudaMemcpyAsync(sel->ring_pos + (size_t)slot * 3 * N, pos, sizeof(double) * 3 * N,
+                                    cudaMemcpyDeviceToDevice, st);
+                    sel->ring_steps[slot] = step;
+                    sel->ring_gamma[slot] = g;
+                }
+                ++sel->n_selected;
+            }
+            if (g >= sel->g_break) {
+                sel->stop_step = step;
+                stop = true;
+                if (cudaStreamSynchronize(st) != cudaSuccess) s2 = MTP_ECUDA;
+            }
+        }
         return s2;
     };
+    int done = n_steps;
     mtp_status s = forces(false);
     if (!s) s = record(0);
-    for (int step = 1; step <= n_steps && !s; ++step) {
+    if (stop) done = 0;
+    for (int step = 1; step <= n_steps && !s && !stop; ++step) {
         M->launches += mtp::launch_kick(n, M->S, vel, F, types, mass, 0.5 * dt, st, M->n_sm);
         cudaMemsetAsync(flag, 0, sizeof(int), st);
         M->launches += mtp::launch_drift(n, pos, vel, M->nb.x0.as<double>(), dt, lim2, flag, st, M->n_sm);
@@ -1317,13 +1654,14 @@ mtp_status mtp_md_run(mtp_model* M, int n, double* pos, double* vel, const int32
         if (s) break;
         M->launches += mtp::launch_kick(n, M->S, vel, F, types, mass, 0.5 * dt, st, M->n_sm);
         s = record(step);
+        if (stop) done = step;
     }
     if (s) return s;
-    if (e_pot) std::copy(ep.begin(), ep.end(), e_pot);
-    if (e_kin) std::copy(ek.begin(), ek.end(), e_kin);
+    if (e_pot) std::copy(ep.begin(), ep.begin() + done + 1, e_pot);
+    if (e_kin) std::copy(ek.begin(), ek.begin() + done + 1, e_kin);
     if (n_rebuilds) *n_rebuilds = rebuilds;
     return MTP_OK;
 }
 
-}  // extern "C"
+}  // namespace
 

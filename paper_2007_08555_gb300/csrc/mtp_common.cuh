@@ -82,6 +82,7 @@ struct EvalCtx {
     T* dslots;            // [2][ceil(n/32)][NDSLOT][32] dV/dM and its tangent, per tangent-contraction part
     double* dxt;          // [ceil(n/32)][M] per-tile shares of dL/dxi from the tangent contraction
     double* dc;           // [S][S][NMU][NQ] accumulated dL/dc
+    double* dc_rows;      // [n_cfg][S][S][NMU][NQ] per-configuration dE_k/dc (Jacobian rows) or NULL
 };
 
 // Loss (Sec. 2.2): residuals and the directions of the gradient.  Scalings of Eqs. 7, 11, 12.
@@ -99,6 +100,7 @@ struct LossArgs {
     double* loss;           // [1] accumulated
     double* gew;            // [K]
     int loss_only;          // 1: residuals and loss only, no gradient kernels
+    int jacobian;           // 1: per-configuration dE/dc (the caller set e_k = 1, D = 0, eps = 0)
 };
 
 __host__ __device__ inline void loss_scales(int kind, double n, double* se, double* sf, double* ss) {

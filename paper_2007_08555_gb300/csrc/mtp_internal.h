@@ -69,7 +69,7 @@ int scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_t st);
 // Active set (mtp_maxvol.cu)
 int launch_maxvol(int n, int m, const double* B, double* Bs, double* D, double* W, int* perm, int* sel, double* A,
                   double* Ai, double* C, double tol, int max_iter, int* status, int* swaps, double* gmax,
-                  cudaStream_t st);
+                  cudaStream_t st, int start_given = 0);
 int launch_invert(int m, const double* A, double* Ai, double* W, int* status, cudaStream_t st);
 template <class T>
 int launch_grade(int n, int m, const T* B, int ldb, const T* Ai, unsigned long long* gbits, cudaStream_t st);
@@ -81,6 +81,26 @@ int launch_grade_tc_prep(int m, const double* A, const double* Ai, void* digits,
                          cudaStream_t st);
 int launch_grade_tc(int n, int m, const double* B, int ldb, const void* digits, const int* ecol, const float* cscale,
                     unsigned long long* gbits, int* err, cudaStream_t st, int n_sm);
+
+// Batched relaxation (mtp_relax.cu): FIRE state of every configuration and the evaluation at the
+// current coordinates (forces, virial, energy, cell, grade or NULL).
+enum { kRelaxRunning = 0, kRelaxConverged = 1, kRelaxStopped = 2, kRelaxStepLimit = 3, kRelaxDiverged = 4 };
+struct RelaxArgs {
+    const int* off;
+    int relax_cell, max_steps;
+    double fmax, smax, gamma_break, dt_max;
+    const double* F;      // [n][3]
+    const double* W;      // [K][9]
+    const double* E;      // [K]
+    const double* H;      // [K][9] current cells
+    const double* gamma;  // [K] or NULL
+    double *u, *vu, *D, *vD, *dt, *alpha, *e_final;
+    int *npos, *status, *steps;
+};
+int launch_relax_init(const RelaxArgs& a, int n, int K, const double* x, double dt0, cudaStream_t st);
+int launch_relax_map(int n, int K, const int* off, const double* u, const double* D, const double* H0, double* x,
+                     double* H, cudaStream_t st);
+int launch_fire(const RelaxArgs& a, int K, int step, cudaStream_t st);
 
 // Molecular dynamics helpers (mtp_md.cu).  The refreshed r_ij go to nb.cx/cy/cz.
 int launch_update_pairs(const NbrState& nb, const double* x, cudaStream_t st, int n_sm);

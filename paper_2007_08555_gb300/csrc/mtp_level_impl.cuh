@@ -1389,7 +1389,9 @@ __global__ void __launch_bounds__(128) k_dc(const EvalCtx<T> a) {
                 }
             }
             if (any) {
-                double* dst = dcs + (size_t)((zi * a.S + zp) * NMU) * NQ;
+                // the loss gradient sums over the batch (shared memory first); Jacobian rows go to
+                // their configuration's row directly
+                double* dst = (a.dc_rows ? a.dc_rows + (size_t)k * nc : dcs) + (size_t)((zi * a.S + zp) * NMU) * NQ;
 #pragma unroll
                 for (int mu = 0; mu < NMU; ++mu)
 #pragma unroll
@@ -1399,8 +1401,9 @@ __global__ void __launch_bounds__(128) k_dc(const EvalCtx<T> a) {
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < nc; q += blockDim.x)
-        if (dcs[q] != 0.0) atomicAdd(&a.dc[q], dcs[q]);
+    if (!a.dc_rows)
+        for (int q = threadIdx.x; q < nc; q += blockDim.x)
+            if (dcs[q] != 0.0) atomicAdd(&a.dc[q], dcs[q]);
 }
 
 template <class T, int TPA>
@@ -1425,9 +1428,11 @@ int grad_all(EvalCtx<T>& a, const LossArgs& L, cudaStream_t st, int n_sm) {
     int launches = 0;
     T* D = const_cast<T*>(a.gD);
     T* eps = const_cast<T*>(a.geps);
-    k_resid_atoms<T><<<min((a.n_atoms + 127) / 128 + 1, n_sm * 8), 128, 0, st>>>(a, L, D);
-    k_resid_cfgs<T><<<min((a.n_cfg + 127) / 128 + 1, n_sm * 8), 128, 0, st>>>(L, eps);
-    launches += 2;
+    if (!L.jacobian) {
+        k_resid_atoms<T><<<min((a.n_atoms + 127) / 128 + 1, n_sm * 8), 128, 0, st>>>(a, L, D);
+        k_resid_cfgs<T><<<min((a.n_cfg + 127) / 128 + 1, n_sm * 8), 128, 0, st>>>(L, eps);
+        launches += 2;
+    }
     if (a.n_atoms == 0 || L.loss_only) return launches;
     switch (a.tpa) {
         case 8: launches += launch_grad_pairs<T, 8>(a, st, n_sm); break;

@@ -4,7 +4,8 @@
 //   0. columns are scaled by 1 / max |column| (the grades and the selection are invariant under
 //      B -> B D, and the scaled matrix is far better conditioned);
 //   1. start rows: the pivot rows of Gaussian elimination with partial pivoting on the tall
-//      matrix B (n_rows x m); ties go to the smaller current row position;
+//      matrix B (n_rows x m); ties go to the smaller current row position (or, for the select-add
+//      update, the first m rows: the current active set stacked above the candidates);
 //   2. A^-1 of A = B[sel] by Gauss-Jordan elimination with partial pivoting;
 //   3. C = B A^-1 for every row;
 //   4. repeat at most max_iter times: (k, j) = argmax |C_kj| (ties: smallest k, then smallest j);
@@ -116,7 +117,7 @@ __device__ bool gauss_jordan(const double* A, double* Ai, double* W, int m, ArgM
 __global__ void __launch_bounds__(kMvThreads) k_maxvol(int n, int m, const double* Braw, double* Bs, double* D,
                                                        double* W, int* perm, int* sel, double* A, double* Ai, double* C,
                                                        double tol, int max_iter, int* status, int* swaps_out,
-                                                       double* gmax_out) {
+                                                       double* gmax_out, int start_given) {
     __shared__ ArgMax sbuf[33];
     __shared__ int s_flag;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -135,6 +136,11 @@ __global__ void __launch_bounds__(kMvThreads) k_maxvol(int n, int m, const doubl
     for (int e = tid; e < n * m; e += nt) Bs[e] = Braw[e] * D[e % m];
     __syncthreads();
     const double* B = Bs;
+    if (start_given) {  // select-add: start from the first m rows (the current active set)
+        for (int j = tid; j < m; j += nt) sel[j] = j;
+        __syncthreads();
+        goto have_start;
+    }
     // 1. pivot rows of LU with partial pivoting (row interchanges tracked in perm)
     for (int e = tid; e < n * m; e += nt) W[e] = B[e];
     for (int r = tid; r < n; r += nt) perm[r] = r;
@@ -174,6 +180,7 @@ __global__ void __launch_bounds__(kMvThreads) k_maxvol(int n, int m, const doubl
     }
     for (int j = tid; j < m; j += nt) sel[j] = perm[j];
     __syncthreads();
+have_start:
     // 2. A and its inverse
     for (int e = tid; e < m * m; e += nt) A[e] = B[sel[e / m] * m + (e % m)];
     __syncthreads();
@@ -314,8 +321,9 @@ int launch_invert(int m, const double* A, double* Ai, double* W, int* status, cu
 
 int launch_maxvol(int n, int m, const double* B, double* Bs, double* D, double* W, int* perm, int* sel, double* A,
                   double* Ai, double* C, double tol, int max_iter, int* status, int* swaps, double* gmax,
-                  cudaStream_t st) {
-    k_maxvol<<<1, kMvThreads, 0, st>>>(n, m, B, Bs, D, W, perm, sel, A, Ai, C, tol, max_iter, status, swaps, gmax);
+                  cudaStream_t st, int start_given) {
+    k_maxvol<<<1, kMvThreads, 0, st>>>(n, m, B, Bs, D, W, perm, sel, A, Ai, C, tol, max_iter, status, swaps, gmax,
+                                       start_given);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -401,7 +409,7 @@ extern "C" mtp_status mtp_select_active_set_noalloc(int n_rows, int m, const dou
     double* gmax = reinterpret_cast<double*>(base + (need - 1));
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(status, 0, 2 * sizeof(int), st) != cudaSuccess) return MTP_ECUDA;
-    if (launch_maxvol(n_rows, m, b_rows, Bs, D, W, perm, sel, A, Ai, C, 1e-3, 100 * m, status, swaps, gmax, st) < 0)
+    if (launch_maxvol(n_rows, m, b_rows, Bs, D, W, perm, sel, A, Ai, C, 1e-3, 100 * m, status, swaps, gmax, st, 0) < 0)
         return MTP_ECUDA;
     int h[2] = {0, 0};
     if (cudaMemcpyAsync(h, status, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MTP_ECUDA;

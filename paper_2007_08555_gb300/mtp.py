@@ -77,6 +77,13 @@ _SIGS = {
     "mtp_save": (_I, [_P, ctypes.c_char_p]),
     "mtp_load": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "mtp_fp32_peak": (_I, [_I, ctypes.POINTER(_D)]),
+    "mtp_set_grade_kind": (_I, [_P, _I]),
+    "mtp_relax_batch": (_I, [_P, _I, _I, _P, _P, _P, _P, _I, _D, _D, _D, _I, _D, _D, _P, _P, _P, _P]),
+    "mtp_grade_width": (_I, [_P]),
+    "mtp_jacobian_rows": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, _P]),
+    "mtp_select_add": (_I, [_P, _I, _P, _P, ctypes.POINTER(_I), _P, ctypes.POINTER(_I), _I, _P]),
+    "mtp_md_select": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _I, _D, _D, _I, _P, _P, _P, ctypes.POINTER(_I),
+                           ctypes.POINTER(_I), _P, _P, _P, ctypes.POINTER(_I), _I, _P]),
     "mtp_autotune": (_I, [_P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _P]),
 }
 
@@ -198,6 +205,39 @@ def mtp_md_run(h, n_atoms, pos, vel, types, cell, masses, dt, n_steps, stream=No
     _check(load().mtp_md_run(h, int(n_atoms), _ptr(pos), _ptr(vel), _ptr(types), _ptr(cell), _ptr(m), float(dt),
                              int(n_steps), _ptr(ep), _ptr(ek), ctypes.byref(nr), 0, _stream(stream)), "mtp_md_run")
     return ep, ek, int(nr.value)
+
+
+def mtp_select_add(h, m, n_cand, cand_rows, flags=0, stream=None):
+    """Select-add update of the active set; returns (entered candidate indices, rows [m], swaps)."""
+    entered = np.zeros(m, dtype=np.int32)
+    rows = np.zeros(m, dtype=np.int32)
+    ne, sw = ctypes.c_int(), ctypes.c_int()
+    s = None if flags & HOST_MEMORY else _stream(stream)
+    _check(load().mtp_select_add(h, int(n_cand), _ptr(cand_rows), _ptr(entered), ctypes.byref(ne), _ptr(rows),
+                                 ctypes.byref(sw), int(flags), s), "mtp_select_add")
+    return entered[:ne.value].tolist(), rows, int(sw.value)
+
+
+def mtp_md_select(h, n_atoms, pos, vel, types, cell, masses, dt, n_steps, gamma_select, gamma_break, ring_pos,
+                  stream=None):
+    """MD with the two-threshold check (device tensors; ring_pos [cap, n, 3] float64 device).  Returns a
+    dict: n_selected, stop_step (None if completed), ring_steps, ring_gamma, gammas, e_pot, e_kin, rebuilds."""
+    cap = 0 if ring_pos is None else int(ring_pos.shape[0])
+    rs = np.zeros(max(cap, 1), dtype=np.int32)
+    rg = np.zeros(max(cap, 1))
+    g = np.full(n_steps + 1, np.nan)
+    ep = np.full(n_steps + 1, np.nan)
+    ek = np.full(n_steps + 1, np.nan)
+    ns, stop, nr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    m = np.ascontiguousarray(masses, dtype=np.float64)
+    _check(load().mtp_md_select(h, int(n_atoms), _ptr(pos), _ptr(vel), _ptr(types), _ptr(cell), _ptr(m), float(dt),
+                                int(n_steps), float(gamma_select), float(gamma_break), cap, _ptr(ring_pos),
+                                _ptr(rs), _ptr(rg), ctypes.byref(ns), ctypes.byref(stop), _ptr(g), _ptr(ep), _ptr(ek),
+                                ctypes.byref(nr), 0, _stream(stream)), "mtp_md_select")
+    last = n_steps if stop.value < 0 else stop.value
+    return {"n_selected": int(ns.value), "stop_step": None if stop.value < 0 else int(stop.value),
+            "ring_steps": rs[:min(cap, ns.value)], "ring_gamma": rg[:min(cap, ns.value)], "gammas": g[:last + 1],
+            "e_pot": ep[:last + 1], "e_kin": ek[:last + 1], "rebuilds": int(nr.value)}
 
 
 def mtp_sync(h, stream=None):
@@ -427,11 +467,54 @@ class Model:
         """Velocity Verlet in place (device tensors); returns (e_pot, e_kin, rebuilds)."""
         return mtp_md_run(self.h, pos.shape[0], pos, vel, types, cell, masses, dt, n_steps, stream)
 
+    def relax_batch(self, pos, types, cells, cfg_off, relax_cell=True, fmax=1e-4, smax=1e-5, gamma_break=float("inf"),
+                    max_steps=5000, dt=0.05, dt_max=0.5):
+        """FIRE relaxation of a batch in place (device tensors pos [N,3], cells [K,3,3]); returns
+        (energy [K] device, steps [K], status [K]: 1 converged, 2 stopped by the grade, 3 step limit, 4 diverged)."""
+        import torch
+
+        K = cells.shape[0]
+        energy = torch.empty(K, dtype=torch.float64, device=pos.device)
+        steps = np.zeros(K, dtype=np.int32)
+        status = np.zeros(K, dtype=np.int32)
+        _check(load().mtp_relax_batch(self.h, K, pos.shape[0], _ptr(cfg_off), _ptr(pos), _ptr(types), _ptr(cells),
+                                      int(bool(relax_cell)), float(fmax), float(smax), float(gamma_break),
+                                      int(max_steps), float(dt), float(dt_max), _ptr(energy), _ptr(steps),
+                                      _ptr(status), _stream(None)), "mtp_relax_batch")
+        return energy, steps, status
+
+    def set_grade_kind(self, nonlinear):
+        """0: grades of b rows (linear criterion); 1: grades of Jacobian rows dE/dtheta (nonlinear)."""
+        _check(load().mtp_set_grade_kind(self.h, int(nonlinear)), "mtp_set_grade_kind")
+
+    @property
+    def grade_width(self):
+        return int(load().mtp_grade_width(self.h))
+
+    def jacobian_rows(self, pos, types, cells, cfg_off):
+        """Rows [K, m + S^2 N_mu N_Q] = [b(cfg), dE/dc] of the nonlinear criterion (device float64)."""
+        import torch
+
+        K = cells.shape[0]
+        w = self.m + self.n_species ** 2 * self.n_mu * self.n_radial
+        rows = torch.empty((K, w), dtype=torch.float64, device=pos.device)
+        _check(load().mtp_jacobian_rows(self.h, K, pos.shape[0], _ptr(cfg_off), _ptr(pos), _ptr(types), _ptr(cells),
+                                        _ptr(rows), 0, _stream(None)), "mtp_jacobian_rows")
+        return rows
+
+    def select_add(self, cand_rows):
+        """Select-add update from candidate b rows (device float64 [k, m]); (entered, rows, swaps)."""
+        return mtp_select_add(self.h, self.grade_width, cand_rows.shape[0], cand_rows.contiguous())
+
+    def md_select(self, pos, vel, types, cell, masses, dt, n_steps, gamma_select, gamma_break, ring_pos=None):
+        return mtp_md_select(self.h, pos.shape[0], pos, vel, types, cell, masses, dt, n_steps, gamma_select,
+                             gamma_break, ring_pos)
+
     def select_active_set(self, b_rows):
         """MaxVol over the rows of b_rows (device float64 [n, m]); returns (rows, swaps, max |C|)."""
         import torch
 
-        sel = torch.empty(self.m, dtype=torch.int32, device=b_rows.device)
+        sel = torch.empty(self.grade_width, dtype=torch.int32, device=b_rows.device)
         swaps, g = mtp_select_active_set(self.h, b_rows.shape[0], b_rows.contiguous(), sel)
         return sel, swaps, g
 

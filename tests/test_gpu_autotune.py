@@ -63,4 +63,7 @@ def test_work_queues_restart_every_evaluation(gpu_lib, precision):
     model.set_skin(0.3)
     model.eval_batch(pos, types, cells, off)
     again = model.eval_batch(pos, types, cells, off, flags=mtp.REUSE_NEIGHBORS)
-    np.testing.assert_allclose(again["energy"].cpu().numpy(), first["energy"].cpu().numpy(), rtol=1e-12)
+    # the list with a skin holds more pairs, which changes how pairs fall on the lanes of an atom, so
+    # the float path agrees to rounding of its sums only
+    np.testing.assert_allclose(again["energy"].cpu().numpy(), first["energy"].cpu().numpy(),
+                               rtol=1e-12 if precision == "fp64" else 1e-4)
