@@ -230,21 +230,28 @@ mtp_status mtp_select_add(mtp_model* model, int n_cand, const double* cand_rows,
 
 /*
  * Kind of extrapolation grade (Sec. 2.3): 0 (default) the linear criterion, rows b(cfg) of width m;
- * 1 the nonlinear criterion, where the rows are the Jacobian dE(cfg)/dtheta over every parameter
- * theta = [xi (m), c (S, S, N_mu, N_Q) in C order], width m + S^2 N_mu N_Q (mtp_grade_width()).
- * The active set (mtp_select_active_set, mtp_select_add, mtp_set_active_set, mtp_get_active_set,
- * mtp_grade, model files) then has that width; changing the kind drops the installed active set.
- * In the nonlinear kind, rows come from mtp_jacobian_rows() and are graded with mtp_grade();
- * mtp_eval_batch's grades and mtp_md_select return MTP_EUNSUPPORTED.
+ * 1 the nonlinear criterion, where the rows are the Jacobian dE(cfg)/dtheta over the parameters
+ * theta = [xi (m), c (S, S, N_mu, N_Q) in C order].  The full Jacobian rows satisfy exact linear
+ * relations (E is homogeneous in each radial block c[:, :, mu, :], Euler's theorem), so no square
+ * submatrix of them is invertible; cols (host, n_cols ascending indices into theta) selects an
+ * independent set of parameter columns, e.g. by a column-pivoted QR of training rows; NULL takes
+ * all m + S^2 N_mu N_Q.  The active set (mtp_select_active_set, mtp_select_add, mtp_set_active_set,
+ * mtp_get_active_set, mtp_grade, model files) then has width n_cols (mtp_grade_width(),
+ * mtp_grade_columns()); changing the kind drops the installed active set.  In the nonlinear kind,
+ * rows come from mtp_jacobian_rows() and are graded with mtp_grade(); mtp_eval_batch's grades,
+ * mtp_md_select and grade-checked relaxations return MTP_EUNSUPPORTED.  MTP_EINVAL for columns
+ * out of range or not ascending.
  */
-mtp_status mtp_set_grade_kind(mtp_model* model, int nonlinear);
+mtp_status mtp_set_grade_kind(mtp_model* model, int nonlinear, int n_cols, const int32_t* cols);
 int mtp_grade_width(const mtp_model* model);
+mtp_status mtp_grade_columns(const mtp_model* model, int32_t* cols /* host [mtp_grade_width()] */);
 
 /*
  * Jacobian rows of the nonlinear criterion (Sec. 2.3) for a batch (layout of mtp_eval_batch, device
- * arrays): rows [n_cfg][m + S^2 N_mu N_Q] (double, device), row k = [b(cfg_k), dE_k/dc] with
- * b(cfg_k) = sum_i B(n_i) = dE_k/dxi (Eq. 2) and dE_k/dc from the adjoint kernels of mtp_param_grad,
- * summed per configuration in double precision.  Flags: MTP_ASYNC.
+ * arrays): rows [n_cfg][mtp_grade_width()] (double, device), the columns selected by
+ * mtp_set_grade_kind() of [b(cfg_k), dE_k/dc] with b(cfg_k) = sum_i B(n_i) = dE_k/dxi (Eq. 2) and
+ * dE_k/dc from the adjoint kernels of mtp_param_grad, summed per configuration in double precision.
+ * In the linear kind the rows are [b(cfg_k), dE_k/dc] in full.  Flags: MTP_ASYNC.
  */
 mtp_status mtp_jacobian_rows(mtp_model* model, int n_cfg, int n_atoms, const int32_t* cfg_off, const double* pos,
                              const int32_t* types, const double* cells, double* rows, int flags, void* stream);

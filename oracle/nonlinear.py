@@ -9,11 +9,20 @@ parameter, and the rest of the active-learning algorithm (MaxVol, grades) is unc
 Here theta = (xi, c), flattened as [xi (m), c (S, S, N_mu, N_Q) in C order].  E is linear in xi
 (Eq. 2), so the first m columns are b(cfg) = sum_i B(n_i); the c columns are the exact
 derivatives of E along each unit direction of c (the oracle's forward-mode evaluation).
+
+Reading where the paper is silent: the rows satisfy exact linear relations for every configuration
+(Euler's theorem for each radial index mu: scaling the block c[:, :, mu, :] by t scales every
+M_{mu, nu} by t, so sum_k c_k dE/dc_k over the block equals sum_alpha n_alpha(mu) xi_alpha b_alpha;
+at low levels further relations between the radial blocks), so no m x m submatrix of the full
+rows is invertible.  MaxVol therefore runs over a maximal linearly independent set of parameter
+columns: those chosen by a QR factorisation with column pivoting of the (column-scaled) training
+rows, up to the numerical rank (pivots above 1e-10 of the first), in ascending order.
 """
 
 from __future__ import annotations
 
 import numpy as np
+import scipy.linalg
 
 
 def jacobian_row(pot, cfg, xi, c):
@@ -33,3 +42,16 @@ def jacobian_row(pot, cfg, xi, c):
 def jacobian_rows(pot, configs, xi, c):
     """The tall matrix B of the nonlinear criterion: one Jacobian row per configuration."""
     return np.array([jacobian_row(pot, cfg, xi, c) for cfg in configs])
+
+
+def independent_columns(rows, rtol=1e-10):
+    """Indices (ascending) of a maximal linearly independent set of the columns of `rows`: the first
+    `rank` pivots of a column-pivoted QR of the column-scaled rows, rank = number of |R_kk| above
+    rtol |R_00|."""
+    R = np.asarray(rows, dtype=np.float64)
+    mx = np.abs(R).max(axis=0)
+    R = R / np.where(mx > 0, mx, 1.0)
+    _, Rq, piv = scipy.linalg.qr(R, pivoting=True, mode="economic")
+    d = np.abs(np.diag(Rq))
+    rank = int((d > rtol * d[0]).sum())
+    return np.sort(piv[:rank])

@@ -74,7 +74,8 @@ struct mtp_model {
     // Jacobian rows dE/dtheta)
     int gw = 0;
     bool nonlinear = false;
-    DevBuf j_rows;  // per-configuration dE/dc of the Jacobian rows
+    std::vector<int> gcols;  // nonlinear kind: the parameter columns of the rows (indices into [xi, c])
+    DevBuf j_rows, j_full, d_gcols;  // per-configuration dE/dc, full Jacobian rows, the column list
     // batched relaxation state
     DevBuf r_u, r_vu, r_D, r_vD, r_H0, r_H, r_x, r_dt, r_alpha, r_npos, r_status, r_steps, r_E, r_W, r_F, r_gamma,
         r_efinal;
@@ -785,11 +786,19 @@ mtp_status run_jacobian(mtp_model* M, int K, int n, const int* off, const int* t
         l = M->ops->grad_f32(a, L, st, M->n_sm);
     if (l < 0) return MTP_EUNSUPPORTED;
     M->launches += l;
-    // rows = [b (m) | dE/dc (nc)]
+    // full rows [b (m) | dE/dc (nc)], then the selected columns
+    if (M->j_full.reserve(sizeof(double) * (size_t)K * (m + nc) + 8)) return MTP_ENOMEM;
+    double* full = M->j_full.as<double>();
     const size_t w = sizeof(double) * (size_t)(m + nc);
-    cudaMemcpy2DAsync(rows, w, M->g_brows.p, sizeof(double) * m, sizeof(double) * m, K, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpy2DAsync(rows + m, w, M->j_rows.p, sizeof(double) * nc, sizeof(double) * nc, K, cudaMemcpyDeviceToDevice,
+    cudaMemcpy2DAsync(full, w, M->g_brows.p, sizeof(double) * m, sizeof(double) * m, K, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpy2DAsync(full + m, w, M->j_rows.p, sizeof(double) * nc, sizeof(double) * nc, K, cudaMemcpyDeviceToDevice,
                       st);
+    if (!M->nonlinear) {
+        cudaMemcpyAsync(rows, full, w * K, cudaMemcpyDeviceToDevice, st);
+    } else {
+        if (mtp::launch_gather_columns(K, m + nc, full, M->gw, M->d_gcols.as<int>(), rows, st) < 0) return MTP_ECUDA;
+        M->launches += 1;
+    }
     return cuda_status(cudaGetLastError());
 }
 
@@ -872,10 +881,26 @@ mtp_status mtp_relax_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, d
     return MTP_OK;
 }
 
-mtp_status mtp_set_grade_kind(mtp_model* M, int nonlinear) {
+mtp_status mtp_set_grade_kind(mtp_model* M, int nonlinear, int n_cols, const int32_t* cols) {
     if (!M || (nonlinear != 0 && nonlinear != 1)) return MTP_EINVAL;
+    const int full = M->m + (int)M->c.size();
+    std::vector<int> c;
+    if (nonlinear) {
+        if (cols) {
+            if (n_cols < 1 || n_cols > full) return MTP_EINVAL;
+            c.assign(cols, cols + n_cols);
+            for (int q = 0; q < n_cols; ++q)
+                if (c[q] < 0 || c[q] >= full || (q > 0 && c[q] <= c[q - 1])) return MTP_EINVAL;  // ascending
+        } else {
+            for (int q = 0; q < full; ++q) c.push_back(q);
+        }
+        if (M->d_gcols.reserve(sizeof(int) * c.size() + 8)) return MTP_ENOMEM;
+        if (cudaMemcpy(M->d_gcols.p, c.data(), sizeof(int) * c.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return MTP_ECUDA;
+    }
     M->nonlinear = nonlinear == 1;
-    M->gw = M->m + (M->nonlinear ? (int)M->c.size() : 0);
+    M->gcols = c;
+    M->gw = M->nonlinear ? (int)c.size() : M->m;
     M->has_active = false;  // an active set of the other kind has the wrong width
     M->tc_ready = false;
     M->active_rows.clear();
@@ -884,6 +909,12 @@ mtp_status mtp_set_grade_kind(mtp_model* M, int nonlinear) {
 }
 
 int mtp_grade_width(const mtp_model* M) { return M ? M->gw : 0; }
+
+mtp_status mtp_grade_columns(const mtp_model* M, int32_t* cols) {
+    if (!M || !cols) return MTP_EINVAL;
+    for (int q = 0; q < M->gw; ++q) cols[q] = M->nonlinear ? M->gcols[q] : q;
+    return MTP_OK;
+}
 
 mtp_status mtp_jacobian_rows(mtp_model* M, int K, int n, const int32_t* cfg_off, const double* pos,
                              const int32_t* types, const double* cells, double* rows, int flags, void* stream) {
@@ -1302,14 +1333,14 @@ mtp_status mtp_get_active_set(const mtp_model* M, double* A, double* A_inv, int3
 namespace {
 
 constexpr const char* kFileMagic = "mtp-gb300-potential";
-constexpr int kFileVersion = 1;
+constexpr int kFileVersion = 2;  // version 1 files (no grade_kind record) are still read
 
 struct ModelFile {
     int L = 0, S = 0, NQ = 0, cap = 128, tpa_m = 0, tpa_p = 0;
     double rmin = 0, rcut = 0, skin = 0;
     mtp_precision prec = MTP_FP64;
     std::vector<double> xi, c, A, Ai;
-    std::vector<int> rows;
+    std::vector<int> rows, cols;
     bool active = false;
     bool nonlinear = false;
 };
@@ -1358,7 +1389,8 @@ bool parse_model_file(const char* path, ModelFile& mf) {
     if (!f) return false;
     Tokens t(f);
     long v = 0;
-    if (!t.key(kFileMagic) || !t.integer(kFileVersion, kFileVersion, v)) return false;
+    if (!t.key(kFileMagic) || !t.integer(1, kFileVersion, v)) return false;
+    const int version = (int)v;
     if (!t.key("lev_max") || !t.integer(2, 20, v) || v % 2) return false;
     mf.L = (int)v;
     if (!t.key("n_species") || !t.integer(1, mtp::kMaxSpecies, v)) return false;
@@ -1392,11 +1424,24 @@ bool parse_model_file(const char* path, ModelFile& mf) {
     const size_t m = (size_t)ops->M;
     const size_t nc = (size_t)mf.S * mf.S * ops->NMU * mf.NQ;
     if (!t.reals("xi", m, mf.xi) || !t.reals("c", nc, mf.c)) return false;
-    if (!t.key("active_set") || !t.integer(0, 2, v)) return false;
-    mf.active = v >= 1;
-    mf.nonlinear = v == 2;
+    if (version >= 2) {  // grade kind: 0, or 1 followed by the column count and the ascending columns
+        long kind = 0, ncol = 0;
+        if (!t.key("grade_kind") || !t.integer(0, 1, kind)) return false;
+        mf.nonlinear = kind == 1;
+        if (mf.nonlinear) {
+            if (!t.integer(1, (long)(m + nc), ncol)) return false;
+            mf.cols.resize(ncol);
+            for (long q = 0; q < ncol; ++q) {
+                long c = 0;
+                if (!t.integer(0, (long)(m + nc) - 1, c) || (q > 0 && c <= mf.cols[q - 1])) return false;
+                mf.cols[q] = (int)c;
+            }
+        }
+    }
+    if (!t.key("active_set") || !t.integer(0, 1, v)) return false;
+    mf.active = v == 1;
     if (mf.active) {
-        const size_t w = mf.nonlinear ? m + nc : m;
+        const size_t w = mf.nonlinear ? mf.cols.size() : m;
         if (!t.reals("A", w * w, mf.A) || !t.reals("A_inv", w * w, mf.Ai)) return false;
         long n = 0;
         if (!t.key("rows") || !t.integer(0, 1L << 30, n) || (size_t)n != w) return false;
@@ -1438,8 +1483,15 @@ mtp_status mtp_save(const mtp_model* M, const char* path) {
     std::fprintf(f, "neighbor_capacity %d\nthreads_per_atom %d %d\n", M->cap, M->tpa_moments, M->tpa_pairs);
     write_reals(f, "xi", M->xi.data(), M->xi.size());
     write_reals(f, "c", M->c.data(), M->c.size());
-    // 0: none; 1: linear active set (m x m); 2: nonlinear (Jacobian rows, (m + #c) x (m + #c))
-    std::fprintf(f, "active_set %d\n", M->has_active ? (M->nonlinear ? 2 : 1) : 0);
+    std::fprintf(f, "grade_kind %d", M->nonlinear ? 1 : 0);
+    if (M->nonlinear) {
+        std::fprintf(f, " %zu\n", M->gcols.size());
+        for (size_t q = 0; q < M->gcols.size(); ++q)
+            std::fprintf(f, "%d%c", M->gcols[q], (q + 1) % 16 == 0 || q + 1 == M->gcols.size() ? '\n' : ' ');
+    } else {
+        std::fprintf(f, "\n");
+    }
+    std::fprintf(f, "active_set %d\n", M->has_active ? 1 : 0);
     if (M->has_active) {
         write_reals(f, "A", A.data(), A.size());
         write_reals(f, "A_inv", Ai.data(), Ai.size());
@@ -1462,7 +1514,7 @@ mtp_status mtp_load(const char* path, mtp_model** out) {
     if (!st) st = mtp_set_skin(M, mf.skin);
     if (!st) st = mtp_set_neighbor_capacity(M, mf.cap);
     if (!st) st = mtp_set_threads_per_atom(M, mf.tpa_m, mf.tpa_p);
-    if (!st && mf.nonlinear) st = mtp_set_grade_kind(M, 1);
+    if (!st && mf.nonlinear) st = mtp_set_grade_kind(M, 1, (int)mf.cols.size(), mf.cols.data());
     if (!st && mf.active) {
         // A and A^-1 as saved (not recomputed), so that grades read back bit for bit
         const size_t bytes = sizeof(double) * mf.A.size();

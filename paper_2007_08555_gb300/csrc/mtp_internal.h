@@ -73,6 +73,9 @@ int launch_maxvol(int n, int m, const double* B, double* Bs, double* D, double* 
 int launch_invert(int m, const double* A, double* Ai, double* W, int* status, cudaStream_t st);
 template <class T>
 int launch_grade(int n, int m, const T* B, int ldb, const T* Ai, unsigned long long* gbits, cudaStream_t st);
+// out[r][q] = in[r][cols[q]] (rows x w_out from rows x w_in)
+int launch_gather_columns(int rows, int w_in, const double* in, int w_out, const int* cols, double* out,
+                          cudaStream_t st);
 
 // Tensor-core grade (mtp_grade_tc.cu): digits of (A D)^-1 prepared once per active set (m <= 480),
 // then gamma of n rows (gbits cleared by the launcher); return launches or -1.

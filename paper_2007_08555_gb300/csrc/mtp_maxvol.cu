@@ -17,6 +17,7 @@
 //   of b A^-1 gives gamma = +inf, so a broken configuration reads as extrapolating.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <algorithm>
 #include <mutex>
 #include "../../include/mtp.h"
 #include "mtp_common.cuh"
@@ -324,6 +325,23 @@ int launch_maxvol(int n, int m, const double* B, double* Bs, double* D, double* 
                   cudaStream_t st, int start_given) {
     k_maxvol<<<1, kMvThreads, 0, st>>>(n, m, B, Bs, D, W, perm, sel, A, Ai, C, tol, max_iter, status, swaps, gmax,
                                        start_given);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+__global__ void k_gather_columns(int rows, int w_in, const double* in, int w_out, const int* cols, double* out) {
+    const size_t total = (size_t)rows * w_out;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = e / w_out, q = e - r * w_out;
+        out[e] = in[r * w_in + cols[q]];
+    }
+}
+
+int launch_gather_columns(int rows, int w_in, const double* in, int w_out, const int* cols, double* out,
+                          cudaStream_t st) {
+    const size_t total = (size_t)rows * w_out;
+    if (total == 0) return 0;
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 32);
+    k_gather_columns<<<blocks, 256, 0, st>>>(rows, w_in, in, w_out, cols, out);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

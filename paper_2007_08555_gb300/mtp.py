@@ -77,7 +77,8 @@ _SIGS = {
     "mtp_save": (_I, [_P, ctypes.c_char_p]),
     "mtp_load": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "mtp_fp32_peak": (_I, [_I, ctypes.POINTER(_D)]),
-    "mtp_set_grade_kind": (_I, [_P, _I]),
+    "mtp_set_grade_kind": (_I, [_P, _I, _I, _P]),
+    "mtp_grade_columns": (_I, [_P, _P]),
     "mtp_relax_batch": (_I, [_P, _I, _I, _P, _P, _P, _P, _I, _D, _D, _D, _I, _D, _D, _P, _P, _P, _P]),
     "mtp_grade_width": (_I, [_P]),
     "mtp_jacobian_rows": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, _P]),
@@ -483,9 +484,13 @@ class Model:
                                       _ptr(status), _stream(None)), "mtp_relax_batch")
         return energy, steps, status
 
-    def set_grade_kind(self, nonlinear):
-        """0: grades of b rows (linear criterion); 1: grades of Jacobian rows dE/dtheta (nonlinear)."""
-        _check(load().mtp_set_grade_kind(self.h, int(nonlinear)), "mtp_set_grade_kind")
+    def set_grade_kind(self, nonlinear, cols=None):
+        """0: grades of b rows (linear criterion); 1: grades of Jacobian rows dE/dtheta (nonlinear) over
+        the parameter columns `cols` (ascending indices into [xi, c]; None = all)."""
+        c = None if cols is None else np.ascontiguousarray(cols, dtype=np.int32)
+        _check(load().mtp_set_grade_kind(self.h, int(nonlinear), 0 if c is None else len(c), _ptr(c)),
+               "mtp_set_grade_kind")
+        self.nonlinear = bool(nonlinear)
 
     @property
     def grade_width(self):
@@ -496,7 +501,8 @@ class Model:
         import torch
 
         K = cells.shape[0]
-        w = self.m + self.n_species ** 2 * self.n_mu * self.n_radial
+        nonlin = getattr(self, "nonlinear", self.grade_width != self.m)
+        w = self.grade_width if nonlin else self.m + self.n_species ** 2 * self.n_mu * self.n_radial
         rows = torch.empty((K, w), dtype=torch.float64, device=pos.device)
         _check(load().mtp_jacobian_rows(self.h, K, pos.shape[0], _ptr(cfg_off), _ptr(pos), _ptr(types), _ptr(cells),
                                         _ptr(rows), 0, _stream(None)), "mtp_jacobian_rows")

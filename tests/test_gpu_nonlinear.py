@@ -3,7 +3,8 @@
 * Jacobian rows dE(cfg)/dtheta = [b(cfg), dE/dc] of a batch of small cells equal the oracle's rows
   (forward-mode derivatives of E along every unit direction of c): 1e-9 relative in double precision,
   1e-4 of each row's norm in float;
-* with the nonlinear kind, MaxVol over the first 2 w rows (w = m + S^2 N_mu N_Q) picks the oracle's
+* with the nonlinear kind over the oracle's independent parameter columns (the full rows obey Euler's
+  theorem per radial block and are rank-deficient), MaxVol over the first 2 w rows picks the oracle's
   active set, and the grades of every row match the oracle's within the conditioning bound of
   tests/test_gpu_maxvol.py; grade requests of mtp_eval_batch are refused; a model file keeps the
   nonlinear active set bit for bit.
@@ -53,12 +54,15 @@ def test_jacobian_rows_match_oracle(gpu_lib, precision):
 def test_nonlinear_active_set_and_grades(gpu_lib, tmp_path):
     p, b = _case(100, 31)
     pot = oracle.Potential(p)
-    rows_o = nonlinear.jacobian_rows(pot, [b.config(k) for k in range(b.n_cfg)], p.xi, p.c)
+    full_o = nonlinear.jacobian_rows(pot, [b.config(k) for k in range(b.n_cfg)], p.xi, p.c)
+    cols = nonlinear.independent_columns(full_o)  # the full rows are rank-deficient (Euler)
+    rows_o = full_o[:, cols]
     model = mtp.Model.from_params(p, "fp64")
-    model.set_grade_kind(1)
+    model.set_grade_kind(1, cols)
     w = model.grade_width
-    assert w == model.m + p.c.size and 2 * w <= b.n_cfg
+    assert w == len(cols) < model.m + p.c.size and 2 * w <= b.n_cfg
     rows = model.jacobian_rows(*_batch(b))
+    assert rows.shape == (b.n_cfg, w)
     sel_o, swaps_o, _ = maxvol.maxvol(rows_o[:2 * w])
     sel, swaps, _ = model.select_active_set(rows[:2 * w].contiguous())
     assert sel.cpu().numpy().tolist() == sel_o.tolist() and swaps == swaps_o

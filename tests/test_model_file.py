@@ -50,7 +50,12 @@ def test_missing_file(lib, tmp_path):
 
 @pytest.mark.parametrize("case", [
     dict(magic="mtp-potential"),
-    dict(version=2),
+    dict(version=3),
+    dict(version=2),                                    # version 2 needs the grade_kind record
+    dict(version=2, active=["grade_kind 2", "active_set 0"]),
+    dict(version=2, active=["grade_kind 1 3", "0 5 5", "active_set 0"]),   # columns must ascend
+    dict(version=2, active=["grade_kind 1 2", "0 23", "active_set 0"]),    # m + #c = 23 columns
+    dict(version=2, active=["grade_kind 1 2", "0 1", "active_set 1", "A 9", "1 0 0 1"]),
     dict(lev=11),
     dict(lev=22),
     dict(S=9),

@@ -65,3 +65,35 @@ def test_c_part_satisfies_euler_homogeneity(setup):
         lhs = float(p.c.reshape(-1) @ row[m:])
         rhs = float(np.sum(n_alpha * p.xi * b))
         assert lhs == pytest.approx(rhs, rel=1e-10, abs=1e-12 * np.abs(p.xi * b).sum())
+
+
+def test_rows_satisfy_euler_per_radial_index_and_independent_columns_span_them():
+    """Every Jacobian row satisfies, for each radial index mu, sum over the block c[:, :, mu, :] of
+    c_k dE/dc_k = sum_alpha n_alpha(mu) xi_alpha b_alpha (Euler's theorem for the block scaling);
+    the independent columns drop at least one column per mu, are of full rank, and reproduce every
+    dropped column by least squares."""
+    L, S, NQ = 8, 2, 4
+    p = synth.random_params(L, S, NQ, 2.0, 5.0, len(levels.basis(L)), seed=31)
+    b = synth.small_cells(n_cfg=60, n_lo=6, n_hi=24, seed=32, max_species=S)
+    b.types = np.minimum(b.types, S - 1).astype(np.int32)
+    rows = nonlinear.jacobian_rows(oracle.Potential(p), [b.config(k) for k in range(b.n_cfg)], p.xi, p.c)
+    m = len(p.xi)
+    labels = synth.labels_from_level_table(levels.level_table(L))
+    n_mu = p.c.shape[2]
+    for mu in range(n_mu):
+        mask = np.zeros(p.c.shape)
+        mask[:, :, mu, :] = 1.0
+        nmu = np.array([sum(1 for (mm, _) in lab if mm == mu) for lab in labels])
+        lhs = rows[:, m:] @ (p.c * mask).reshape(-1)
+        rhs = rows[:, :m] @ (nmu * p.xi)
+        np.testing.assert_allclose(lhs, rhs, rtol=1e-9, atol=1e-12 * np.abs(rhs).max())
+    cols = nonlinear.independent_columns(rows)
+    w = rows.shape[1]
+    assert len(cols) <= w - n_mu and np.all(np.diff(cols) > 0)
+    kept = rows[:, cols] / np.abs(rows[:, cols]).max(0)
+    sv = np.linalg.svd(kept, compute_uv=False)
+    assert sv[-1] > 1e-9 * sv[0]
+    dropped = [k for k in range(w) if k not in set(cols.tolist())]
+    coef, *_ = np.linalg.lstsq(rows[:, cols], rows[:, dropped], rcond=None)
+    resid = np.abs(rows[:, cols] @ coef - rows[:, dropped]).max(0) / np.abs(rows[:, dropped]).max(0)
+    assert resid.max() <= 1e-8
