@@ -362,6 +362,23 @@ mtp_status mtp_relax_batch(mtp_model* model, int n_cfg, int n_atoms, const int32
                            double gamma_break, int max_steps, double dt, double dt_max, double* energy, int32_t* steps,
                            int32_t* status, void* stream);
 
+/*
+ * Training (Sec. 2.2: theta = (xi, c) minimises the loss of Eqs. 7, 11, 12; the paper names no
+ * optimiser): limited-memory BFGS from the model's current parameters, with the last `history`
+ * (s, y) pairs (two-loop recursion, H0 = s.y / y.y of the newest pair, before the first pair
+ * I / max(1, max |g|); a pair with s.y <= 1e-12 |s| |y| is not kept) and a backtracking line search
+ * (step 1 halved until L(theta + t d) <= L + 1e-4 t g.d, at most 40 halvings).  Every loss and
+ * gradient is mtp_param_grad() on the batch (layout and arguments as there, device arrays);
+ * direction, history and parameters stay on the device.  Stops when max |dL/dtheta| <= gtol
+ * (status 0), after max_iter iterations (1) or when the line search fails (2).  The model keeps the
+ * last accepted parameters.  losses ([max_iter + 1], host, L at each iterate), iterations and
+ * status (host) may be NULL.  Synchronous.
+ */
+mtp_status mtp_train(mtp_model* model, int n_cfg, int n_atoms, const int32_t* cfg_off, const double* pos,
+                     const int32_t* types, const double* cells, const double* e_ref, const double* f_ref,
+                     const double* w_ref, double w_e, double w_f, double w_s, int scaling, int history, int max_iter,
+                     double gtol, double* losses, int* iterations, int* status, void* stream);
+
 /* Wait for the model's work on `stream` and report errors detected on the device since the last
  * check (MTP_EOVERFLOW, MTP_EINVAL for bad species or shifts). */
 mtp_status mtp_sync(mtp_model* model, void* stream);

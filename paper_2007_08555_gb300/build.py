@@ -56,7 +56,7 @@ def build(levels=codegen.SUPPORTED_LEVELS, jobs=None, verbose=False) -> str:
     common = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "mtp.h"),
                                                          os.path.join(HERE, "codegen.py")]
     units = []
-    for name in ("mtp_api.cu", "mtp_nbr.cu", "mtp_maxvol.cu", "mtp_md.cu", "mtp_peak.cu", "mtp_grade_tc.cu", "mtp_relax.cu"):
+    for name in ("mtp_api.cu", "mtp_nbr.cu", "mtp_maxvol.cu", "mtp_md.cu", "mtp_peak.cu", "mtp_grade_tc.cu", "mtp_relax.cu", "mtp_train.cu"):
         units.append((os.path.join(CSRC, name), os.path.join(OUT, name.replace(".cu", ".o")), common, verbose))
     for L in levels:
         src = os.path.join(GEN, f"mtp_level_L{L}.cu")

@@ -76,6 +76,8 @@ struct mtp_model {
     bool nonlinear = false;
     std::vector<int> gcols;  // nonlinear kind: the parameter columns of the rows (indices into [xi, c])
     DevBuf j_rows, j_full, d_gcols;  // per-configuration dE/dc, full Jacobian rows, the column list
+    // training optimiser state (theta, trial point, gradients, direction, (s, y) history)
+    DevBuf t_theta, t_trial, t_g, t_gnew, t_d, t_S, t_Y, t_alpha, t_scalars, t_loss, t_order;
     // batched relaxation state
     DevBuf r_u, r_vu, r_D, r_vD, r_H0, r_H, r_x, r_dt, r_alpha, r_npos, r_status, r_steps, r_E, r_W, r_F, r_gamma,
         r_efinal;
@@ -441,6 +443,9 @@ void mtp_destroy(mtp_model* M) {
     M->g_dslots.release();
     M->g_dxt.release();
     M->epart.release();
+    for (DevBuf* b : {&M->t_theta, &M->t_trial, &M->t_g, &M->t_gnew, &M->t_d, &M->t_S, &M->t_Y, &M->t_alpha,
+                      &M->t_scalars, &M->t_loss, &M->t_order})
+        b->release();
     for (DevBuf* b : {&M->r_u, &M->r_vu, &M->r_D, &M->r_vD, &M->r_H0, &M->r_H, &M->r_x, &M->r_dt, &M->r_alpha,
                       &M->r_npos, &M->r_status, &M->r_steps, &M->r_E, &M->r_W, &M->r_F, &M->r_gamma, &M->r_efinal,
                       &M->j_rows})
@@ -878,6 +883,117 @@ mtp_status mtp_relax_batch(mtp_model* M, int K, int n, const int32_t* cfg_off, d
     if ((s = finish(M, st))) return s;
     if (status) std::copy(hs.begin(), hs.end(), status);
     if (steps) std::copy(hsteps.begin(), hsteps.end(), steps);
+    return MTP_OK;
+}
+
+namespace {
+// Installs theta + t d as the model's parameters (trial = that point); -1 on a launch error.
+int train_set(mtp_model* M, const double* theta, const double* d, double t, double* trial, cudaStream_t st) {
+    const int P = M->m + (int)M->c.size();
+    if (is_fp64(M))
+        return mtp::launch_train_set<double>(P, M->m, theta, d, t, trial, M->d_xi.as<double>(), M->d_c.as<double>(),
+                                             M->d_seed.as<double>(), M->V, M->d_basis_value.as<int>(), st);
+    return mtp::launch_train_set<float>(P, M->m, theta, d, t, trial, M->d_xi.as<float>(), M->d_c.as<float>(),
+                                        M->d_seed.as<float>(), M->V, M->d_basis_value.as<int>(), st);
+}
+}  // namespace
+
+mtp_status mtp_train(mtp_model* M, int K, int n, const int32_t* cfg_off, const double* pos, const int32_t* types,
+                     const double* cells, const double* e_ref, const double* f_ref, const double* w_ref, double w_e,
+                     double w_f, double w_s, int scaling, int history, int max_iter, double gtol, double* losses,
+                     int* iterations, int* status, void* stream) {
+    mtp_status s = check_batch(M, K, n, cfg_off, pos, cells);
+    if (s) return s;
+    if (n < 1 || !types || !e_ref || !f_ref || !w_ref || history < 1 || history > 64 || max_iter < 0 ||
+        !(gtol >= 0.0))
+        return MTP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = M->m, nc = (int)M->c.size(), P = m + nc;
+    const size_t Pd = sizeof(double) * (size_t)P;
+    if (M->t_theta.reserve(Pd) || M->t_trial.reserve(Pd) || M->t_g.reserve(Pd) || M->t_gnew.reserve(Pd) ||
+        M->t_d.reserve(Pd) || M->t_S.reserve(Pd * (history + 1)) || M->t_Y.reserve(Pd * (history + 1)) ||
+        M->t_alpha.reserve(sizeof(double) * history) || M->t_scalars.reserve(64) || M->t_loss.reserve(16) ||
+        M->t_order.reserve(sizeof(int) * history))
+        return MTP_ENOMEM;
+    double* theta = M->t_theta.as<double>();
+    double* trial = M->t_trial.as<double>();
+    double* g = M->t_g.as<double>();
+    double* gnew = M->t_gnew.as<double>();
+    double* d = M->t_d.as<double>();
+    double* sc = M->t_scalars.as<double>();
+    std::vector<double> th(P);
+    std::copy(M->xi.begin(), M->xi.end(), th.begin());
+    std::copy(M->c.begin(), M->c.end(), th.begin() + m);
+    cudaMemcpyAsync(theta, th.data(), Pd, cudaMemcpyHostToDevice, st);
+    M->g_sig.clear();
+    auto eval = [&](double* grad, double* L) -> mtp_status {  // loss (and gradient) at the installed parameters
+        mtp_status e = mtp_param_grad(M, K, n, cfg_off, pos, types, cells, e_ref, f_ref, w_ref, w_e, w_f, w_s, scaling,
+                                      M->t_loss.as<double>(), grad, grad ? grad + m : nullptr, 0, stream);
+        if (e) return e;
+        return cudaMemcpy(L, M->t_loss.p, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess ? MTP_OK : MTP_ECUDA;
+    };
+    if (train_set(M, theta, theta, 0.0, trial, st) < 0) return MTP_ECUDA;
+    double L = 0.0;
+    if ((s = eval(g, &L))) return s;
+    std::vector<double> hist{L};
+    std::vector<int> order;  // slots of the stored pairs, oldest first (history + 1 slots: one always free)
+    int st_code = 1, it = 0;
+    double h_sc[8];
+    for (; it < max_iter; ++it) {
+        cudaMemcpyAsync(M->t_order.p, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, st);
+        if (mtp::launch_lbfgs_direction(P, (int)order.size(), M->t_order.as<int>(), M->t_S.as<double>(),
+                                        M->t_Y.as<double>(), g, d, M->t_alpha.as<double>(), sc, st) < 0)
+            return MTP_ECUDA;
+        if (cudaMemcpy(h_sc, sc, sizeof(double) * 2, cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
+        const double gd = h_sc[0], gmax = h_sc[1];
+        if (gmax <= gtol) {
+            st_code = 0;
+            break;
+        }
+        double t = 1.0, Lnew = 0.0;
+        bool ok = false;
+        for (int h = 0; h <= 40 && !ok; ++h) {  // Armijo backtracking
+            if (train_set(M, theta, d, t, trial, st) < 0) return MTP_ECUDA;
+            if ((s = eval(nullptr, &Lnew))) return s;
+            if (Lnew <= L + 1e-4 * t * gd) ok = true; else t *= 0.5;
+        }
+        if (!ok) {
+            st_code = 2;
+            break;
+        }
+        if ((s = eval(gnew, &Lnew))) return s;  // gradient at the accepted point (installed last)
+        int slot = 0;
+        while (std::find(order.begin(), order.end(), slot) != order.end()) ++slot;
+        if (mtp::launch_lbfgs_pair(P, theta, trial, g, gnew, M->t_S.as<double>(), M->t_Y.as<double>(), slot, sc, st) < 0)
+            return MTP_ECUDA;
+        if (cudaMemcpy(h_sc, sc, sizeof(double) * 6, cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
+        if (h_sc[2] > 1e-12 * h_sc[3] * h_sc[4]) {  // keep the pair (else its slot stays free)
+            order.push_back(slot);
+            if ((int)order.size() > history) order.erase(order.begin());
+        }
+        std::swap(M->t_theta, M->t_trial);
+        std::swap(M->t_g, M->t_gnew);
+        theta = M->t_theta.as<double>();
+        trial = M->t_trial.as<double>();
+        g = M->t_g.as<double>();
+        gnew = M->t_gnew.as<double>();
+        L = Lnew;
+        hist.push_back(L);
+        if (h_sc[5] <= gtol) {
+            st_code = 0;
+            ++it;
+            break;
+        }
+    }
+    // the model keeps theta (also after a failed line search)
+    if (train_set(M, theta, theta, 0.0, trial, st) < 0) return MTP_ECUDA;
+    if (cudaMemcpy(th.data(), theta, Pd, cudaMemcpyDeviceToHost) != cudaSuccess) return MTP_ECUDA;
+    std::copy(th.begin(), th.begin() + m, M->xi.begin());
+    std::copy(th.begin() + m, th.end(), M->c.begin());
+    M->g_sig.clear();
+    if (losses) std::copy(hist.begin(), hist.end(), losses);
+    if (iterations) *iterations = it;
+    if (status) *status = st_code;
     return MTP_OK;
 }
 

@@ -105,6 +105,15 @@ int launch_relax_map(int n, int K, const int* off, const double* u, const double
                      double* H, cudaStream_t st);
 int launch_fire(const RelaxArgs& a, int K, int step, cudaStream_t st);
 
+// Training optimiser (mtp_train.cu): L-BFGS direction, parameter update, history pair.
+int launch_lbfgs_direction(int P, int k, const int* order, const double* S, const double* Y, const double* g,
+                           double* d, double* alpha, double* scalars, cudaStream_t st);
+template <class T>
+int launch_train_set(int P, int m, const double* theta, const double* d, double t, double* trial, T* xi, T* c, T* seed,
+                     int V, const int* basis_value, cudaStream_t st);
+int launch_lbfgs_pair(int P, const double* theta, const double* trial, const double* g, const double* g_new,
+                      double* S, double* Y, int slot, double* scalars, cudaStream_t st);
+
 // Molecular dynamics helpers (mtp_md.cu).  The refreshed r_ij go to nb.cx/cy/cz.
 int launch_update_pairs(const NbrState& nb, const double* x, cudaStream_t st, int n_sm);
 int launch_kick(int n, int S, double* v, const double* F, const int* types, const double* masses, double half_dt,

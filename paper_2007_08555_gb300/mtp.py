@@ -78,6 +78,8 @@ _SIGS = {
     "mtp_load": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "mtp_fp32_peak": (_I, [_I, ctypes.POINTER(_D)]),
     "mtp_set_grade_kind": (_I, [_P, _I, _I, _P]),
+    "mtp_train": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, _D, _D, _D, _I, _I, _I, _D, _P,
+                       ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),
     "mtp_grade_columns": (_I, [_P, _P]),
     "mtp_relax_batch": (_I, [_P, _I, _I, _P, _P, _P, _P, _I, _D, _D, _D, _I, _D, _D, _P, _P, _P, _P]),
     "mtp_grade_width": (_I, [_P]),
@@ -483,6 +485,20 @@ class Model:
                                       int(max_steps), float(dt), float(dt_max), _ptr(energy), _ptr(steps),
                                       _ptr(status), _stream(None)), "mtp_relax_batch")
         return energy, steps, status
+
+    def train(self, pos, types, cells, cfg_off, e_ref, f_ref, w_ref, weights=(1.0, 0.01, 0.001),
+              scaling="vibrations", history=10, max_iter=100, gtol=1e-8):
+        """L-BFGS on the training loss (mtp_train); the model keeps the fitted parameters.
+        Returns (losses per iterate, iterations, status: 0 converged, 1 max_iter, 2 line search)."""
+        kind = {"molecules": 0, "structures": 1, "vibrations": 2}[scaling] if isinstance(scaling, str) else scaling
+        losses = np.zeros(max_iter + 1)
+        it, stt = ctypes.c_int(), ctypes.c_int()
+        _check(load().mtp_train(self.h, cells.shape[0], pos.shape[0], _ptr(cfg_off), _ptr(pos), _ptr(types),
+                                _ptr(cells), _ptr(e_ref), _ptr(f_ref), _ptr(w_ref), float(weights[0]),
+                                float(weights[1]), float(weights[2]), int(kind), int(history), int(max_iter),
+                                float(gtol), _ptr(losses), ctypes.byref(it), ctypes.byref(stt), _stream(None)),
+               "mtp_train")
+        return losses[:it.value + 1], int(it.value), int(stt.value)
 
     def set_grade_kind(self, nonlinear, cols=None):
         """0: grades of b rows (linear criterion); 1: grades of Jacobian rows dE/dtheta (nonlinear) over
