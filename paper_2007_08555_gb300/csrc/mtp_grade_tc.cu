@@ -9,28 +9,39 @@
 //      columns of A D have maxima in [1/2, 1) (c = b' G exactly, and the scaling itself is exact);
 //   2. each row of b' is rounded to T_r,k = b'_rk 2^(56 - E_r) (an integer, |T| < 2^55, E_r from the
 //      row's largest exponent), each column of G to U_k,j = G_kj 2^(56 - F_j), and both integers are
-//      written as 8 base-128 digits q_s, p_t (balanced, |digit| <= 65: exact in BF16);
-//   3. for every digit pair (s, t) with s + t <= 9 the tensor cores form sum_k q_s,k p_t,k; pairs with
-//      the same g = s + t share one FP32 accumulator (8 groups, 8 x 64 TMEM columns).  Each group sum
-//      is an integer below 8 x 460 x 65^2 < 2^24, so the FP32 accumulation is exact;
+//      written as 8 base-128 digits q_t (of b') and p_s (of G) (balanced, |digit| <= 65: exact in BF16);
+//   3. for every digit pair (s, t) with s + t <= 7 the tensor cores form sum_k p_s,jk q_t,rk; pairs with
+//      the same g = s + t share one FP32 accumulator (8 groups).  Each group sum is an integer below
+//      8 x 460 x 65^2 < 2^24, so the FP32 accumulation is exact;
 //   4. the epilogue combines the groups exactly in 64-bit integers,
-//      sum_k T_r,k U_k,j ~ 2^49 (sum_g A_g 128^(9-g)),  c_rj = 2^(E_r + F_j - 63) (sum_g A_g 128^(9-g)),
-//      rounds once to float and keeps the row maximum of |c|.
-// Error: the rounding of b' and G to 56-bit grids and the dropped pairs (s + t >= 10) are each below
+//      sum_k T_r,k U_k,j = 2^49 sum_g A_g 128^(7-g) + (dropped pairs),
+//      c_rj = 2^(E_r + F_j - 63) sum_g A_g 128^(7-g), rounds once to float and keeps the row maximum.
+// Error: the rounding of b' and G to 56-bit grids and the dropped pairs (s + t >= 8) are each below
 // ~1e-15 of 2^(E_r + F_j) (the scales of the row and the column), comparable to a double-precision
 // product; the final rounding to float adds 2^-24 relative to gamma.  Rows holding NaN or inf get
 // gamma = +inf.
 //
-// Layout (shared memory, canonical K-major without swizzle): a plane of R rows x 64 k of BF16 is
-// made of 8 x 8 core matrices of 8 rows x 16 bytes; element (r, k) sits at
-// (r / 8) * 1024 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 bytes (k groups 128 bytes apart: the
-// descriptor's leading byte offset; row groups 1024 bytes apart: its stride byte offset).
+// Shapes: the digits of G are the MMA's A operand (M = 128 output columns j per tile, so m <= 128
+// takes one column tile), the digits of the rows of b its B operand (64 rows per tile).  The row
+// digit planes of a K chunk sit in shared memory behind three zero planes, z_0..z_2 = 0 and
+// z_(3+t) = q_t, each plane 64 rows x 32 k: for column digit s, the N = 256 window of planes
+// 3 + 4h - s .. 6 + 4h - s holds q_(g-s) for the groups g = 4h .. 4h + 3, so one MMA accumulates the
+// four pairs (s, g - s) into the TMEM columns of groups 4h .. 4h + 3 (TMEM lane = j, column
+// = 64 g + r).  Per K step of 16 that is 12 MMAs of 128 x 256 (h = 0 only for s <= 3).
 //
-// One persistent CTA per SM (256 threads, 195 KB of shared memory, all 512 TMEM columns) walks over
-// tiles of 128 rows x 64 output columns; per 64-wide K chunk: the column digits of G are copied from
-// global memory by the bulk-copy engine (cp.async.bulk, prepared once per active set), the threads
-// write the row digits, one thread issues the 36 x 4 MMAs and commits them to an mbarrier.  Every
-// wait on an mbarrier gives up after ~2 s, sets the error word and leaves the kernel.
+// Layout (shared memory, canonical K-major without swizzle): a plane of R rows x 32 k of BF16 is
+// made of core matrices of 8 rows x 16 bytes; element (r, k) sits at
+// (r / 8) * 512 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 bytes (k groups 128 bytes apart: the
+// descriptor's leading byte offset; row groups 512 bytes apart: its stride byte offset); planes of
+// the same shape follow each other, so consecutive planes form one taller operand.
+//
+// One persistent CTA per SM (256 threads, ~220 KB of shared memory, all 512 TMEM columns) walks over
+// row tiles of 64 (their exponents found once) and, for each, over the column tiles of 128; K is taken
+// in chunks of 32 through two stages of shared memory: per chunk the column digits of G are copied
+// from global memory by the bulk-copy engine (cp.async.bulk, prepared once per active set), the
+// threads write the row digits, and one thread issues the 24 MMAs and commits them to the stage's
+// mbarrier, so the digits of the next chunk are written while the tensor cores multiply.  Every wait
+// on an mbarrier gives up after ~2 s, sets the error word and leaves the kernel.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "mtp_common.cuh"
@@ -41,23 +52,29 @@ namespace mtp {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr int kTcRows = 128;                   // M of the MMA (rows of b per tile)
-constexpr int kTcCols = 64;                    // N of the MMA (output columns per tile)
-constexpr int kTcK = 64;                       // K per chunk
+constexpr int kTcJ = 128;                      // M of the MMA: output columns j per tile
+constexpr int kTcR = 64;                       // rows of b per tile (N = 4 x 64 per MMA)
+constexpr int kTcK = 32;                       // K per chunk (two MMAs of K = 16)
+constexpr int kStages = 2;                     // chunks in flight: digits of one while the other multiplies
 constexpr int kDigits = 8;                     // base-128 digits per operand
-constexpr int kGroups = 8;                     // g = s + t = 2 .. 9
-constexpr int kPlaneA = kTcRows * kTcK * 2;    // 16 KB
-constexpr int kPlaneB = kTcCols * kTcK * 2;    // 8 KB
-constexpr int kSmA = 0;
-constexpr int kSmB = kSmA + kDigits * kPlaneA;             // 128 KB of row digits
-constexpr int kSmMisc = kSmB + kDigits * kPlaneB;          // 64 KB of column digits
+constexpr int kGroups = 8;                     // g = s + t = 0 .. 7
+constexpr int kZero = 3;                       // zero planes in front of the row digits
+constexpr int kSbo = (kTcK / 8) * 128;         // bytes between 8-row groups of a plane
+constexpr int kPlaneG = kTcJ * kTcK * 2;       // 8 KB: one digit plane of G (A operand)
+constexpr int kPlaneQ = kTcR * kTcK * 2;       // 4 KB: one digit plane of the rows (B operand)
+constexpr int kStageG = kDigits * kPlaneG;     // 64 KB
+constexpr int kStageQ = (kZero + kDigits) * kPlaneQ;  // 44 KB
+constexpr int kSmG = 0;
+constexpr int kSmQ = kSmG + kStages * kStageG;
+constexpr int kSmMisc = kSmQ + kStages * kStageQ;  // barriers: [0,1] MMAs done per stage, [2,3] digits landed
 constexpr int kMaxK = 512;                                 // K padded to whole chunks
 constexpr int kMaxM = 480;  // exact FP32 group sums need 8 pairs x m x 65 x 64 < 2^24 (lev_max 20: m = 460)
 constexpr int kSmEk = kSmMisc + 64;                        // int [kMaxK]
-constexpr int kSmErow = kSmEk + 4 * kMaxK;                 // int [128]
-constexpr int kSmBad = kSmErow + 4 * kTcRows;              // int [128]
-constexpr int kSmScale = kSmBad + 4 * kTcRows;             // float [64]
-constexpr int kSmFlag = kSmScale + 4 * kTcCols;            // int
+constexpr int kSmErow = kSmEk + 4 * kMaxK;                 // int [64]
+constexpr int kSmBad = kSmErow + 4 * kTcR;                 // int [64]
+constexpr int kSmScale = kSmBad + 4 * kTcR;                // float [128]
+constexpr int kSmRed = kSmScale + 4 * kTcJ;                // [8][64] words: row-pass partials, row maxima
+constexpr int kSmFlag = kSmRed + 4 * 8 * kTcR;             // int
 constexpr int kSmTotal = kSmFlag + 16;
 constexpr int kSmAlloc = kSmTotal + 1024;                  // room to align the base to 1 KB
 constexpr long long kWaitNs = 2000000000ll;                // give up on an mbarrier after 2 s
@@ -75,14 +92,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFFu);           // start address
     d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;     // leading byte offset: next 8 k
-    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;    // stride byte offset: next 8 rows
+    d |= (uint64_t)(((uint32_t)kSbo >> 4) & 0x3FFFu) << 32;  // stride byte offset: next 8 rows
     d |= (uint64_t)1 << 46;                           // descriptor version of this architecture
     return d;                                         // base offset 0, no swizzle
 }
 
-// instruction descriptor, kind::f16: D in F32, A and B in BF16, both K-major, N = 64, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcCols >> 3) << 17) |
-                            ((uint32_t)(kTcRows >> 4) << 24);
+// instruction descriptor, kind::f16: D in F32, A and B in BF16, both K-major, N = 256, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((4 * kTcR) >> 3) << 17) |
+                            ((uint32_t)(kTcJ >> 4) << 24);
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -129,9 +146,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
         : "memory");
 }
 
-// Byte offset of element (r, k) in a plane (canonical K-major, no swizzle).
+// Byte offset of element (r, k) in a plane of kTcK columns (canonical K-major, no swizzle).
 __host__ __device__ __forceinline__ int plane_off(int r, int k) {
-    return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+    return (r >> 3) * kSbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
 // round(x 2^shift) for |x 2^shift| < 2^55 (the caller's choice of shift): an integer from the bits
@@ -158,25 +175,25 @@ __device__ __forceinline__ int exponent_of(double x) {
     return ex == 0 ? -(1 << 29) : ex - 1023;
 }
 
-// Eight base-128 digits of T (|T| < 2^55), most significant first; digits 2..8 balanced in
-// [-64, 63], the first takes what remains (|q0| <= 65).  32-bit arithmetic on the two halves.
+// NaN or infinity, from the exponent bits (integer work: no double-precision instruction)
+__device__ __forceinline__ bool nonfinite(double x) {
+    return (((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffu) == 0x7ffu;
+}
+
+// Eight base-128 digits of T (|T| < 2^55), most significant first: with U = T + 64 (1 + 128 + ...
+// + 128^7), which makes every balanced digit non-negative, digit s of T is digit s of U minus 64
+// (digits 2..8 in [-64, 63]); the first takes the rest of U (|q0| <= 65).  The two 28-bit halves
+// of U give the digits with independent 32-bit shifts.
 __device__ __forceinline__ void base128_digits(long long T, int* q) {
-    int lo = (int)(T & ((1ll << 28) - 1));  // [0, 2^28)
-    int hi = (int)(T >> 28);                // floor
+    constexpr long long kBias = 64ll * ((1ll << 56) - 1) / 127;  // 64 (1 + 128 + ... + 128^7)
+    const long long U = T + kBias;
+    const int lo = (int)(U & ((1ll << 28) - 1));
+    const int hi = (int)(U >> 28);
 #pragma unroll
-    for (int s = 7; s >= 4; --s) {
-        const int d = ((lo + 64) & 127) - 64;
-        q[s] = d;
-        lo = (lo - d) >> 7;
-    }
-    hi += lo;  // carry 0 or 1
+    for (int s = 4; s < 8; ++s) q[s] = ((lo >> (7 * (7 - s))) & 127) - 64;
 #pragma unroll
-    for (int s = 3; s >= 1; --s) {
-        const int d = ((hi + 64) & 127) - 64;
-        q[s] = d;
-        hi = (hi - d) >> 7;
-    }
-    q[0] = hi;
+    for (int s = 1; s < 4; ++s) q[s] = ((hi >> (7 * (3 - s))) & 127) - 64;
+    q[0] = (hi >> 21) - 64;
 }
 
 // BF16 bits of a small integer (|d| < 2^8: exact)
@@ -187,13 +204,13 @@ __device__ __forceinline__ uint32_t bf16_bits(int d) {
 
 // ------------------------------------------------------------------------------------------------
 // Preparation once per active set: column exponents e_k of D, column scales F_j of G = (A D)^-1 and
-// the digit planes of G in the layout of the MMA's B operand:
-//   digits[((ct * n_kc + kc) * 8 + t) * 4096 + plane_off(j % 64, k % 64) / 2] = digit t of G_kj.
+// the digit planes of G in the layout of the MMA's A operand:
+//   digits[((jt * n_kc + kc) * 8 + s) * 4096 + plane_off(j % 128, k % 32) / 2] = digit s of G_kj.
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_grade_tc_prep(int m, const double* A, const double* Ai, uint16_t* digits,
-                                                       int* ecol, float* cscale, int n_ct, int n_kc) {
+                                                       int* ecol, float* cscale, int n_jt, int n_kc) {
     __shared__ int s_e[kMaxK];
-    const int mpad = n_ct * kTcCols;
+    const int mpad = n_jt * kTcJ;
     // D_k = 2^e_k with max_r |A_rk| 2^e_k in [1/2, 1)
     for (int k = threadIdx.x; k < kMaxK; k += blockDim.x) {
         int e = 0;
@@ -203,7 +220,7 @@ __global__ void __launch_bounds__(512) k_grade_tc_prep(int m, const double* A, c
             e = mx > -(1 << 28) ? -(mx + 1) : 0;
         }
         s_e[k] = e;
-        if (k < mpad) ecol[k] = e;
+        if (k < n_kc * kTcK) ecol[k] = e;
     }
     __syncthreads();
     // G_kj = Ai_kj 2^(-e_k); F_j from the column's largest exponent (|G_kj| < 2^(F_j - 1))
@@ -216,14 +233,14 @@ __global__ void __launch_bounds__(512) k_grade_tc_prep(int m, const double* A, c
         }
         // 2^(F - 63); a column whose entries are all below 2^-60 contributes nothing measurable
         cscale[j] = j >= m || F <= -60 ? 0.f : (F >= 120 ? (float)INFINITY : __int_as_float((F - 63 + 127) << 23));
-        const int ct = j / kTcCols, jj = j % kTcCols;
+        const int jt = j / kTcJ, jj = j % kTcJ;
         for (int k = 0; k < n_kc * kTcK; ++k) {
             int q[kDigits] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (j < m && k < m) base128_digits(fixed_point(Ai[(size_t)k * m + j], 56 - F - s_e[k]), q);
             const int kc = k / kTcK, kk = k % kTcK;
-            const size_t base = ((size_t)(ct * n_kc + kc) * kDigits) * (kPlaneB / 2) + plane_off(jj, kk) / 2;
+            const size_t base = ((size_t)(jt * n_kc + kc) * kDigits) * (kPlaneG / 2) + plane_off(jj, kk) / 2;
 #pragma unroll
-            for (int t = 0; t < kDigits; ++t) digits[base + (size_t)t * (kPlaneB / 2)] = (uint16_t)bf16_bits(q[t]);
+            for (int t = 0; t < kDigits; ++t) digits[base + (size_t)t * (kPlaneG / 2)] = (uint16_t)bf16_bits(q[t]);
         }
     }
 }
@@ -246,24 +263,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grade_tc(const TcArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kSmMisc);  // [0] MMAs done, [1] column digits landed
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kSmMisc + 16);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kSmMisc);  // [s] MMAs of stage s done, [2 + s] its digits landed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kSmMisc + 32);
     int* s_ek = reinterpret_cast<int*>(sm + kSmEk);
     int* s_erow = reinterpret_cast<int*>(sm + kSmErow);
     int* s_bad = reinterpret_cast<int*>(sm + kSmBad);
     float* s_scale = reinterpret_cast<float*>(sm + kSmScale);
+    float* s_red = reinterpret_cast<float*>(sm + kSmRed);
     int* s_flag = reinterpret_cast<int*>(sm + kSmFlag);
-    const uint32_t bar_mma = smem_u32(&bars[0]), bar_cp = smem_u32(&bars[1]);
-    const uint32_t sA = smem_u32(sm + kSmA), sB = smem_u32(sm + kSmB);
+    const uint32_t sG = smem_u32(sm + kSmG), sQ = smem_u32(sm + kSmQ);
 
     if (tid == 0) {
-        mbar_init(bar_mma, 1);
-        mbar_init(bar_cp, 1);
+        for (int q = 0; q < 2 * kStages; ++q) mbar_init(smem_u32(&bars[q]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *s_flag = 0;
     }
     for (int k = tid; k < kMaxK; k += kTcThreads) s_ek[k] = k < a.n_kc * kTcK ? a.ecol[k] : 0;
-    if (warp == 0) {  // all 512 TMEM columns: 8 groups x 64 columns
+    // the zero planes in front of each stage's row digits (never written again)
+    for (int st = 0; st < kStages; ++st)
+        for (int e = tid; e < kZero * kPlaneQ / 16; e += kTcThreads)
+            reinterpret_cast<uint4*>(sm + kSmQ + st * kStageQ)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (warp == 0) {  // all 512 TMEM columns: 8 groups x 64 rows
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -272,107 +292,151 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grade_tc(const TcArgs a) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    uint32_t ph_mma = 0, ph_cp = 0;
+    uint32_t ph_mma[kStages] = {0u, 0u}, ph_cp[kStages] = {0u, 0u};
+    bool pending[kStages] = {false, false};  // MMAs committed on the stage's barrier, not yet waited for
     bool failed = false;
+    // every thread waits on a stage's barrier (consuming its phase); false after ~2 s
+    auto drain = [&](int st) -> bool {
+        if (!pending[st]) return true;
+        const bool ok = mbar_wait(smem_u32(&bars[st]), ph_mma[st]);
+        ph_mma[st] ^= 1u;
+        pending[st] = false;
+        return ok;
+    };
 
-    for (int tile = blockIdx.x; tile < a.n_tiles && !failed; tile += gridDim.x) {
-        const int rt = tile / a.n_ct, ct = tile - rt * a.n_ct;
-        const int row0 = rt * kTcRows;
-        // 1. row exponents E_r (|b'_rk| < 2^(E_r - 1)) and non-finite rows; warp w takes rows w, w + 8, ...
-        for (int rr = warp; rr < kTcRows; rr += kTcThreads / 32) {
-            const int r = row0 + rr;
-            int mx = -(1 << 29), bad = 0;
-            if (r < a.n) {
-                for (int k = lane; k < a.m; k += 32) {
-                    const double x = a.B[(size_t)r * a.ldb + k];
-                    bad |= !isfinite(x);
-                    mx = max(mx, exponent_of(x) + s_ek[k]);
-                }
-            }
-            mx = __reduce_max_sync(0xffffffffu, mx);
-            bad = __reduce_or_sync(0xffffffffu, bad);
-            if (lane == 0) {
-                s_erow[rr] = mx > -(1 << 28) ? mx + 2 : 0;
-                s_bad[rr] = bad;
+    const int n_rt = (a.n + kTcR - 1) / kTcR;
+    for (int rt = blockIdx.x; rt < n_rt && !failed; rt += gridDim.x) {
+      const int row0 = rt * kTcR;
+      // 1. row exponents E_r (|b'_rk| < 2^(E_r - 1)) and non-finite rows, once per row tile: four
+      //    threads per row, each scanning a quarter with 16 loads in flight
+      {
+        const int rr = tid & (kTcR - 1), part = tid >> 6;
+        const int r = row0 + rr;
+        int mx = -(1 << 29), bad = 0;
+        if (r < a.n) {
+            const int k0 = (part * a.m) / 4, k1 = ((part + 1) * a.m) / 4;
+            const double* row = a.B + (size_t)r * a.ldb;
+            for (int k = k0; k < k1; k += 16) {
+                double x[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) x[u] = k + u < k1 ? row[k + u] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    if (k + u < k1) {
+                        bad |= nonfinite(x[u]);
+                        mx = max(mx, exponent_of(x[u]) + s_ek[k + u]);
+                    }
             }
         }
-        if (tid < kTcCols) s_scale[tid] = a.cscale[ct * kTcCols + tid];
+        int* red = reinterpret_cast<int*>(s_red);  // [4][64]
+        red[part * kTcR + rr] = mx;
+        red[4 * kTcR + part * kTcR + rr] = bad;  // words 256 .. 511 of the 8 x 64
         __syncthreads();
+        if (part == 0) {
+            for (int q = 1; q < 4; ++q) {
+                mx = max(mx, red[q * kTcR + rr]);
+                bad |= red[4 * kTcR + q * kTcR + rr];
+            }
+            s_erow[rr] = mx > -(1 << 28) ? mx + 2 : 0;
+            s_bad[rr] = bad;
+        }
+        __syncthreads();
+      }
+      for (int jt = 0; jt < a.n_ct && !failed; ++jt) {
+        if (tid < kTcJ) s_scale[tid] = a.cscale[jt * kTcJ + tid];
         for (int kc = 0; kc < a.n_kc; ++kc) {
-            // 2. column digits of this (column tile, K chunk): 8 planes, 64 KB, by the bulk-copy engine
-            if (tid == 0) {
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_cp),
-                             "r"(kDigits * kPlaneB)
-                             : "memory");
-                const unsigned char* src =
-                    reinterpret_cast<const unsigned char*>(a.digits) + (size_t)(ct * a.n_kc + kc) * kDigits * kPlaneB;
-                for (int t = 0; t < kDigits; ++t)
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            sB + t * kPlaneB),
-                        "l"(src + (size_t)t * kPlaneB), "r"(kPlaneB), "r"(bar_cp)
-                        : "memory");
-            }
-            // 3. row digits: thread item = (row, 8 consecutive k), 8 planes of 16-byte stores
-            for (int item = tid; item < kTcRows * (kTcK / 8); item += kTcThreads) {
-                const int rr = item >> 3, kg = item & 7;
-                const int r = row0 + rr, k0 = kc * kTcK + kg * 8;
-                const int E = s_erow[rr];
-                uint32_t w[kDigits][4];
-#pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    int q0[kDigits], q1[kDigits];
-                    const int ka = k0 + e, kb = k0 + e + 1;
-                    const double xa = (r < a.n && ka < a.m) ? a.B[(size_t)r * a.ldb + ka] : 0.0;
-                    const double xb = (r < a.n && kb < a.m) ? a.B[(size_t)r * a.ldb + kb] : 0.0;
-                    base128_digits(fixed_point(xa, 56 - E + s_ek[ka]), q0);
-                    base128_digits(fixed_point(xb, 56 - E + s_ek[kb]), q1);
-#pragma unroll
-                    for (int s = 0; s < kDigits; ++s) w[s][e >> 1] = bf16_bits(q0[s]) | (bf16_bits(q1[s]) << 16);
-                }
-                const int off = plane_off(rr, kg * 8);
-#pragma unroll
-                for (int s = 0; s < kDigits; ++s)
-                    *reinterpret_cast<uint4*>(sm + kSmA + s * kPlaneA + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tc_fence_before();
-            __syncthreads();
-            // 4. one thread issues the MMAs: every digit pair (s, t) with s + t <= 9 into group s + t
-            if (tid == 0) {
-                tc_fence_after();
-                if (!mbar_wait(bar_cp, ph_cp)) {
-                    atomicOr(a.err, kErrTimeout);
-                    *s_flag = 1;
-                    mbar_wait(bar_cp, ph_cp);  // one more bounded wait for the copies in flight
-                } else {
-#pragma unroll 1
-                    for (int s = 0; s < kDigits; ++s) {
-#pragma unroll 1
-                        for (int t = 0; s + t < kGroups; ++t) {
-                            const int g = s + t;
-                            const uint32_t d = tmem + (uint32_t)(g * kTcCols);
-#pragma unroll
-                            for (int ks = 0; ks < kTcK / 16; ++ks) {
-                                // the first product into a group overwrites it (new tile), later ones add
-                                const uint32_t acc = (kc > 0 || ks > 0 || s > 0) ? 1u : 0u;
-                                mma_bf16(d, smem_desc(sA + s * kPlaneA + ks * 256), smem_desc(sB + t * kPlaneB + ks * 256),
-                                         acc);
-                            }
-                        }
-                    }
-                    mma_commit(bar_mma);
-                }
-            }
-            ph_cp ^= 1u;
+            const int st = kc & 1;
+            // 2. the stage's buffers are free once its previous MMAs (chunk kc - 2) have read them
+            if (!drain(st)) *s_flag = 1;
             __syncthreads();
             if (*s_flag) {
                 failed = true;
                 break;
             }
-            // 5. the MMAs have read the digit planes (and written TMEM) before anything is overwritten
-            const bool ok = mbar_wait(bar_mma, ph_mma);
-            ph_mma ^= 1u;
+            // 3. column digits of this (column tile, K chunk): 8 planes, 64 KB, by the bulk-copy engine
+            const uint32_t bar_cp = smem_u32(&bars[2 + st]);
+            if (tid == 0) {
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_cp), "r"(kStageG)
+                             : "memory");
+                const unsigned char* src =
+                    reinterpret_cast<const unsigned char*>(a.digits) + (size_t)(jt * a.n_kc + kc) * kStageG;
+                for (int h = 0; h < 2; ++h)
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            sG + st * kStageG + h * (kStageG / 2)),
+                        "l"(src + (size_t)h * (kStageG / 2)), "r"(kStageG / 2), "r"(bar_cp)
+                        : "memory");
+            }
+            // 4. row digits: thread = (row, 8 consecutive k), 8 planes of 16-byte stores behind the zeros
+            {
+                unsigned char* Qs = sm + kSmQ + st * kStageQ + kZero * kPlaneQ;
+                const int rr = tid / (kTcK / 8), kg = tid % (kTcK / 8);  // 64 rows x 4 k groups = 256 items
+                const int r = row0 + rr, k0 = kc * kTcK + kg * 8;
+                const int E = s_erow[rr];
+                uint32_t w[kDigits][4];
+                double x[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = (r < a.n && k0 + e < a.m) ? a.B[(size_t)r * a.ldb + k0 + e] : 0.0;
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    int q0[kDigits], q1[kDigits];
+                    base128_digits(fixed_point(x[e], 56 - E + s_ek[k0 + e]), q0);
+                    base128_digits(fixed_point(x[e + 1], 56 - E + s_ek[k0 + e + 1]), q1);
+#pragma unroll
+                    for (int q = 0; q < kDigits; ++q) w[q][e >> 1] = bf16_bits(q0[q]) | (bf16_bits(q1[q]) << 16);
+                }
+                const int off = plane_off(rr, kg * 8);
+#pragma unroll
+                for (int q = 0; q < kDigits; ++q)
+                    *reinterpret_cast<uint4*>(Qs + q * kPlaneQ + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            __syncthreads();
+            // 5. one thread issues the chunk's MMAs: for column digit s, the windows of row-digit planes
+            //    that line up the groups 0-3 (s <= 3) and 4-7; committed to the stage's barrier
+            if (tid == 0) {
+                tc_fence_after();
+                if (!mbar_wait(bar_cp, ph_cp[st])) {
+                    atomicOr(a.err, kErrTimeout);
+                    *s_flag = 1;
+                    mbar_wait(bar_cp, ph_cp[st]);  // one more bounded wait for the copy in flight
+                } else {
+                    // shared-memory addresses stay below 2^18, so offsets add to the descriptors'
+                    // start-address field (addr >> 4, 14 bits) without carries
+                    const uint64_t dg = smem_desc(sG + st * kStageG), dq = smem_desc(sQ + st * kStageQ);
+#pragma unroll
+                    for (int ks = 0; ks < kTcK / 16; ++ks) {
+#pragma unroll
+                        for (int sd = 0; sd < kDigits; ++sd) {
+                            const uint32_t acc = (kc > 0 || ks > 0 || sd > 0) ? 1u : 0u;  // first product overwrites
+                            const uint64_t da = dg + (uint64_t)((sd * kPlaneG + ks * 256) >> 4);
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                if (h == 0 && sd > 3) continue;
+                                const int zs = kZero + 4 * h - sd;  // first plane of the window
+                                mma_bf16(tmem + (uint32_t)(h * 4 * kTcR), da,
+                                         dq + (uint64_t)((zs * kPlaneQ + ks * 256) >> 4), acc);
+                            }
+                        }
+                    }
+                    mma_commit(smem_u32(&bars[st]));
+                }
+            }
+            ph_cp[st] ^= 1u;
+            pending[st] = true;
+            __syncthreads();
+            if (*s_flag) {
+                failed = true;
+                break;
+            }
+        }
+        if (failed) break;
+        // 6. all MMAs of the tile done (both stages' barriers consumed, in issue order)
+        {
+            const int last = (a.n_kc - 1) & 1;
+            bool ok = drain(last ^ 1);
+            ok = drain(last) && ok;
             if (!ok) *s_flag = 1;
             __syncthreads();
             if (*s_flag) {
@@ -381,28 +445,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grade_tc(const TcArgs a) {
                 break;
             }
         }
-        if (failed) break;
-        // 6. epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows), columns 32 (w / 4) .. + 31
+        // 7. epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its columns j) and rows 32 (w / 4) .. + 31
+        //    of the tile; the row maxima over j go through shared memory
         tc_fence_after();
         {
-            const int quarter = warp & 3, half = warp >> 2;
-            const int rr = quarter * 32 + lane;
-            const int r = row0 + rr;
-            float best = 0.f;
+            const int quarter = warp & 3, halfr = warp >> 2;
+            const int j = quarter * 32 + lane;
+            const float scale = s_scale[j];
 #pragma unroll 1
             for (int c16 = 0; c16 < 2; ++c16) {
-                const int col0 = half * 32 + c16 * 16;
+                const int r0 = halfr * 32 + c16 * 16;
                 uint32_t v[kGroups][16];
 #pragma unroll
                 for (int g = 0; g < kGroups; ++g)
-                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * kTcCols + col0), v[g]);
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * kTcR + r0), v[g]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int i = 0; i < 16; ++i) {
                     long long A[kGroups];
 #pragma unroll
-                    for (int g = 0; g < kGroups; ++g) A[g] = (long long)__float2int_rn(__uint_as_float(v[g][j]));
-                    // sum_g A_g 128^(7 - g') = H 2^28 + L, exactly (g' = 0 .. 7 for g = 2 .. 9)
+                    for (int g = 0; g < kGroups; ++g) A[g] = (long long)__float2int_rn(__uint_as_float(v[g][i]));
+                    // sum_g A_g 128^(7 - g) = H 2^28 + L, exactly
                     long long H = ((A[0] * 128 + A[1]) * 128 + A[2]) * 128 + A[3];
                     long long L = ((A[4] * 128 + A[5]) * 128 + A[6]) * 128 + A[7];
                     const long long Lh = L >> 28;
@@ -413,19 +476,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grade_tc(const TcArgs a) {
                         mag = fabsf(__ll2float_rn((H << 28) + Ll));
                     else
                         mag = fabsf(__fmaf_rn(__ll2float_rn(H), 268435456.0f, __ll2float_rn(Ll)));
-                    best = fmaxf(best, mag * s_scale[col0 + j]);
+                    // maximum over the warp's 32 columns j (non-negative floats order as their bits)
+                    float v = mag * scale;
+                    if (!(v >= 0.f)) v = 0.f;  // 0 x inf from a column scale beyond float range
+                    const unsigned mbits = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+                    if (lane == i) s_red[quarter * kTcR + r0 + i] = __uint_as_float(mbits);
                 }
             }
+        }
+        __syncthreads();
+        if (tid < kTcR) {
+            const int r = row0 + tid;
+            const float best = fmaxf(fmaxf(s_red[tid], s_red[kTcR + tid]), fmaxf(s_red[2 * kTcR + tid], s_red[3 * kTcR + tid]));
             if (r < a.n) {
-                double gam = scalbn((double)best, s_erow[rr]);
-                if (s_bad[rr]) gam = (double)INFINITY;
+                double gam = scalbn((double)best, s_erow[tid]);
+                if (s_bad[tid]) gam = (double)INFINITY;
                 if (gam > 0.0) atomicMax(&a.gbits[r], (unsigned long long)__double_as_longlong(gam));
             }
         }
-        // TMEM reads are complete before the next tile's MMAs overwrite it
+        // TMEM reads and the row maxima are complete before the next tile overwrites them
         tc_fence_before();
         __syncthreads();
+      }
     }
+    // leave no MMA behind (on a failure, bounded waits only), then free the tensor memory
+    drain(0);
+    drain(1);
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
@@ -436,15 +512,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grade_tc(const TcArgs a) {
 }  // namespace
 
 size_t grade_tc_digit_bytes(int m) {
-    const int n_ct = (m + kTcCols - 1) / kTcCols, n_kc = (m + kTcK - 1) / kTcK;
-    return (size_t)n_ct * n_kc * kDigits * kPlaneB;
+    const int n_jt = (m + kTcJ - 1) / kTcJ, n_kc = (m + kTcK - 1) / kTcK;
+    return (size_t)n_jt * n_kc * kStageG;
 }
 
 int launch_grade_tc_prep(int m, const double* A, const double* Ai, void* digits, int* ecol, float* cscale,
                          cudaStream_t st) {
     if (m < 1 || m > kMaxM) return -1;
-    const int n_ct = (m + kTcCols - 1) / kTcCols, n_kc = (m + kTcK - 1) / kTcK;
-    k_grade_tc_prep<<<1, 512, 0, st>>>(m, A, Ai, static_cast<uint16_t*>(digits), ecol, cscale, n_ct, n_kc);
+    const int n_jt = (m + kTcJ - 1) / kTcJ, n_kc = (m + kTcK - 1) / kTcK;
+    k_grade_tc_prep<<<1, 512, 0, st>>>(m, A, Ai, static_cast<uint16_t*>(digits), ecol, cscale, n_jt, n_kc);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -457,9 +533,9 @@ int launch_grade_tc(int n, int m, const double* B, int ldb, const void* digits, 
     a.n = n;
     a.m = m;
     a.ldb = ldb;
-    a.n_ct = (m + kTcCols - 1) / kTcCols;
+    a.n_ct = (m + kTcJ - 1) / kTcJ;
     a.n_kc = (m + kTcK - 1) / kTcK;
-    a.n_tiles = ((n + kTcRows - 1) / kTcRows) * a.n_ct;
+    a.n_tiles = ((n + kTcR - 1) / kTcR) * a.n_ct;
     a.B = B;
     a.digits = static_cast<const uint16_t*>(digits);
     a.ecol = ecol;
@@ -471,7 +547,8 @@ int launch_grade_tc(int n, int m, const double* B, int ldb, const void* digits, 
         cudaFuncSetAttribute(k_grade_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmAlloc);
         attr = true;
     }
-    const int grid = a.n_tiles < n_sm ? a.n_tiles : n_sm;
+    const int n_rt = (n + kTcR - 1) / kTcR;
+    const int grid = n_rt < n_sm ? n_rt : n_sm;
     k_grade_tc<<<grid, kTcThreads, kSmAlloc, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 2 : -1;
 }
