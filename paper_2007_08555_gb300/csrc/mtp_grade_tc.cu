@@ -51,7 +51,8 @@ namespace mtp {
 
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 288;                // 8 producer / epilogue warps and one MMA warp
+constexpr int kProd = 256;                     // producer threads
 constexpr int kTcJ = 128;                      // M of the MMA: output columns j per tile
 constexpr int kTcR = 64;                       // rows of b per tile (N = 4 x 64 per MMA)
 constexpr int kTcK = 32;                       // K per chunk (two MMAs of K = 16)
@@ -66,10 +67,12 @@ constexpr int kStageG = kDigits * kPlaneG;     // 64 KB
 constexpr int kStageQ = (kZero + kDigits) * kPlaneQ;  // 44 KB
 constexpr int kSmG = 0;
 constexpr int kSmQ = kSmG + kStages * kStageG;
-constexpr int kSmMisc = kSmQ + kStages * kStageQ;  // barriers: [0,1] MMAs done per stage, [2,3] digits landed
+// barriers: [0,1] MMAs of a stage done, [2,3] its column digits landed, [4,5] its row digits written,
+// [6] the epilogue has read TMEM
+constexpr int kSmMisc = kSmQ + kStages * kStageQ;
 constexpr int kMaxK = 512;                                 // K padded to whole chunks
 constexpr int kMaxM = 480;  // exact FP32 group sums need 8 pairs x m x 65 x 64 < 2^24 (lev_max 20: m = 460)
-constexpr int kSmEk = kSmMisc + 64;                        // int [kMaxK]
+constexpr int kSmEk = kSmMisc + 128;                       // int [kMaxK]
 constexpr int kSmErow = kSmEk + 4 * kMaxK;                 // int [64]
 constexpr int kSmBad = kSmErow + 4 * kTcR;                 // int [64]
 constexpr int kSmScale = kSmBad + 4 * kTcR;                // float [128]
@@ -259,24 +262,35 @@ struct TcArgs {
     int* err;
 };
 
+constexpr int kSmallSumsM = 127;
+constexpr unsigned long long kMagicSum = 0x4B400000ull * (128ull * 128 * 128 + 128 * 128 + 128 + 1);
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProd) : "memory"); }
+
+// Nine warps share the four sub-partitions of an SM (three on one of them), which caps a thread at
+// 168 registers.
 __global__ void __launch_bounds__(kTcThreads, 1) k_grade_tc(const TcArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kSmMisc);  // [s] MMAs of stage s done, [2 + s] its digits landed
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kSmMisc + 32);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kSmMisc);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kSmMisc + 64);
     int* s_ek = reinterpret_cast<int*>(sm + kSmEk);
     int* s_erow = reinterpret_cast<int*>(sm + kSmErow);
     int* s_bad = reinterpret_cast<int*>(sm + kSmBad);
     float* s_scale = reinterpret_cast<float*>(sm + kSmScale);
     float* s_red = reinterpret_cast<float*>(sm + kSmRed);
-    int* s_flag = reinterpret_cast<int*>(sm + kSmFlag);
     const uint32_t sG = smem_u32(sm + kSmG), sQ = smem_u32(sm + kSmQ);
+    auto bar = [&](int q) { return smem_u32(&bars[q]); };
 
     if (tid == 0) {
-        for (int q = 0; q < 2 * kStages; ++q) mbar_init(smem_u32(&bars[q]), 1);
+        for (int q = 0; q < 2 * kStages; ++q) mbar_init(bar(q), 1);   // MMA commits, bulk copies
+        for (int q = 0; q < kStages; ++q) mbar_init(bar(4 + q), kProd);  // row digits written
+        mbar_init(bar(6), kProd);                                         // TMEM read by the epilogue
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *s_flag = 0;
     }
     for (int k = tid; k < kMaxK; k += kTcThreads) s_ek[k] = k < a.n_kc * kTcK ? a.ecol[k] : 0;
     // the zero planes in front of each stage's row digits (never written again)
@@ -288,220 +302,250 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grade_tc(const TcArgs a) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the zero planes, for the tensor cores
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    uint32_t ph_mma[kStages] = {0u, 0u}, ph_cp[kStages] = {0u, 0u};
-    bool pending[kStages] = {false, false};  // MMAs committed on the stage's barrier, not yet waited for
-    bool failed = false;
-    // every thread waits on a stage's barrier (consuming its phase); false after ~2 s
-    auto drain = [&](int st) -> bool {
-        if (!pending[st]) return true;
-        const bool ok = mbar_wait(smem_u32(&bars[st]), ph_mma[st]);
-        ph_mma[st] ^= 1u;
-        pending[st] = false;
-        return ok;
-    };
-
     const int n_rt = (a.n + kTcR - 1) / kTcR;
-    for (int rt = blockIdx.x; rt < n_rt && !failed; rt += gridDim.x) {
-      const int row0 = rt * kTcR;
-      // 1. row exponents E_r (|b'_rk| < 2^(E_r - 1)) and non-finite rows, once per row tile: four
-      //    threads per row, each scanning a quarter with 16 loads in flight
-      {
-        const int rr = tid & (kTcR - 1), part = tid >> 6;
-        const int r = row0 + rr;
-        int mx = -(1 << 29), bad = 0;
-        if (r < a.n) {
-            const int k0 = (part * a.m) / 4, k1 = ((part + 1) * a.m) / 4;
-            const double* row = a.B + (size_t)r * a.ldb;
-            for (int k = k0; k < k1; k += 16) {
-                double x[16];
+
+    if (warp == kProd / 32) {
+        // ---- MMA warp, one thread: bulk copies of the column digits and the MMAs, chunk by chunk ----
+        if (lane == 0) {
+            // phase parities and pending commits, one bit per stage (registers, not local memory)
+            uint32_t ph_empty = 0u, ph_cp = 0u, ph_full = 0u, used = 0u, ph_tmem = 0u;
+            bool ok = true, first_tile = true;
+            for (int rt = blockIdx.x; rt < n_rt && ok; rt += gridDim.x) {
+                for (int jt = 0; jt < a.n_ct && ok; ++jt) {
+                    for (int kc = 0; kc < a.n_kc && ok; ++kc) {
+                        const int st = kc & 1;
+                        // the stage's previous MMAs have read its buffers
+                        if ((used >> st) & 1u) {
+                            ok = mbar_wait(bar(st), (ph_empty >> st) & 1u);
+                            ph_empty ^= 1u << st;
+                            used &= ~(1u << st);
+                            if (!ok) break;
+                        }
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(2 + st)),
+                                     "r"(kStageG)
+                                     : "memory");
+                        const unsigned char* src =
+                            reinterpret_cast<const unsigned char*>(a.digits) + (size_t)(jt * a.n_kc + kc) * kStageG;
+                        for (int h = 0; h < 2; ++h)
+                            asm volatile(
+                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                    sG + st * kStageG + h * (kStageG / 2)),
+                                "l"(src + (size_t)h * (kStageG / 2)), "r"(kStageG / 2), "r"(bar(2 + st))
+                                : "memory");
+                        // before the first MMA of a tile: the epilogue of the previous tile has read TMEM
+                        if (kc == 0 && !first_tile) {
+                            ok = mbar_wait(bar(6), ph_tmem);
+                            ph_tmem ^= 1u;
+                        }
+                        first_tile = false;
+                        // column digits landed and row digits written
+                        ok = ok && mbar_wait(bar(2 + st), (ph_cp >> st) & 1u);
+                        ph_cp ^= 1u << st;
+                        ok = ok && mbar_wait(bar(4 + st), (ph_full >> st) & 1u);
+                        ph_full ^= 1u << st;
+                        if (!ok) break;
+                        tc_fence_after();
+                        // shared-memory addresses stay below 2^18, so offsets add to the descriptors'
+                        // start-address field (addr >> 4, 14 bits) without carries
+                        const uint64_t dg = smem_desc(sG + st * kStageG), dq = smem_desc(sQ + st * kStageQ);
 #pragma unroll
-                for (int u = 0; u < 16; ++u) x[u] = k + u < k1 ? row[k + u] : 0.0;
+                        for (int ks = 0; ks < kTcK / 16; ++ks) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    if (k + u < k1) {
-                        bad |= nonfinite(x[u]);
-                        mx = max(mx, exponent_of(x[u]) + s_ek[k + u]);
-                    }
-            }
-        }
-        int* red = reinterpret_cast<int*>(s_red);  // [4][64]
-        red[part * kTcR + rr] = mx;
-        red[4 * kTcR + part * kTcR + rr] = bad;  // words 256 .. 511 of the 8 x 64
-        __syncthreads();
-        if (part == 0) {
-            for (int q = 1; q < 4; ++q) {
-                mx = max(mx, red[q * kTcR + rr]);
-                bad |= red[4 * kTcR + q * kTcR + rr];
-            }
-            s_erow[rr] = mx > -(1 << 28) ? mx + 2 : 0;
-            s_bad[rr] = bad;
-        }
-        __syncthreads();
-      }
-      for (int jt = 0; jt < a.n_ct && !failed; ++jt) {
-        if (tid < kTcJ) s_scale[tid] = a.cscale[jt * kTcJ + tid];
-        for (int kc = 0; kc < a.n_kc; ++kc) {
-            const int st = kc & 1;
-            // 2. the stage's buffers are free once its previous MMAs (chunk kc - 2) have read them
-            if (!drain(st)) *s_flag = 1;
-            __syncthreads();
-            if (*s_flag) {
-                failed = true;
-                break;
-            }
-            // 3. column digits of this (column tile, K chunk): 8 planes, 64 KB, by the bulk-copy engine
-            const uint32_t bar_cp = smem_u32(&bars[2 + st]);
-            if (tid == 0) {
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_cp), "r"(kStageG)
-                             : "memory");
-                const unsigned char* src =
-                    reinterpret_cast<const unsigned char*>(a.digits) + (size_t)(jt * a.n_kc + kc) * kStageG;
-                for (int h = 0; h < 2; ++h)
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            sG + st * kStageG + h * (kStageG / 2)),
-                        "l"(src + (size_t)h * (kStageG / 2)), "r"(kStageG / 2), "r"(bar_cp)
-                        : "memory");
-            }
-            // 4. row digits: thread = (row, 8 consecutive k), 8 planes of 16-byte stores behind the zeros
-            {
-                unsigned char* Qs = sm + kSmQ + st * kStageQ + kZero * kPlaneQ;
-                const int rr = tid / (kTcK / 8), kg = tid % (kTcK / 8);  // 64 rows x 4 k groups = 256 items
-                const int r = row0 + rr, k0 = kc * kTcK + kg * 8;
-                const int E = s_erow[rr];
-                uint32_t w[kDigits][4];
-                double x[8];
+                            for (int sd = 0; sd < kDigits; ++sd) {
+                                const uint32_t acc = (kc > 0 || ks > 0 || sd > 0) ? 1u : 0u;  // first overwrites
+                                const uint64_t da = dg + (uint64_t)((sd * kPlaneG + ks * 256) >> 4);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = (r < a.n && k0 + e < a.m) ? a.B[(size_t)r * a.ldb + k0 + e] : 0.0;
-#pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    int q0[kDigits], q1[kDigits];
-                    base128_digits(fixed_point(x[e], 56 - E + s_ek[k0 + e]), q0);
-                    base128_digits(fixed_point(x[e + 1], 56 - E + s_ek[k0 + e + 1]), q1);
-#pragma unroll
-                    for (int q = 0; q < kDigits; ++q) w[q][e >> 1] = bf16_bits(q0[q]) | (bf16_bits(q1[q]) << 16);
-                }
-                const int off = plane_off(rr, kg * 8);
-#pragma unroll
-                for (int q = 0; q < kDigits; ++q)
-                    *reinterpret_cast<uint4*>(Qs + q * kPlaneQ + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tc_fence_before();
-            __syncthreads();
-            // 5. one thread issues the chunk's MMAs: for column digit s, the windows of row-digit planes
-            //    that line up the groups 0-3 (s <= 3) and 4-7; committed to the stage's barrier
-            if (tid == 0) {
-                tc_fence_after();
-                if (!mbar_wait(bar_cp, ph_cp[st])) {
-                    atomicOr(a.err, kErrTimeout);
-                    *s_flag = 1;
-                    mbar_wait(bar_cp, ph_cp[st]);  // one more bounded wait for the copy in flight
-                } else {
-                    // shared-memory addresses stay below 2^18, so offsets add to the descriptors'
-                    // start-address field (addr >> 4, 14 bits) without carries
-                    const uint64_t dg = smem_desc(sG + st * kStageG), dq = smem_desc(sQ + st * kStageQ);
-#pragma unroll
-                    for (int ks = 0; ks < kTcK / 16; ++ks) {
-#pragma unroll
-                        for (int sd = 0; sd < kDigits; ++sd) {
-                            const uint32_t acc = (kc > 0 || ks > 0 || sd > 0) ? 1u : 0u;  // first product overwrites
-                            const uint64_t da = dg + (uint64_t)((sd * kPlaneG + ks * 256) >> 4);
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                if (h == 0 && sd > 3) continue;
-                                const int zs = kZero + 4 * h - sd;  // first plane of the window
-                                mma_bf16(tmem + (uint32_t)(h * 4 * kTcR), da,
-                                         dq + (uint64_t)((zs * kPlaneQ + ks * 256) >> 4), acc);
+                                for (int h = 0; h < 2; ++h) {
+                                    if (h == 0 && sd > 3) continue;
+                                    const int zs = kZero + 4 * h - sd;  // first plane of the window
+                                    mma_bf16(tmem + (uint32_t)(h * 4 * kTcR), da,
+                                             dq + (uint64_t)((zs * kPlaneQ + ks * 256) >> 4), acc);
+                                }
                             }
                         }
+                        mma_commit(bar(st));  // frees the stage; the tile's last commit releases the epilogue
+                        used |= 1u << st;
                     }
-                    mma_commit(smem_u32(&bars[st]));
                 }
             }
-            ph_cp[st] ^= 1u;
-            pending[st] = true;
-            __syncthreads();
-            if (*s_flag) {
-                failed = true;
-                break;
-            }
+            if (!ok) atomicOr(a.err, kErrTimeout);
+            // leave no MMA or copy behind before the tensor memory is freed (bounded waits)
+            for (int st = 0; st < kStages; ++st)
+                if ((used >> st) & 1u) mbar_wait(bar(st), (ph_empty >> st) & 1u);
         }
-        if (failed) break;
-        // 6. all MMAs of the tile done (both stages' barriers consumed, in issue order)
-        {
-            const int last = (a.n_kc - 1) & 1;
-            bool ok = drain(last ^ 1);
-            ok = drain(last) && ok;
-            if (!ok) *s_flag = 1;
-            __syncthreads();
-            if (*s_flag) {
-                if (tid == 0) atomicOr(a.err, kErrTimeout);
-                failed = true;
-                break;
+        __syncwarp();
+    } else {
+        // ---- producers: row exponents, row digits, epilogue.  Their control flow never depends on a
+        // wait's outcome, so every producer reaches every producer barrier; after a failed wait a
+        // thread skips the remaining waits and the kernel's results are void (error word set). ----
+        bool ok = true;
+        uint32_t ph_done = 0u;  // phase parity of each stage's MMA barrier, one bit per stage
+        // thread = (row rr of the tile, k group kg: 8 consecutive k of every chunk); the four threads of
+        // a row are adjacent lanes
+        const int rr = tid >> 2, kg = tid & 3;
+        // Row exponents E_r (|b'_rk| < 2^(E_r - 1)) and non-finite rows of row tile t, combined over the
+        // row's four threads by shuffles.  Called for the next row tile while the tensor cores finish
+        // the current one.
+        auto row_pass = [&](int t, int& E_out, int& bad_out) {
+            const int r = t * kTcR + rr;
+            const double* brow = a.B + (size_t)(r < a.n ? r : 0) * a.ldb;
+            int mx = -(1 << 29), bad = 0;
+            for (int c = 0; c < a.n_kc; c += 2) {
+                double x[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int k = (c + (u >> 3)) * kTcK + kg * 8 + (u & 7);
+                    x[u] = (r < a.n && k < a.m) ? brow[k] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int k = (c + (u >> 3)) * kTcK + kg * 8 + (u & 7);
+                    if (k < a.m) {
+                        bad |= nonfinite(x[u]);
+                        mx = max(mx, exponent_of(x[u]) + s_ek[k]);
+                    }
+                }
             }
-        }
-        // 7. epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its columns j) and rows 32 (w / 4) .. + 31
-        //    of the tile; the row maxima over j go through shared memory
-        tc_fence_after();
-        {
-            const int quarter = warp & 3, halfr = warp >> 2;
-            const int j = quarter * 32 + lane;
-            const float scale = s_scale[j];
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+            bad |= __shfl_xor_sync(0xffffffffu, bad, 1);
+            bad |= __shfl_xor_sync(0xffffffffu, bad, 2);
+            E_out = mx > -(1 << 28) ? mx + 2 : 0;
+            bad_out = bad;
+        };
+        int E = 0, bad_row = 0;
+        if (blockIdx.x < n_rt) row_pass(blockIdx.x, E, bad_row);
+        for (int rt = blockIdx.x; rt < n_rt; rt += gridDim.x) {
+          const int row0 = rt * kTcR;
+          const int r = row0 + rr;
+          const double* brow = a.B + (size_t)(r < a.n ? r : 0) * a.ldb;
+          if (kg == 0) {  // for the tile's final step (the previous one ended with a producer barrier)
+              s_erow[rr] = E;
+              s_bad[rr] = bad_row;
+          }
+          for (int jt = 0; jt < a.n_ct; ++jt) {
+            if (tid < kTcJ) s_scale[tid] = a.cscale[jt * kTcJ + tid];
+            producers_sync();  // row exponents and column scales visible to all producers
+            for (int kc = 0; kc < a.n_kc; ++kc) {
+                const int st = kc & 1;
+                // 2. the stage is free once the MMAs that read it (two chunks back) are done
+                if (kc >= 2) {
+                    ok = ok && mbar_wait(bar(st), (ph_done >> st) & 1u);
+                    ph_done ^= 1u << st;
+                }
+                // 3. row digits: thread = (row, 8 consecutive k), 8 planes of 16-byte stores behind the zeros
+                {
+                    unsigned char* Qs = sm + kSmQ + st * kStageQ + kZero * kPlaneQ;
+                    const int k0 = kc * kTcK + kg * 8;
+                    uint32_t w[kDigits][4];
+                    double x[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) x[e] = (r < a.n && k0 + e < a.m) ? brow[k0 + e] : 0.0;
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        int q0[kDigits], q1[kDigits];
+                        base128_digits(fixed_point(x[e], 56 - E + s_ek[k0 + e]), q0);
+                        base128_digits(fixed_point(x[e + 1], 56 - E + s_ek[k0 + e + 1]), q1);
+#pragma unroll
+                        for (int q = 0; q < kDigits; ++q) w[q][e >> 1] = bf16_bits(q0[q]) | (bf16_bits(q1[q]) << 16);
+                    }
+                    const int off = plane_off(rr, kg * 8);
+#pragma unroll
+                    for (int q = 0; q < kDigits; ++q)
+                        *reinterpret_cast<uint4*>(Qs + q * kPlaneQ + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(bar(4 + st));  // this thread's digits of the chunk are written
+            }
+            // the next row tile's exponents, while the tensor cores finish this one
+            if (jt == a.n_ct - 1 && rt + (int)gridDim.x < n_rt) row_pass(rt + gridDim.x, E, bad_row);
+            // 4. the tile's MMAs are done: the commits of its last two chunks (one per stage)
+            for (int kc = a.n_kc > 2 ? a.n_kc - 2 : 0; kc < a.n_kc; ++kc) {
+                const int st = kc & 1;
+                ok = ok && mbar_wait(bar(st), (ph_done >> st) & 1u);
+                ph_done ^= 1u << st;
+            }
+            // 5. epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its columns j) and rows
+            //    32 (w / 4) .. + 31 of the tile; the row maxima over j go through shared memory
+            tc_fence_after();
+            {
+                const int quarter = warp & 3, halfr = warp >> 2;
+                const int j = quarter * 32 + lane;
+                // group sums stay below 2^22 for m <= 127: 8 pairs x m x 65 x 64 (digit bounds)
+                const bool small_sums = a.m <= kSmallSumsM;
+                const float scale = s_scale[j];
 #pragma unroll 1
-            for (int c16 = 0; c16 < 2; ++c16) {
-                const int r0 = halfr * 32 + c16 * 16;
-                uint32_t v[kGroups][16];
+                for (int c16 = 0; c16 < 2; ++c16) {
+                    const int r0 = halfr * 32 + c16 * 16;
+                    uint32_t v[kGroups][16];
 #pragma unroll
-                for (int g = 0; g < kGroups; ++g)
-                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * kTcR + r0), v[g]);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    for (int g = 0; g < kGroups; ++g)
+                        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * kTcR + r0), v[g]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (c16 == 1) {  // TMEM fully read: the next tile's MMAs may overwrite it
+                        tc_fence_before();
+                        mbar_arrive(bar(6));
+                    }
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    long long A[kGroups];
+                    for (int i = 0; i < 16; ++i) {
+                        // sum_g A_g 128^(7 - g) = H 2^28 + L, exactly
+                        long long H, L;
+                        if (small_sums) {
+                            // A_g + 1.5 2^23 is exact in [2^23, 2^24) and its bits are 0x4B400000 + A_g;
+                            // the offsets of the four groups of a half are subtracted as one constant
+                            unsigned long long h = 0ull - kMagicSum, l = 0ull - kMagicSum;
 #pragma unroll
-                    for (int g = 0; g < kGroups; ++g) A[g] = (long long)__float2int_rn(__uint_as_float(v[g][i]));
-                    // sum_g A_g 128^(7 - g) = H 2^28 + L, exactly
-                    long long H = ((A[0] * 128 + A[1]) * 128 + A[2]) * 128 + A[3];
-                    long long L = ((A[4] * 128 + A[5]) * 128 + A[6]) * 128 + A[7];
-                    const long long Lh = L >> 28;
-                    const long long Ll = L - (Lh << 28);  // [0, 2^28)
-                    H += Lh;
-                    float mag;
-                    if (H > -(1ll << 34) && H < (1ll << 34))
-                        mag = fabsf(__ll2float_rn((H << 28) + Ll));
-                    else
-                        mag = fabsf(__fmaf_rn(__ll2float_rn(H), 268435456.0f, __ll2float_rn(Ll)));
-                    // maximum over the warp's 32 columns j (non-negative floats order as their bits)
-                    float v = mag * scale;
-                    if (!(v >= 0.f)) v = 0.f;  // 0 x inf from a column scale beyond float range
-                    const unsigned mbits = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
-                    if (lane == i) s_red[quarter * kTcR + r0 + i] = __uint_as_float(mbits);
+                            for (int g = 0; g < 4; ++g) {
+                                const uint32_t ug = __float_as_uint(__uint_as_float(v[g][i]) + 12582912.0f);
+                                const uint32_t ul = __float_as_uint(__uint_as_float(v[g + 4][i]) + 12582912.0f);
+                                h += (unsigned long long)ug << (7 * (3 - g));
+                                l += (unsigned long long)ul << (7 * (3 - g));
+                            }
+                            H = (long long)h;
+                            L = (long long)l;
+                        } else {
+                            long long A[kGroups];
+#pragma unroll
+                            for (int g = 0; g < kGroups; ++g) A[g] = (long long)__float2int_rn(__uint_as_float(v[g][i]));
+                            H = ((A[0] * 128 + A[1]) * 128 + A[2]) * 128 + A[3];
+                            L = ((A[4] * 128 + A[5]) * 128 + A[6]) * 128 + A[7];
+                        }
+                        const long long Lh = L >> 28;
+                        const long long Ll = L - (Lh << 28);  // [0, 2^28)
+                        H += Lh;
+                        float mag;
+                        if (H > -(1ll << 34) && H < (1ll << 34))
+                            mag = fabsf(__ll2float_rn((H << 28) + Ll));
+                        else
+                            mag = fabsf(__fmaf_rn(__ll2float_rn(H), 268435456.0f, __ll2float_rn(Ll)));
+                        float v2 = mag * scale;
+                        if (!(v2 >= 0.f)) v2 = 0.f;  // 0 x inf from a column scale beyond float range
+                        // maximum over the warp's 32 columns j (non-negative floats order as their bits)
+                        const unsigned mbits = __reduce_max_sync(0xffffffffu, __float_as_uint(v2));
+                        if (lane == i) s_red[quarter * kTcR + r0 + i] = __uint_as_float(mbits);
+                    }
                 }
             }
-        }
-        __syncthreads();
-        if (tid < kTcR) {
-            const int r = row0 + tid;
-            const float best = fmaxf(fmaxf(s_red[tid], s_red[kTcR + tid]), fmaxf(s_red[2 * kTcR + tid], s_red[3 * kTcR + tid]));
-            if (r < a.n) {
-                double gam = scalbn((double)best, s_erow[tid]);
-                if (s_bad[tid]) gam = (double)INFINITY;
-                if (gam > 0.0) atomicMax(&a.gbits[r], (unsigned long long)__double_as_longlong(gam));
+            producers_sync();
+            if (tid < kTcR) {
+                const int r = row0 + tid;
+                const float best = fmaxf(fmaxf(s_red[tid], s_red[kTcR + tid]), fmaxf(s_red[2 * kTcR + tid], s_red[3 * kTcR + tid]));
+                if (r < a.n && ok) {
+                    double gam = scalbn((double)best, s_erow[tid]);
+                    if (s_bad[tid]) gam = (double)INFINITY;
+                    if (gam > 0.0) atomicMax(&a.gbits[r], (unsigned long long)__double_as_longlong(gam));
+                }
             }
+            producers_sync();
+          }
         }
-        // TMEM reads and the row maxima are complete before the next tile overwrites them
-        tc_fence_before();
-        __syncthreads();
-      }
+        if (!ok) atomicOr(a.err, kErrTimeout);
     }
-    // leave no MMA behind (on a failure, bounded waits only), then free the tensor memory
-    drain(0);
-    drain(1);
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
