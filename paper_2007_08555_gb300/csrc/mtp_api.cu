@@ -243,11 +243,8 @@ mtp_status fill_ctx(mtp_model* M, int K, int n, const int* cfg_off, const int* t
     a.cfg_of = M->nb.cfg_of.as<int>();
     a.cfg_off = cfg_off;
     a.count = M->nb.count.as<int>();
-    a.jz = M->nb.jz.as<int>();
+    a.pr = M->reused ? M->nb.cpr.as<mtp::PairRec<T>>() : M->nb.pr.as<mtp::PairRec<T>>();
     a.rev = M->nb.rev.as<int>();
-    a.rx = M->reused ? M->nb.cx.as<T>() : M->nb.rx.as<T>();
-    a.ry = M->reused ? M->nb.cy.as<T>() : M->nb.ry.as<T>();
-    a.rz = M->reused ? M->nb.cz.as<T>() : M->nb.rz.as<T>();
     a.c = M->d_c.as<T>();
     a.xi = M->d_xi.as<T>();
     a.seed = M->d_seed.as<T>();
@@ -428,12 +425,12 @@ void mtp_destroy(mtp_model* M) {
                       &M->d_adj_ops, &M->d_adj_layers, &M->d_weights, &M->mom,
                       &M->adjm, &M->gx, &M->s_off, &M->s_pos, &M->s_types, &M->s_cells,
                       &M->s_energy, &M->s_forces, &M->s_virial, &M->s_site, &M->s_brows, &M->s_batoms,
-                      &M->nb.count, &M->nb.jz, &M->nb.rev, &M->nb.rx, &M->nb.ry, &M->nb.rz,
+                      &M->nb.count, &M->nb.pr, &M->nb.rev,
                       &M->nb.cfg_of, &M->nb.desc, &M->nb.atom_bin, &M->nb.atom_wrap, &M->nb.atom_local,
-                      &M->nb.bin_count, &M->nb.bin_start, &M->nb.bin_fill, &M->nb.bin_atoms, &M->nb.counters,
+                      &M->nb.bin_count, &M->nb.bin_start, &M->nb.atom_slot, &M->nb.bin_atoms, &M->nb.counters,
                       &M->nb.err, &M->g_energy, &M->g_forces, &M->g_virial, &M->g_D, &M->g_eps, &M->g_ew,
                       &M->g_momt, &M->g_adjmt, &M->g_out, &M->g_refs, &M->md_F, &M->md_scalars, &M->md_masses,
-                      &M->md_flag, &M->nb.x0, &M->nb.cx, &M->nb.cy, &M->nb.cz, &M->d_A, &M->d_Ai, &M->mv_Bs, &M->mv_D, &M->mv_W, &M->mv_perm, &M->mv_sel,
+                      &M->md_flag, &M->nb.x0, &M->nb.cpr, &M->d_A, &M->d_Ai, &M->mv_Bs, &M->mv_D, &M->mv_W, &M->mv_perm, &M->mv_sel,
                       &M->mv_C, &M->mv_status, &M->mv_swaps, &M->mv_gmax, &M->s_rows, &M->s_gamma, &M->g_brows,
                       &M->g_batoms};
     for (DevBuf* b : bufs) b->release();
@@ -611,8 +608,8 @@ static mtp_status prepare_neighbors(mtp_model* M, int K, int n, const int* off, 
 // Refresh r_ij of the last list for new positions (same atoms); requires a build with a skin.
 static mtp_status refresh_neighbors(mtp_model* M, int K, int n, const double* pos, cudaStream_t st) {
     if (!M->nb.has_x0 || M->nb.n_atoms != n || M->nb.n_cfg != K) return MTP_EINVAL;
-    const size_t bytes = (size_t)n * M->nb.cap * (is_fp64(M) ? 8 : 4);
-    if (M->nb.cx.reserve(bytes) || M->nb.cy.reserve(bytes) || M->nb.cz.reserve(bytes)) return MTP_ENOMEM;
+    const size_t bytes = (size_t)n * M->nb.cap * (is_fp64(M) ? sizeof(mtp::PairRec<double>) : sizeof(mtp::PairRec<float>));
+    if (M->nb.cpr.reserve(bytes)) return MTP_ENOMEM;
     if (M->profiling) mtp::record_mark(M->ev_nbr[0], st);
     M->launches += mtp::launch_update_pairs(M->nb, pos, st, M->n_sm);
     if (M->profiling) mtp::record_mark(M->ev_nbr[1], st);

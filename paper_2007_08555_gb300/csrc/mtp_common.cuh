@@ -29,6 +29,21 @@ struct alignas(4 * sizeof(T)) Vec4 {
     T x, y, z, w;
 };
 
+// One neighbour pair of the slot-major lists: r_ij and (neighbour index | species << 24), written
+// and read as one record (16 bytes in float, two 16-byte halves in double).
+template <class T>
+struct PairRec;
+template <>
+struct __align__(16) PairRec<float> {
+    float x, y, z;
+    int jz;
+};
+template <>
+struct __align__(32) PairRec<double> {
+    double x, y, z;
+    int jz, pad;
+};
+
 template <class T>
 struct EvalCtx {
     int n_atoms;      // atoms in the batch
@@ -40,11 +55,8 @@ struct EvalCtx {
     const int* cfg_of;    // [n] atom -> configuration
     const int* cfg_off;   // [n_cfg + 1] first atom of each configuration
     const int* count;     // [n] neighbours of each atom
-    const int* jz;        // [cap][n] neighbour index | species << 24
+    const PairRec<T>* pr;  // [cap][n] r_ij and neighbour index | species << 24
     const int* rev;       // [cap][n] slot of the reverse pair in the neighbour's list, -1 if absent
-    const T* rx;          // [cap][n] r_ij components
-    const T* ry;
-    const T* rz;
     const T* c;           // [S][S][NMU][NQ] radial coefficients
     const T* xi;          // [M]
     const T* seed;        // [V] adjoint seed: xi at the value index of each basis function

@@ -44,11 +44,12 @@ struct NbrState {
     int n_atoms = 0, n_cfg = 0, cap = 0;
     bool fp64 = false;
     double rsearch = 0.0;
-    DevBuf count, jz, rev, rx, ry, rz, keys_am;
-    DevBuf cfg_of, desc, atom_bin, atom_wrap, atom_local, atom_wp, bin_count, bin_start, bin_fill, bin_atoms, counters;
+    DevBuf count, pr, rev, keys_am;  // pr: [cap][n] PairRec (r_ij, neighbour | species << 24)
+    DevBuf cfg_of, desc, atom_bin, atom_wrap, atom_local, atom_wp, bin_count, bin_start, atom_slot, bin_atoms, counters;
     DevBuf err;
-    // reuse with a skin: positions at the build and the current displacements (float or double)
-    DevBuf x0, cx, cy, cz;
+    // reuse with a skin: positions at the build and the pair records with r_ij refreshed for the
+    // current positions
+    DevBuf x0, cpr;
     bool has_x0 = false;
 };
 

@@ -257,7 +257,8 @@ struct PairIn {
 };
 template <class T>
 __device__ __forceinline__ PairIn<T> load_pair(const EvalCtx<T>& a, size_t idx) {
-    return PairIn<T>{a.rx[idx], a.ry[idx], a.rz[idx], a.jz[idx] >> 24};
+    const PairRec<T> q = a.pr[idx];
+    return PairIn<T>{q.x, q.y, q.z, q.jz >> 24};
 }
 
 template <class T, int S, int TPA>
@@ -730,8 +731,9 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
                 for (int p = sub; p < cnt; p += TPA) {
                     const size_t idx = (size_t)p * n + i;
                     const Vec4<T> gv = a.g[idx];
+                    const PairRec<T> pq = a.pr[idx];
                     const T g3[3] = {gv.x, gv.y, gv.z};
-                    const T r[3] = {a.rx[idx], a.ry[idx], a.rz[idx]};
+                    const T r[3] = {pq.x, pq.y, pq.z};
 #pragma unroll
                     for (int u = 0; u < 3; ++u) {
                         F[u] += g3[u];
@@ -740,7 +742,7 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
                     }
                     const int q = a.rev[idx];
                     if (q >= 0) {
-                        const Vec4<T> gr = a.g[(size_t)q * n + (a.jz[idx] & 0xffffff)];
+                        const Vec4<T> gr = a.g[(size_t)q * n + (pq.jz & 0xffffff)];
                         F[0] -= gr.x;
                         F[1] -= gr.y;
                         F[2] -= gr.z;
@@ -753,11 +755,12 @@ __global__ void __launch_bounds__(128, TPA >= 4 ? 8 : 1) k_gather(const EvalCtx<
                     GatherIn<T> d;
                     const size_t idx = (size_t)p * n + i;
                     d.g = a.g[idx];
-                    d.rx = a.rx[idx];
-                    d.ry = a.ry[idx];
-                    d.rz = a.rz[idx];
+                    const PairRec<T> pq = a.pr[idx];
+                    d.rx = pq.x;
+                    d.ry = pq.y;
+                    d.rz = pq.z;
                     d.rev = a.rev[idx];
-                    d.j = a.jz[idx] & 0xffffff;
+                    d.j = pq.jz & 0xffffff;
                     return d;
                 };
                 auto reverse = [&](const GatherIn<T>& d) {
@@ -1084,9 +1087,9 @@ __device__ __forceinline__ void tmom_slice(const EvalCtx<T>& a, int i, int sub, 
         const int csz = coef_row(a);
         for (int p = sub; p < cnt; p += TPA) {
             const size_t idx = (size_t)p * n + i;
-            const int jz = a.jz[idx];
-            const int j = jz & 0xffffff, zj = jz >> 24;
-            const T x = a.rx[idx], y = a.ry[idx], z = a.rz[idx];
+            const PairRec<T> pq = a.pr[idx];
+            const int j = pq.jz & 0xffffff, zj = pq.jz >> 24;
+            const T x = pq.x, y = pq.y, z = pq.z;
             const T r = my_sqrt(x * x + y * y + z * z);
             T f[G::NMU_], df[G::NMU_];
             radial<T, true>(r, cs + (zi * a.S + zj) * csz, a.NQ, a.rmin, a.rcut, a.inv_span, f, df);
@@ -1346,11 +1349,11 @@ __global__ void __launch_bounds__(128) k_dc(const EvalCtx<T> a) {
             bool any = false;
             for (int p = sub; p < cnt; p += TPA) {
                 const size_t idx = (size_t)p * n + i;
-                const int jz = a.jz[idx];
-                if ((jz >> 24) != zp) continue;
+                const PairRec<T> pq = a.pr[idx];
+                if ((pq.jz >> 24) != zp) continue;
                 any = true;
-                const int j = jz & 0xffffff;
-                const T x = a.rx[idx], y = a.ry[idx], z = a.rz[idx];
+                const int j = pq.jz & 0xffffff;
+                const T x = pq.x, y = pq.y, z = pq.z;
                 const T r = my_sqrt(x * x + y * y + z * z);
                 T ux, uy, uz;
                 pair_u(a, Di, E, j, x, y, z, ux, uy, uz);

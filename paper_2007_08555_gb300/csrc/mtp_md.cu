@@ -17,8 +17,8 @@ namespace {
 constexpr double kMvv2eV = 103.642696;  // amu Angstrom^2 fs^-2 in eV
 
 template <class T>
-__global__ void k_update_pairs(int n, const int* count, const int* jz, const T* r0x, const T* r0y, const T* r0z,
-                               const double* x, const double* x0, T* rx, T* ry, T* rz, int* err) {
+__global__ void k_update_pairs(int n, const int* count, const PairRec<T>* r0, const double* x, const double* x0,
+                               PairRec<T>* pr, int* err) {
     const size_t N = (size_t)n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double ui0 = x[3 * (size_t)i] - x0[3 * (size_t)i];
@@ -29,13 +29,15 @@ __global__ void k_update_pairs(int n, const int* count, const int* jz, const T* 
         const int cnt = count[i];
         for (int p = 0; p < cnt; ++p) {
             const size_t o = (size_t)p * N + i;
-            const int j = jz[o] & 0xffffff;
+            PairRec<T> q = r0[o];
+            const int j = q.jz & 0xffffff;
             const T uj0 = (T)(x[3 * (size_t)j] - x0[3 * (size_t)j]);
             const T uj1 = (T)(x[3 * (size_t)j + 1] - x0[3 * (size_t)j + 1]);
             const T uj2 = (T)(x[3 * (size_t)j + 2] - x0[3 * (size_t)j + 2]);
-            rx[o] = r0x[o] + (uj0 - fi0);
-            ry[o] = r0y[o] + (uj1 - fi1);
-            rz[o] = r0z[o] + (uj2 - fi2);
+            q.x = q.x + (uj0 - fi0);
+            q.y = q.y + (uj1 - fi1);
+            q.z = q.z + (uj2 - fi2);
+            pr[o] = q;
         }
     }
 }
@@ -100,12 +102,12 @@ int launch_update_pairs(const NbrState& nb, const double* x, cudaStream_t st, in
     cudaMemsetAsync(nb.counters.as<int>() + 4, 0, 2 * sizeof(int), st);
     if (nb.fp64)
         k_update_pairs<double><<<grid_for(n, 128, n_sm), 128, 0, st>>>(
-            n, nb.count.as<int>(), nb.jz.as<int>(), nb.rx.as<double>(), nb.ry.as<double>(), nb.rz.as<double>(), x,
-            nb.x0.as<double>(), nb.cx.as<double>(), nb.cy.as<double>(), nb.cz.as<double>(), nb.err.as<int>());
+            n, nb.count.as<int>(), nb.pr.as<PairRec<double>>(), x, nb.x0.as<double>(), nb.cpr.as<PairRec<double>>(),
+            nb.err.as<int>());
     else
         k_update_pairs<float><<<grid_for(n, 128, n_sm), 128, 0, st>>>(
-            n, nb.count.as<int>(), nb.jz.as<int>(), nb.rx.as<float>(), nb.ry.as<float>(), nb.rz.as<float>(), x,
-            nb.x0.as<double>(), nb.cx.as<float>(), nb.cy.as<float>(), nb.cz.as<float>(), nb.err.as<int>());
+            n, nb.count.as<int>(), nb.pr.as<PairRec<float>>(), x, nb.x0.as<double>(), nb.cpr.as<PairRec<float>>(),
+            nb.err.as<int>());
     return 1;
 }
 

@@ -40,13 +40,8 @@ __device__ __forceinline__ int find_cfg(const int* cfg_off, int K, int i) {
 }
 
 // Per-configuration geometry: inverse cell, perpendicular widths, bin counts and reach.
-__global__ void k_cells(int K, const double* cells, const int* cfg_off, double rsearch, CellDesc* d,
-                        int* bin_total, int* err, int* zero_a, int* zero_b, int n_zero) {
-    pdl_enter();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    // the launch also clears the per-bin counters for k_bin_atoms and k_bin_scatter
-    for (int t = k; t < n_zero; t += gridDim.x * blockDim.x) zero_a[t] = zero_b[t] = 0;
-    if (k >= K) return;
+__device__ void cell_desc(int k, const double* cells, const int* cfg_off, double rsearch, CellDesc* d, int* bin_total,
+                          int* err) {
     CellDesc D;
     const double* H = cells + 9 * (size_t)k;
     bool finite = true;
@@ -65,9 +60,9 @@ __global__ void k_cells(int K, const double* cells, const int* cfg_off, double r
     {
         const double a = H[0], b = H[1], c = H[2], e = H[3], f = H[4], g = H[5], h = H[6], ii = H[7], jj = H[8];
         const double det = a * (f * jj - g * ii) - b * (e * jj - g * h) + c * (e * ii - f * h);
-        const double l0 = sqrt(a * a + b * b + c * c), l1 = sqrt(e * e + f * f + g * g),
-                     l2 = sqrt(h * h + ii * ii + jj * jj);
-        if (finite && !(fabs(det) > 1e-9 * l0 * l1 * l2)) atomicOr(err, kErrCell);  // flat or degenerate cell
+        // flat or degenerate cell: |det| <= 1e-9 |a_0| |a_1| |a_2|, compared squared (no square roots)
+        const double q0 = a * a + b * b + c * c, q1 = e * e + f * f + g * g, q2 = h * h + ii * ii + jj * jj;
+        if (finite && !(det * det > 1e-18 * q0 * q1 * q2)) atomicOr(err, kErrCell);
         const double id = 1.0 / det;
         D.Hi[0] = (f * jj - g * ii) * id; D.Hi[1] = (c * ii - b * jj) * id; D.Hi[2] = (b * g - c * f) * id;
         D.Hi[3] = (g * h - e * jj) * id; D.Hi[4] = (a * jj - c * h) * id; D.Hi[5] = (c * e - a * g) * id;
@@ -121,12 +116,12 @@ __global__ void k_cells(int K, const double* cells, const int* cfg_off, double r
     d[k] = D;
 }
 
-__global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, int S, const int* cfg_off,
-                            const CellDesc* d, int* cfg_of, int* atom_bin, int* atom_wrap, float4* local,
-                            float4* wp, int* bin_count, int* err) {
-    pdl_enter();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// Bin of atom i: fractional coordinates from the inverse cell, the lattice wrap w (x - w H lies in
+// the cell), its position relative to its bin's origin (float, for the prefilter) and the wrapped
+// position as a float pair (for the double-float displacements).  Returns the global bin index.
+__device__ int bin_atom(int i, int K, const double* pos, const int* types, int S, const int* cfg_off,
+                        const CellDesc* d, int* cfg_of, int* atom_bin, int* atom_wrap, float4* local, float4* wp,
+                        int* err) {
     const int k = find_cfg(cfg_off, K, i);
     cfg_of[i] = k;
     if (types[i] < 0 || types[i] >= S) atomicOr(err, kErrSpecies);
@@ -162,37 +157,110 @@ __global__ void k_bin_atoms(int n, int K, const double* pos, const int* types, i
     const int bin = D.bin0 + (b[0] * D.n[1] + b[1]) * D.n[2] + b[2];
     atom_bin[i] = bin;
     atom_wrap[i] = ((w[0] + 128) & 255) | (((w[1] + 128) & 255) << 8) | (((w[2] + 128) & 255) << 16);
-    atomicAdd(&bin_count[bin], 1);
+    return bin;
 }
 
-// Start of every non-empty bin in bin_atoms: one atomic per warp on the running total (the
-// placement order is irrelevant downstream, see k_cells).
-__global__ void k_alloc_bins(int nbins, const int* bin_count, int* bin_start, int* atom_total) {
-    pdl_enter();
-    const int lane = threadIdx.x & 31;
-    for (int b0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; b0 < nbins; b0 += gridDim.x * blockDim.x) {
-        const int b = b0 + lane;
-        const int c = b < nbins ? bin_count[b] : 0;
-        int incl = c;
-#pragma unroll
-        for (int sh = 1; sh < 32; sh <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, sh);
-            if (lane >= sh) incl += y;
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Barrier over the whole grid of a cooperative launch (every block resident).  Barrier number
+// `phase` (1, 2, ...) completes when the counter, zero at launch, reaches phase x gridDim.x.  The
+// wait gives up after ~1 s: it sets kErrTimeout and returns false, and the block then leaves the
+// kernel (the blocks still waiting give up the same way).
+__device__ bool grid_barrier(int* ctr, int phase, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1);
+        const int target = phase * (int)gridDim.x;
+        const unsigned long long t0 = now_ns();
+        int ok = 1;
+        while (ld_acquire(ctr) < target) {
+            if (now_ns() - t0 > 1000000000ull) {
+                atomicOr(err, kErrTimeout);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
         }
-        int base = 0;
-        if (lane == 31) base = atomicAdd(atom_total, incl);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        if (b < nbins) bin_start[b] = base + incl - c;
+        s_ok = ok;
     }
+    __syncthreads();
+    return s_ok != 0;
 }
 
-__global__ void k_bin_scatter(int n, const int* atom_bin, const int* bin_start, int* bin_fill, int* bin_atoms) {
-    pdl_enter();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int bin = atom_bin[i];
-    const int slot = atomicAdd(&bin_fill[bin], 1);
-    bin_atoms[bin_start[bin] + slot] = i;
+struct BinArgs {
+    int K, n, S, n_zero;
+    double rsearch;
+    const double* cells;
+    const int* cfg_off;
+    const double* pos;
+    const int* types;
+    CellDesc* desc;
+    int* counters;  // [0] bins handed out, [1] atoms handed out, [6] grid barrier (zero at launch)
+    int* cfg_of;
+    int* atom_bin;
+    int* atom_wrap;
+    int* atom_slot;
+    float4* local;
+    float4* wp;
+    int* bin_count;
+    int* bin_start;
+    int* bin_atoms;
+    int* err;
+};
+
+constexpr int kBinThreads = 128;
+
+// The cell lists of a batch in one cooperative launch, four phases separated by grid barriers:
+//   0. per configuration: geometry and its range of bins; every bin counter cleared;
+//   1. per atom: its bin and wrap, and its slot in the bin (an atomic on the bin's counter);
+//   2. per bin: its start in bin_atoms (a warp-wide scan, one atomic per warp on the running total;
+//      the placement order changes nothing downstream);
+//   3. per atom: bin_atoms[start of its bin + its slot] = i.
+__global__ void __launch_bounds__(kBinThreads) k_bin_all(const BinArgs a) {
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    int* ctr = a.counters + 6;
+    for (int k = t0; k < a.K; k += stride) cell_desc(k, a.cells, a.cfg_off, a.rsearch, a.desc, a.counters, a.err);
+    for (int t = t0; t < a.n_zero; t += stride) a.bin_count[t] = 0;
+    if (!grid_barrier(ctr, 1, a.err)) return;
+    for (int i = t0; i < a.n; i += stride) {
+        const int bin = bin_atom(i, a.K, a.pos, a.types, a.S, a.cfg_off, a.desc, a.cfg_of, a.atom_bin, a.atom_wrap,
+                                 a.local, a.wp, a.err);
+        a.atom_slot[i] = atomicAdd(&a.bin_count[bin], 1);
+    }
+    if (!grid_barrier(ctr, 2, a.err)) return;
+    {
+        const int nbins = ld_acquire(a.counters);  // bins handed out in phase 0
+        const int lane = threadIdx.x & 31;
+        for (int b0 = t0 & ~31; b0 < nbins; b0 += stride) {
+            const int b = b0 + lane;
+            const int c = b < nbins ? a.bin_count[b] : 0;
+            int incl = c;
+#pragma unroll
+            for (int sh = 1; sh < 32; sh <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, sh);
+                if (lane >= sh) incl += y;
+            }
+            int base = 0;
+            if (lane == 31) base = atomicAdd(a.counters + 1, incl);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            if (b < nbins) a.bin_start[b] = base + incl - c;
+        }
+    }
+    if (!grid_barrier(ctr, 3, a.err)) return;
+    pdl_trigger();  // the neighbour-list kernel may start launching
+    for (int i = t0; i < a.n; i += stride) a.bin_atoms[a.bin_start[a.atom_bin[i]] + a.atom_slot[i]] = i;
 }
 
 __device__ __forceinline__ int unpack(int packed, int q) { return ((packed >> (8 * q)) & 255) - 128; }
@@ -226,13 +294,12 @@ struct BuildArgs {
     const int* bin_count;
     const int* bin_atoms;
     int* count;
-    int* jz;
+    void* pr;                     // [cap][n] PairRec<T>: r_ij and j | species << 24, slot-major
     unsigned long long* keys_am;  // [n][cap] the sorted keys, atom-major
-    void* rx;
-    void* ry;
-    void* rz;
     int* err;
     int* max_seen;
+    const int* bin_barrier;  // the cell lists are complete when it equals bin_barrier_done
+    int bin_barrier_done;
 };
 
 // ---- double-float arithmetic (float pairs hi + lo), error-free transformations -------------------
@@ -290,6 +357,10 @@ size_t build_smem(int cap, size_t realsz) { return kSmWarp + (size_t)kBuildWarps
 template <class T>
 __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
     pdl_enter();
+    if (*a.bin_barrier != a.bin_barrier_done) {  // the binning gave up (error word set): empty lists
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) a.count[i] = 0;
+        return;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* cpos = reinterpret_cast<float4*>(smem_raw + kSmCpos);
     int* cshift = reinterpret_cast<int*>(smem_raw + kSmCshift);
@@ -302,9 +373,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw + kSmWarp) + (size_t)warp * a.cap;
     T* rbuf = reinterpret_cast<T*>(reinterpret_cast<unsigned long long*>(smem_raw + kSmWarp) +
                                    (size_t)kBuildWarps * a.cap) + (size_t)warp * 3 * a.cap;
-    T* RX = static_cast<T*>(a.rx);
-    T* RY = static_cast<T*>(a.ry);
-    T* RZ = static_cast<T*>(a.rz);
+    PairRec<T>* PR = static_cast<PairRec<T>*>(a.pr);
     const size_t n = (size_t)a.n;
     __shared__ int smax;
     if (threadIdx.x == 0) smax = 0;
@@ -533,12 +602,14 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                     const int j = (int)(key >> 32);
                     const size_t o = (size_t)rank * n + i;
                     int tj = a.types[j];
-                    tj = tj < 0 ? 0 : (tj >= a.S ? a.S - 1 : tj);  // invalid species are reported by k_bin_atoms
-                    a.jz[o] = j | (tj << 24);
+                    tj = tj < 0 ? 0 : (tj >= a.S ? a.S - 1 : tj);  // invalid species are reported by the binning
+                    PairRec<T> rec;
+                    rec.x = rbuf[3 * e];
+                    rec.y = rbuf[3 * e + 1];
+                    rec.z = rbuf[3 * e + 2];
+                    rec.jz = j | (tj << 24);
+                    PR[o] = rec;  // one vector store per pair
                     a.keys_am[(size_t)i * a.cap + rank] = key;
-                    RX[o] = rbuf[3 * e];
-                    RY[o] = rbuf[3 * e + 1];
-                    RZ[o] = rbuf[3 * e + 2];
                 }
             }
             if (lane == 0) a.count[i] = keep;
@@ -551,7 +622,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
 
 // one thread per (slot, atom): binary search of the reverse pair (i, -s) in the neighbour's sorted
 // keys, stored atom-major so that one search stays within a few cache lines; rev starts at -1
-__global__ void k_reverse(int n, int cap, const int* count, const int* jz,
+__global__ void k_reverse(int n, int cap, const int* count, const int* jz, int jz_stride,
                           const unsigned long long* keys_am, int* rev) {
     const size_t N = (size_t)n;
     const size_t total = N * (size_t)cap;
@@ -559,7 +630,7 @@ __global__ void k_reverse(int n, int cap, const int* count, const int* jz,
         const int p = (int)(o / N);
         const int i = (int)(o - (size_t)p * N);
         if (p >= count[i]) continue;
-        const int j = jz[o] & 0xffffff;
+        const int j = jz[o * jz_stride] & 0xffffff;
         const int sp = (int)(keys_am[(size_t)i * cap + p] & 0xffffffull);
         const int neg = ((256 - (sp & 255)) & 255) | (((256 - ((sp >> 8) & 255)) & 255) << 8) |
                         (((256 - ((sp >> 16) & 255)) & 255) << 16);
@@ -651,7 +722,8 @@ __global__ void k_scan_add(int* out, int n, const int* sums) {
 }
 
 __global__ void k_export(int n, int cap, const double* pos, const CellDesc* desc, const int* cfg_of, const int* count,
-                         const int* jz, const unsigned long long* keys_am, const int* offsets, int* nbr_j, int* nbr_s,
+                         const int* jz, int jz_stride, const unsigned long long* keys_am, const int* offsets,
+                         int* nbr_j, int* nbr_s,
                          double* r_ij) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -660,7 +732,7 @@ __global__ void k_export(int n, int cap, const double* pos, const CellDesc* desc
     const int cnt = count[i];
     for (int p = 0; p < cnt; ++p) {
         const size_t o = (size_t)p * n + i;
-        const int j = jz[o] & 0xffffff;
+        const int j = jz[o * jz_stride] & 0xffffff;
         const int sp = (int)(keys_am[(size_t)i * cap + p] & 0xffffffull);  // slot p of the sorted keys
         const int s[3] = {((sp >> 16) & 255) - 128, ((sp >> 8) & 255) - 128, (sp & 255) - 128};
         const size_t q = (size_t)offsets[i] + p;
@@ -677,6 +749,14 @@ __global__ void k_export(int n, int cap, const double* pos, const CellDesc* desc
 }
 
 }  // namespace
+
+// the jz words inside the pair records: a pointer to the first and the stride in ints
+static const int* pair_jz(const NbrState& nb) {
+    return nb.fp64 ? &nb.pr.as<PairRec<double>>()->jz : &nb.pr.as<PairRec<float>>()->jz;
+}
+static int jz_stride(const NbrState& nb) {
+    return (int)((nb.fp64 ? sizeof(PairRec<double>) : sizeof(PairRec<float>)) / sizeof(int));
+}
 
 size_t scan_tmp_ints(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 8; }
 
@@ -699,11 +779,12 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     const size_t N = (size_t)n;
     const size_t realsz = fp64 ? 8 : 4;
     const size_t bins_max = N + K + 1;
-    if (nb.count.reserve(N * 4) || nb.jz.reserve(N * cap * 4) ||
-        nb.rev.reserve(N * cap * 4) || nb.keys_am.reserve(N * cap * 8) || nb.rx.reserve(N * cap * realsz) || nb.ry.reserve(N * cap * realsz) || nb.rz.reserve(N * cap * realsz) || nb.cfg_of.reserve(N * 4) || nb.desc.reserve(sizeof(CellDesc) * K) ||
+    const size_t recsz = fp64 ? sizeof(PairRec<double>) : sizeof(PairRec<float>);
+    if (nb.count.reserve(N * 4) || nb.pr.reserve(N * cap * recsz) || nb.rev.reserve(N * cap * 4) ||
+        nb.keys_am.reserve(N * cap * 8) || nb.cfg_of.reserve(N * 4) || nb.desc.reserve(sizeof(CellDesc) * K) ||
         nb.atom_bin.reserve(N * 4) || nb.atom_wrap.reserve(N * 4) || nb.atom_local.reserve(N * 16) || nb.atom_wp.reserve(N * 32) ||
         nb.bin_count.reserve(bins_max * 4) || nb.bin_start.reserve((bins_max + 1) * 4) ||
-        nb.bin_fill.reserve(bins_max * 4) || nb.bin_atoms.reserve(N * 4 + 4) ||
+        nb.atom_slot.reserve(N * 4 + 4) || nb.bin_atoms.reserve(N * 4 + 4) ||
         nb.counters.reserve(64) ||
         nb.err.reserve(4))
         return -1;
@@ -720,28 +801,52 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     int* counters = nb.counters.as<int>();
     cudaMemsetAsync(counters, 0, 8 * sizeof(int), st);
     const int total_bins_upper = n + K;  // every configuration has at most max(1, atoms) bins
-    {
-        const int nz = total_bins_upper + 1;
-        int blocks = (std::max(K, nz) + 127) / 128;
-        if (blocks > 152 * 8) blocks = std::max(152 * 8, (K + 127) / 128);
-        k_cells<<<blocks, 128, 0, st>>>(K, cells, cfg_off, rsearch, desc, counters, nb.err.as<int>(), bin_count,
-                                        nb.bin_fill.as<int>(), nz);
+    // the cell lists: one cooperative launch (its blocks wait on one another at grid barriers, so
+    // all of them must be resident: the grid never exceeds the occupancy of the device)
+    static int bin_occ = 0, n_sm = 0;
+    if (!bin_occ) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bin_occ, k_bin_all, kBinThreads, 0);
+        if (bin_occ < 1 || n_sm < 1) return -1;
     }
-    ++launches;
-    launch_pdl(k_bin_atoms, (n + 63) / 64, 64, 0, st, n, K, pos, types, S, cfg_off, (const CellDesc*)desc,
-               nb.cfg_of.as<int>(), nb.atom_bin.as<int>(), nb.atom_wrap.as<int>(), nb.atom_local.as<float4>(),
-               nb.atom_wp.as<float4>(), bin_count, nb.err.as<int>());
-    ++launches;
+    const int bin_grid = std::max(1, std::min((std::max(n, K) + kBinThreads - 1) / kBinThreads, n_sm * bin_occ));
     {
-        int blocks = (total_bins_upper + 255) / 256;
-        if (blocks > 152 * 8) blocks = 152 * 8;
-        launch_pdl(k_alloc_bins, blocks, 256, 0, st, total_bins_upper, (const int*)bin_count, bin_start,
-                   counters + 1);
+        BinArgs b;
+        b.K = K;
+        b.n = n;
+        b.S = S;
+        b.n_zero = total_bins_upper + 1;
+        b.rsearch = rsearch;
+        b.cells = cells;
+        b.cfg_off = cfg_off;
+        b.pos = pos;
+        b.types = types;
+        b.desc = desc;
+        b.counters = counters;
+        b.cfg_of = nb.cfg_of.as<int>();
+        b.atom_bin = nb.atom_bin.as<int>();
+        b.atom_wrap = nb.atom_wrap.as<int>();
+        b.atom_slot = nb.atom_slot.as<int>();
+        b.local = nb.atom_local.as<float4>();
+        b.wp = nb.atom_wp.as<float4>();
+        b.bin_count = bin_count;
+        b.bin_start = bin_start;
+        b.bin_atoms = nb.bin_atoms.as<int>();
+        b.err = nb.err.as<int>();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)bin_grid);
+        cfg.blockDim = dim3((unsigned)kBinThreads);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, k_bin_all, (const BinArgs)b) != cudaSuccess) return -1;
         ++launches;
     }
-    launch_pdl(k_bin_scatter, (n + 63) / 64, 64, 0, st, n, (const int*)nb.atom_bin.as<int>(),
-               (const int*)bin_start, nb.bin_fill.as<int>(), nb.bin_atoms.as<int>());
-    ++launches;
     BuildArgs a;
     a.n = n;
     a.cap = cap;
@@ -761,13 +866,13 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     a.bin_count = bin_count;
     a.bin_atoms = nb.bin_atoms.as<int>();
     a.count = nb.count.as<int>();
-    a.jz = nb.jz.as<int>();
+
     a.keys_am = nb.keys_am.as<unsigned long long>();
-    a.rx = nb.rx.p;
-    a.ry = nb.ry.p;
-    a.rz = nb.rz.p;
+    a.pr = nb.pr.p;
     a.err = nb.err.as<int>();
     a.max_seen = nb.counters.as<int>() + 2;
+    a.bin_barrier = nb.counters.as<int>() + 6;
+    a.bin_barrier_done = 3 * bin_grid;
     a.nbins = total_bins_upper;
     const size_t smem = build_smem(cap, realsz);
     // one block per bin when they fit in one wave (a perturbed lattice has ~12 atoms per bin)
@@ -805,7 +910,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
             rs = side;
         }
         cudaMemsetAsync(nb.rev.p, 0xff, sizeof(int) * total, rs);
-        k_reverse<<<(int)blocks, 256, 0, rs>>>(n, cap, nb.count.as<int>(), nb.jz.as<int>(),
+        k_reverse<<<(int)blocks, 256, 0, rs>>>(n, cap, nb.count.as<int>(), pair_jz(nb), jz_stride(nb),
                                               nb.keys_am.as<unsigned long long>(), nb.rev.as<int>());
         if (side) cudaEventRecord(join, side);
     }
@@ -817,7 +922,7 @@ int export_neighbors(const NbrState& nb, const double* pos, const int* offsets, 
                      double* r_ij, cudaStream_t st) {
     const int n = nb.n_atoms;
     k_export<<<(n + 127) / 128, 128, 0, st>>>(n, nb.cap, pos, nb.desc.as<CellDesc>(), nb.cfg_of.as<int>(),
-                                              nb.count.as<int>(), nb.jz.as<int>(),
+                                              nb.count.as<int>(), pair_jz(nb), jz_stride(nb),
                                               nb.keys_am.as<unsigned long long>(), offsets, nbr_j, nbr_s, r_ij);
     return 1;
 }
