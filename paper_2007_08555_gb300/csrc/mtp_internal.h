@@ -31,7 +31,8 @@ struct DevBuf {
 };
 
 struct CellDesc {
-    double H[9], Hi[9];
+    double H[9];
+    float Hi[9];  // inverse cell (float: it only places atoms in bins and lattice wraps)
     float hn[9];  // lattice vectors divided by the bin counts, rows
     float hhi[9], hlo[9];  // lattice vectors as float pairs (hi + lo = H to ~2^-48)
     float inv_n[3];

@@ -52,26 +52,27 @@ __device__ void cell_desc(int k, const double* cells, const int* cfg_off, double
     // input checks: every geometry below stays finite-indexed for any input (a NaN converts to a
     // zero bin count, clamped to one bin), so bad cells are only reported here
     if (!finite) atomicOr(err, kErrNonFinite);
-    // The inverse cell in double (fractional coordinates of atoms far from the origin need it),
-    // with a single reciprocal; the bin geometry below in float: this thread's chain is serial,
-    // and a double-precision division or square root costs many float operations here.  Float is
-    // enough for bins: counts and reaches keep 1e-5 relative margins, and the 1e-3 Angstrom band
-    // covers atoms binned slightly off; every neighbour decision is taken in double elsewhere.
+    // The degenerate-cell check in double; the inverse cell and the bin geometry in float: fractional
+    // coordinates only place atoms in bins and lattice wraps, where the 1e-3 Angstrom band of the
+    // search covers the float error, and every neighbour decision is taken in double elsewhere (a
+    // double-precision division or square root costs many float operations on this part).
     {
         const double a = H[0], b = H[1], c = H[2], e = H[3], f = H[4], g = H[5], h = H[6], ii = H[7], jj = H[8];
         const double det = a * (f * jj - g * ii) - b * (e * jj - g * h) + c * (e * ii - f * h);
         // flat or degenerate cell: |det| <= 1e-9 |a_0| |a_1| |a_2|, compared squared (no square roots)
         const double q0 = a * a + b * b + c * c, q1 = e * e + f * f + g * g, q2 = h * h + ii * ii + jj * jj;
         if (finite && !(det * det > 1e-18 * q0 * q1 * q2)) atomicOr(err, kErrCell);
-        const double id = 1.0 / det;
-        D.Hi[0] = (f * jj - g * ii) * id; D.Hi[1] = (c * ii - b * jj) * id; D.Hi[2] = (b * g - c * f) * id;
-        D.Hi[3] = (g * h - e * jj) * id; D.Hi[4] = (a * jj - c * h) * id; D.Hi[5] = (c * e - a * g) * id;
-        D.Hi[6] = (e * ii - f * h) * id; D.Hi[7] = (b * h - a * ii) * id; D.Hi[8] = (a * f - b * e) * id;
     }
     const float a = (float)H[0], b = (float)H[1], c = (float)H[2], e = (float)H[3], f = (float)H[4],
                 g = (float)H[5], h = (float)H[6], ii = (float)H[7], jj = (float)H[8];
     const float det = a * (f * jj - g * ii) - b * (e * jj - g * h) + c * (e * ii - f * h);
     const float vol = fabsf(det);
+    {
+        const float id = 1.f / det;
+        D.Hi[0] = (f * jj - g * ii) * id; D.Hi[1] = (c * ii - b * jj) * id; D.Hi[2] = (b * g - c * f) * id;
+        D.Hi[3] = (g * h - e * jj) * id; D.Hi[4] = (a * jj - c * h) * id; D.Hi[5] = (c * e - a * g) * id;
+        D.Hi[6] = (e * ii - f * h) * id; D.Hi[7] = (b * h - a * ii) * id; D.Hi[8] = (a * f - b * e) * id;
+    }
     const float irs = 1.f / (float)rsearch;
     const float Hf[9] = {a, b, c, e, f, g, h, ii, jj};
     float w[3];
@@ -130,30 +131,35 @@ __device__ int bin_atom(int i, int K, const double* pos, const int* types, int S
     // a non-finite position is reported; its bin and wrap below are clamped, and its pairs fail
     // every distance test, so no index is derived from it
     if (!(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]))) atomicOr(err, kErrNonFinite);
+    // bin and lattice wrap from float fractional coordinates (a bin slightly off is covered by the
+    // band); the wrapped position x - w H in double, kept as a float pair (hi, lo) for the
+    // double-float displacements, and the position relative to the bin's origin in float
     int w[3], b[3];
-    double frac[3];
+    const float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
     for (int q = 0; q < 3; ++q) {
-        const double fq = x[0] * D.Hi[0 * 3 + q] + x[1] * D.Hi[1 * 3 + q] + x[2] * D.Hi[2 * 3 + q];
-        const double fl = floor(fq);
+        const float fq = xf[0] * D.Hi[0 * 3 + q] + xf[1] * D.Hi[1 * 3 + q] + xf[2] * D.Hi[2 * 3 + q];
+        const float fl = floorf(fq);
         w[q] = (int)fl;
-        const float fr = (float)(fq - fl);
+        const float fr = fq - fl;
         int bq = (int)(fr * (float)D.n[q]);
         if (bq < 0) bq = 0;
         if (bq >= D.n[q]) bq = D.n[q] - 1;
         b[q] = bq;
-        frac[q] = (double)w[q] + (double)((float)bq * D.inv_n[q]);  // bin origin: only the float prefilter uses it
         if (w[q] > kMaxShift || w[q] < -kMaxShift) atomicOr(err, kErrShift);
     }
-    double o[3], xw[3];
+    double xw[3] = {x[0], x[1], x[2]};
+    if (w[0] | w[1] | w[2])
+        for (int t = 0; t < 3; ++t) xw[t] -= w[0] * D.H[0 * 3 + t] + w[1] * D.H[1 * 3 + t] + w[2] * D.H[2 * 3 + t];
+    float hi[3], lo[3], lc[3];
     for (int t = 0; t < 3; ++t) {
-        o[t] = frac[0] * D.H[0 * 3 + t] + frac[1] * D.H[1 * 3 + t] + frac[2] * D.H[2 * 3 + t];
-        xw[t] = x[t] - (w[0] * D.H[0 * 3 + t] + w[1] * D.H[1 * 3 + t] + w[2] * D.H[2 * 3 + t]);
+        hi[t] = (float)xw[t];
+        lo[t] = (float)(xw[t] - (double)hi[t]);
+        const float o = (float)b[0] * D.hn[0 * 3 + t] + (float)b[1] * D.hn[1 * 3 + t] + (float)b[2] * D.hn[2 * 3 + t];
+        lc[t] = (hi[t] - o) + lo[t];
     }
-    local[i] = make_float4((float)(x[0] - o[0]), (float)(x[1] - o[1]), (float)(x[2] - o[2]), 0.f);
-    // wrapped position x - w H as a float pair (hi, lo) for the double-float displacement
-    const float h0 = (float)xw[0], h1 = (float)xw[1], h2 = (float)xw[2];
-    wp[2 * (size_t)i] = make_float4(h0, h1, h2, 0.f);
-    wp[2 * (size_t)i + 1] = make_float4((float)(xw[0] - h0), (float)(xw[1] - h1), (float)(xw[2] - h2), 0.f);
+    local[i] = make_float4(lc[0], lc[1], lc[2], 0.f);
+    wp[2 * (size_t)i] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    wp[2 * (size_t)i + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
     const int bin = D.bin0 + (b[0] * D.n[1] + b[1]) * D.n[2] + b[2];
     atom_bin[i] = bin;
     atom_wrap[i] = ((w[0] + 128) & 255) | (((w[1] + 128) & 255) << 8) | (((w[2] + 128) & 255) << 16);
@@ -279,7 +285,7 @@ __device__ __forceinline__ double exact_r2(const double* xi, const double* xj, c
 
 struct BuildArgs {
     int n, cap, S;
-    int nbins;       // bins to visit (an upper bound; empty bins are skipped)
+    const int* nbins;  // bins handed out by the binning (its counter; empty bins are skipped)
     double rs2;      // rsearch^2 (double)
     float lo2, hi2;  // (rsearch -/+ band)^2
     const double* pos;
@@ -335,19 +341,20 @@ __device__ __forceinline__ int key_s(int packed, int q) { return unpack(packed, 
 constexpr int kBias3 = 0x808080;  // three zero components
 
 // Shared-memory layout of k_build (bytes): staged candidates, the current group of neighbour bins,
-// then per warp the accepted keys and their r_ij.
+// then per warp the accepted keys and the lattice shift of the neighbour's bin of each.
 constexpr int kBuildThreads = 128, kBuildWarps = kBuildThreads / 32;
 constexpr int kGroup = kBuildThreads;  // neighbour bins described per staging round
 constexpr int kChunk = 512;            // candidates staged per round
 constexpr size_t kSmCpos = 0;
 constexpr size_t kSmCshift = kSmCpos + sizeof(float4) * kChunk;
-constexpr size_t kSmGpre = kSmCshift + sizeof(int) * kChunk;
+constexpr size_t kSmCtb = kSmCshift + sizeof(int) * kChunk;
+constexpr size_t kSmGpre = kSmCtb + sizeof(int) * kChunk;
 constexpr size_t kSmGstart = kSmGpre + sizeof(int) * (kGroup + 4);
 constexpr size_t kSmGtb = kSmGstart + sizeof(int) * kGroup;
 constexpr size_t kSmGoff = kSmGtb + sizeof(int) * kGroup;
 constexpr size_t kSmWsum = kSmGoff + sizeof(float) * 3 * kGroup;
 constexpr size_t kSmWarp = kSmWsum + 64;
-size_t build_smem(int cap, size_t realsz) { return kSmWarp + (size_t)kBuildWarps * cap * (8 + 3 * realsz); }
+size_t build_smem(int cap) { return kSmWarp + (size_t)kBuildWarps * cap * (8 + 4); }
 
 // One block per bin (grid-stride over the bins).  The atoms of the bins around it are the candidates
 // of every atom in it: they are staged once in shared memory (positions relative to the bin's
@@ -364,6 +371,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* cpos = reinterpret_cast<float4*>(smem_raw + kSmCpos);
     int* cshift = reinterpret_cast<int*>(smem_raw + kSmCshift);
+    int* ctb = reinterpret_cast<int*>(smem_raw + kSmCtb);
     int* gpre = reinterpret_cast<int*>(smem_raw + kSmGpre);
     int* gstart = reinterpret_cast<int*>(smem_raw + kSmGstart);
     int* gtb = reinterpret_cast<int*>(smem_raw + kSmGtb);
@@ -371,14 +379,16 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
     int* wsum = reinterpret_cast<int*>(smem_raw + kSmWsum);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw + kSmWarp) + (size_t)warp * a.cap;
-    T* rbuf = reinterpret_cast<T*>(reinterpret_cast<unsigned long long*>(smem_raw + kSmWarp) +
-                                   (size_t)kBuildWarps * a.cap) + (size_t)warp * 3 * a.cap;
+    // lattice shift t = s + w_j - w_i of each accepted pair (the shift of the neighbour's bin)
+    int* ktb = reinterpret_cast<int*>(reinterpret_cast<unsigned long long*>(smem_raw + kSmWarp) +
+                                      (size_t)kBuildWarps * a.cap) + (size_t)warp * a.cap;
     PairRec<T>* PR = static_cast<PairRec<T>*>(a.pr);
     const size_t n = (size_t)a.n;
     __shared__ int smax;
     if (threadIdx.x == 0) smax = 0;
     __syncthreads();
-    for (int bin = blockIdx.x; bin < a.nbins; bin += gridDim.x) {
+    const int nbins = *a.nbins;
+    for (int bin = blockIdx.x; bin < nbins; bin += gridDim.x) {
         const int nat = a.bin_count[bin];
         if (nat == 0) continue;
         const int start = a.bin_start[bin];
@@ -465,8 +475,13 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                             cpos[f] = make_float4(lj.x + goff[g], lj.y + goff[kGroup + g], lj.z + goff[2 * kGroup + g],
                                                   __int_as_float(j));
                             const int tb = gtb[g];
+                            int tz = a.types[j];
+                            tz = tz < 0 ? 0 : (tz >= a.S ? a.S - 1 : tz);  // invalid species are reported by the binning
+                            // the key's low word: image shift in bytes 0..2, the neighbour's species in byte 3
+                            // (a function of j: the key order stays (j, s))
                             cshift[f] = key_shift(unpack(tb, 0) - unpack(wj, 0), unpack(tb, 1) - unpack(wj, 1),
-                                                  unpack(tb, 2) - unpack(wj, 2));
+                                                  unpack(tb, 2) - unpack(wj, 2)) | (tz << 24);
+                            ctb[f] = tb;
                         }
                         __syncthreads();
                     }
@@ -474,17 +489,18 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                         // 1c. float prefilter on the staged candidates, two per lane per round (their
                         //     shared-memory loads overlap); only the rare pairs within 1e-3 Angstrom of
                         //     the cutoff take the double-precision decision
-                        auto test = [&](int e, bool& acc, unsigned long long& key) {
+                        auto test = [&](int e, bool& acc, unsigned long long& key, int& tbe) {
                             acc = false;
                             key = 0;
+                            tbe = 0;
                             if (e >= m) return;
                             const float4 cp = cpos[e];
                             const float dx = cp.x - li.x, dy = cp.y - li.y, dz = cp.z - li.z;
                             const float r2 = dx * dx + dy * dy + dz * dz;
                             if (r2 > a.hi2) return;
                             const int j = __float_as_int(cp.w);
-                            const int ks = cshift[e] + wik;  // key-order shift s
-                            if (j == i && ks == kBias3) return;
+                            const int ks = cshift[e] + wik;  // key-order shift s (species in byte 3)
+                            if (j == i && (ks & 0xffffff) == kBias3) return;
                             if (r2 < a.lo2) {
                                 acc = true;
                             } else {
@@ -496,24 +512,32 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                                 double dd[3];
                                 acc = exact_r2(xi, xj, D.H, sv, dd) < a.rs2;
                             }
-                            key = ((unsigned long long)j << 32) | (unsigned long long)ks;
+                            key = ((unsigned long long)j << 32) | (unsigned long long)(unsigned)ks;
+                            tbe = ctb[e];
                         };
                         for (int e0 = 0; e0 < m; e0 += 64) {
                             bool acc0, acc1;
                             unsigned long long key0, key1;
-                            test(e0 + lane, acc0, key0);
-                            test(e0 + 32 + lane, acc1, key1);
+                            int tb0, tb1;
+                            test(e0 + lane, acc0, key0, tb0);
+                            test(e0 + 32 + lane, acc1, key1, tb1);
                             const unsigned b0 = __ballot_sync(0xffffffffu, acc0);
                             const unsigned b1 = __ballot_sync(0xffffffffu, acc1);
                             const unsigned below = (1u << lane) - 1u;
                             if (acc0) {
                                 const int pos_ = cnt + __popc(b0 & below);
-                                if (pos_ < a.cap) keys[pos_] = key0;
+                                if (pos_ < a.cap) {
+                                    keys[pos_] = key0;
+                                    ktb[pos_] = tb0;
+                                }
                             }
                             cnt += __popc(b0);
                             if (acc1) {
                                 const int pos_ = cnt + __popc(b1 & below);
-                                if (pos_ < a.cap) keys[pos_] = key1;
+                                if (pos_ < a.cap) {
+                                    keys[pos_] = key1;
+                                    ktb[pos_] = tb1;
+                                }
                             }
                             cnt += __popc(b1);
                         }
@@ -529,52 +553,43 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                 if (cnt > a.cap) atomicOr(a.err, kErrOverflow);
                 atomicMax(&smax, cnt);  // one global update per block, at the end
             }
-            // 2. r_ij of the accepted pairs, one pair per lane: exact double precision for the
-            //    double path, double-float arithmetic (then one rounding) for the float path
+            // 2. canonical order (j, s) by rank (keys are distinct), written in slot-major layout and
+            //    atom-major for the reverse-pair search; each pass takes two keys per lane.  r_ij of
+            //    each key: exact double precision for the double path, double-float arithmetic (then
+            //    one rounding) for the float path; the neighbours' positions are loaded before the
+            //    ranking, so their latency overlaps it.
+            double xi[3] = {0.0, 0.0, 0.0};
+            float4 pih = make_float4(0.f, 0.f, 0.f, 0.f), pil = pih;
             if (sizeof(T) == 8) {
-                const double xi[3] = {a.pos[3 * (size_t)i], a.pos[3 * (size_t)i + 1], a.pos[3 * (size_t)i + 2]};
-                for (int e = lane; e < keep; e += 32) {
-                    const unsigned long long key = keys[e];
-                    const int j = (int)(key >> 32);
-                    const int sp = (int)(key & 0xffffffull);
-                    const int s[3] = {key_s(sp, 0), key_s(sp, 1), key_s(sp, 2)};
-                    const double xj[3] = {a.pos[3 * (size_t)j], a.pos[3 * (size_t)j + 1], a.pos[3 * (size_t)j + 2]};
-                    double dd[3];
-                    exact_r2(xi, xj, D.H, s, dd);
-                    rbuf[3 * e] = (T)dd[0];
-                    rbuf[3 * e + 1] = (T)dd[1];
-                    rbuf[3 * e + 2] = (T)dd[2];
-                }
+                xi[0] = a.pos[3 * (size_t)i];
+                xi[1] = a.pos[3 * (size_t)i + 1];
+                xi[2] = a.pos[3 * (size_t)i + 2];
             } else {
-                const float4 pih = a.wp[2 * (size_t)i], pil = a.wp[2 * (size_t)i + 1];
-                for (int e = lane; e < keep; e += 32) {
-                    const unsigned long long key = keys[e];
-                    const int j = (int)(key >> 32);
-                    const int sp = (int)(key & 0xffffffull);
-                    const int wj = a.atom_wrap[j];
-                    // image shift relative to the wrapped positions: t = s + w_j - w_i
-                    const float t[3] = {(float)(key_s(sp, 0) + unpack(wj, 0) - unpack(wi, 0)),
-                                        (float)(key_s(sp, 1) + unpack(wj, 1) - unpack(wi, 1)),
-                                        (float)(key_s(sp, 2) + unpack(wj, 2) - unpack(wi, 2))};
-                    const float4 pjh = a.wp[2 * (size_t)j], pjl = a.wp[2 * (size_t)j + 1];
-                    const float jh[3] = {pjh.x, pjh.y, pjh.z}, jl[3] = {pjl.x, pjl.y, pjl.z};
-                    const float ih[3] = {pih.x, pih.y, pih.z}, il[3] = {pil.x, pil.y, pil.z};
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        DF d = df_add({jh[c], jl[c]}, {-ih[c], -il[c]});
-#pragma unroll
-                        for (int q = 0; q < 3; ++q)
-                            if (t[q] != 0.f) d = df_add(d, df_scale(t[q], D.hhi[3 * q + c], D.hlo[3 * q + c]));
-                        rbuf[3 * e + c] = (T)__fadd_rn(d.hi, d.lo);
-                    }
-                }
+                pih = a.wp[2 * (size_t)i];
+                pil = a.wp[2 * (size_t)i + 1];
             }
-            __syncwarp();
-            // 3. canonical order (j, s) by rank (keys are distinct), written in slot-major layout and
-            //    atom-major for the reverse-pair search; each pass ranks two keys per lane
             for (int e0 = 0; e0 < keep; e0 += 64) {
                 const int ea = e0 + lane, eb = e0 + 32 + lane;
                 const unsigned long long ka = ea < keep ? keys[ea] : ~0ull, kb = eb < keep ? keys[eb] : ~0ull;
+                const int tba = ea < keep ? ktb[ea] : kBias3, tbb = eb < keep ? ktb[eb] : kBias3;
+                // the neighbours' wrapped positions (float pairs) or positions (double)
+                float4 jah = make_float4(0.f, 0.f, 0.f, 0.f), jal = jah, jbh = jah, jbl = jah;
+                double xa[3] = {0.0, 0.0, 0.0}, xb[3] = {0.0, 0.0, 0.0};
+                {
+                    const size_t ja = ea < keep ? (size_t)(ka >> 32) : (size_t)i;
+                    const size_t jb = eb < keep ? (size_t)(kb >> 32) : (size_t)i;
+                    if (sizeof(T) == 8) {
+                        for (int c = 0; c < 3; ++c) {
+                            xa[c] = a.pos[3 * ja + c];
+                            xb[c] = a.pos[3 * jb + c];
+                        }
+                    } else {
+                        jah = a.wp[2 * ja];
+                        jal = a.wp[2 * ja + 1];
+                        jbh = a.wp[2 * jb];
+                        jbl = a.wp[2 * jb + 1];
+                    }
+                }
                 int ra = 0, rb = 0;
                 if (uniq) {  // every j once: its index alone orders the keys (the high words)
                     const unsigned ja = (unsigned)(ka >> 32), jb = (unsigned)(kb >> 32);
@@ -600,13 +615,36 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
                     const unsigned long long key = h ? kb : ka;
                     const int rank = h ? rb : ra;
                     const int j = (int)(key >> 32);
+                    T r[3];
+                    if (sizeof(T) == 8) {
+                        const int sp = (int)(key & 0xffffffull);
+                        const int sv[3] = {key_s(sp, 0), key_s(sp, 1), key_s(sp, 2)};
+                        double dd[3];
+                        exact_r2(xi, h ? xb : xa, D.H, sv, dd);
+                        for (int c = 0; c < 3; ++c) r[c] = (T)dd[c];
+                    } else {
+                        // image shift relative to the wrapped positions, t = s + w_j - w_i: the lattice
+                        // shift of the neighbour's bin, recorded when the pair was accepted
+                        const int tb = h ? tbb : tba;
+                        const float t[3] = {(float)unpack(tb, 0), (float)unpack(tb, 1), (float)unpack(tb, 2)};
+                        const float4 pjh = h ? jbh : jah, pjl = h ? jbl : jal;
+                        const float jh[3] = {pjh.x, pjh.y, pjh.z}, jl[3] = {pjl.x, pjl.y, pjl.z};
+                        const float ih[3] = {pih.x, pih.y, pih.z}, il[3] = {pil.x, pil.y, pil.z};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            DF d = df_add({jh[c], jl[c]}, {-ih[c], -il[c]});
+#pragma unroll
+                            for (int q = 0; q < 3; ++q)
+                                if (t[q] != 0.f) d = df_add(d, df_scale(t[q], D.hhi[3 * q + c], D.hlo[3 * q + c]));
+                            r[c] = (T)__fadd_rn(d.hi, d.lo);
+                        }
+                    }
                     const size_t o = (size_t)rank * n + i;
-                    int tj = a.types[j];
-                    tj = tj < 0 ? 0 : (tj >= a.S ? a.S - 1 : tj);  // invalid species are reported by the binning
+                    const int tj = (int)((key >> 24) & 255);  // the neighbour's species, from the key
                     PairRec<T> rec;
-                    rec.x = rbuf[3 * e];
-                    rec.y = rbuf[3 * e + 1];
-                    rec.z = rbuf[3 * e + 2];
+                    rec.x = r[0];
+                    rec.y = r[1];
+                    rec.z = r[2];
                     rec.jz = j | (tj << 24);
                     PR[o] = rec;  // one vector store per pair
                     a.keys_am[(size_t)i * a.cap + rank] = key;
@@ -622,7 +660,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a) {
 
 // one thread per (slot, atom): binary search of the reverse pair (i, -s) in the neighbour's sorted
 // keys, stored atom-major so that one search stays within a few cache lines; rev starts at -1
-__global__ void k_reverse(int n, int cap, const int* count, const int* jz, int jz_stride,
+__global__ void k_reverse(int n, int cap, int S, const int* types, const int* count, const int* jz, int jz_stride,
                           const unsigned long long* keys_am, int* rev) {
     const size_t N = (size_t)n;
     const size_t total = N * (size_t)cap;
@@ -637,7 +675,10 @@ __global__ void k_reverse(int n, int cap, const int* count, const int* jz, int j
         // each pair is searched once, from its canonical side (i < j, or s above -s for an atom's
         // own images), which writes both slots; a pair without a partner keeps -1 (set before)
         if (!(i < j || (i == j && sp > neg))) continue;
-        const unsigned long long want = ((unsigned long long)i << 32) | (unsigned long long)neg;
+        int zi = types[i];
+        zi = zi < 0 ? 0 : (zi >= S ? S - 1 : zi);
+        const unsigned long long want =
+            ((unsigned long long)i << 32) | (unsigned long long)(unsigned)(neg | (zi << 24));
         const unsigned long long* kj = keys_am + (size_t)j * cap;
         int lo = 0, hi = count[j] - 1, found = -1;
         while (lo <= hi) {
@@ -777,7 +818,6 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
                     cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
     int launches = 0;
     const size_t N = (size_t)n;
-    const size_t realsz = fp64 ? 8 : 4;
     const size_t bins_max = N + K + 1;
     const size_t recsz = fp64 ? sizeof(PairRec<double>) : sizeof(PairRec<float>);
     if (nb.count.reserve(N * 4) || nb.pr.reserve(N * cap * recsz) || nb.rev.reserve(N * cap * 4) ||
@@ -873,8 +913,8 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
     a.max_seen = nb.counters.as<int>() + 2;
     a.bin_barrier = nb.counters.as<int>() + 6;
     a.bin_barrier_done = 3 * bin_grid;
-    a.nbins = total_bins_upper;
-    const size_t smem = build_smem(cap, realsz);
+    a.nbins = counters;
+    const size_t smem = build_smem(cap);
     // one block per bin when they fit in one wave (a perturbed lattice has ~12 atoms per bin)
     const int per_sm = (int)std::min<size_t>(12, (220 * 1024) / (smem + 1024));
     int blocks = std::min(total_bins_upper, 152 * std::max(per_sm, 1));
@@ -910,7 +950,7 @@ int build_neighbors(NbrState& nb, int K, int n, const int* cfg_off, const double
             rs = side;
         }
         cudaMemsetAsync(nb.rev.p, 0xff, sizeof(int) * total, rs);
-        k_reverse<<<(int)blocks, 256, 0, rs>>>(n, cap, nb.count.as<int>(), pair_jz(nb), jz_stride(nb),
+        k_reverse<<<(int)blocks, 256, 0, rs>>>(n, cap, S, types, nb.count.as<int>(), pair_jz(nb), jz_stride(nb),
                                               nb.keys_am.as<unsigned long long>(), nb.rev.as<int>());
         if (side) cudaEventRecord(join, side);
     }
