@@ -271,11 +271,14 @@ __device__ __forceinline__ void moments_slice(const EvalCtx<T>& a, int i, int su
     const size_t n = (size_t)a.n_atoms;
     if (active) {
         const int csz = coef_row(a);
-        // the next pair's loads are issued before this pair's arithmetic (their latency overlaps it)
-        PairIn<T> nx = load_pair(a, sub < cnt ? (size_t)sub * n + i : (size_t)i);
+        // the pair records two steps ahead are in flight during this pair's arithmetic (one record
+        // is one wide load that spans several cache lines of the slot-major rows)
+        PairIn<T> nx1 = load_pair(a, sub < cnt ? (size_t)sub * n + i : (size_t)i);
+        PairIn<T> nx2 = load_pair(a, sub + TPA < cnt ? (size_t)(sub + TPA) * n + i : (size_t)i);
         for (int p = sub; p < cnt; p += TPA) {
-            const PairIn<T> cur = nx;
-            if (p + TPA < cnt) nx = load_pair(a, (size_t)(p + TPA) * n + i);
+            const PairIn<T> cur = nx1;
+            nx1 = nx2;
+            if (p + 2 * TPA < cnt) nx2 = load_pair(a, (size_t)(p + 2 * TPA) * n + i);
             const T x = cur.x, y = cur.y, z = cur.z;
             const T r = my_sqrt(x * x + y * y + z * z);
             T f[G::NMU_];
