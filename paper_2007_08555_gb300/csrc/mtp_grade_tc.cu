@@ -199,6 +199,22 @@ __device__ __forceinline__ void base128_digits(long long T, int* q) {
     q[0] = (hi >> 21) - 64;
 }
 
+// A 64-bit unsigned integer rounded to the nearest float (ties to even), with integer operations
+// only: the leading 24 bits after normalisation are the significand, the 40 bits below decide the
+// rounding (a carry out of the significand moves into the exponent field by the addition).  The
+// conversion instruction for 64-bit integers runs on the double-precision pipe of this part.
+__device__ __forceinline__ float u64_to_float_rn(unsigned long long u) {
+    if (u == 0ull) return 0.f;
+    const int lz = __clzll((long long)u);
+    const unsigned long long v = u << lz;  // bit 63 set
+    unsigned int mant = (unsigned int)(v >> 40);
+    const unsigned long long rem = v & ((1ull << 40) - 1ull);
+    const unsigned long long half = 1ull << 39;
+    mant += (rem > half || (rem == half && (mant & 1u))) ? 1u : 0u;
+    const int e = 63 - lz;  // u in [2^e, 2^(e + 1))
+    return __int_as_float(((e + 127) << 23) + (int)(mant - (1u << 23)));
+}
+
 // BF16 bits of a small integer (|d| < 2^8: exact)
 __device__ __forceinline__ uint32_t bf16_bits(int d) {
     const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;  // exact for |d| < 2^22
@@ -263,7 +279,6 @@ struct TcArgs {
 };
 
 constexpr int kSmallSumsM = 127;
-constexpr unsigned long long kMagicSum = 0x4B400000ull * (128ull * 128 * 128 + 128 * 128 + 128 + 1);
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -493,36 +508,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grade_tc(const TcArgs a) {
                     }
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        // sum_g A_g 128^(7 - g) = H 2^28 + L, exactly
-                        long long H, L;
+                        // sum_g A_g 128^(7 - g) = H 2^28 + L, exactly, with H and L from the pairs
+                        // X = A_0 128 + A_1, Y = A_2 128 + A_3 (and likewise for groups 4..7), which
+                        // fit in 32 bits: |A_g| <= 8 m 65 64 = 15,974,400 for m = 480, so |X| <= 129
+                        // times that, below 2^31
+                        int A[kGroups];
                         if (small_sums) {
-                            // A_g + 1.5 2^23 is exact in [2^23, 2^24) and its bits are 0x4B400000 + A_g;
-                            // the offsets of the four groups of a half are subtracted as one constant
-                            unsigned long long h = 0ull - kMagicSum, l = 0ull - kMagicSum;
+                            // A_g + 1.5 2^23 is exact in [2^23, 2^24) and its bits are 0x4B400000 + A_g
 #pragma unroll
-                            for (int g = 0; g < 4; ++g) {
-                                const uint32_t ug = __float_as_uint(__uint_as_float(v[g][i]) + 12582912.0f);
-                                const uint32_t ul = __float_as_uint(__uint_as_float(v[g + 4][i]) + 12582912.0f);
-                                h += (unsigned long long)ug << (7 * (3 - g));
-                                l += (unsigned long long)ul << (7 * (3 - g));
-                            }
-                            H = (long long)h;
-                            L = (long long)l;
+                            for (int g = 0; g < kGroups; ++g)
+                                A[g] = (int)__float_as_uint(__uint_as_float(v[g][i]) + 12582912.0f) - 0x4B400000;
                         } else {
-                            long long A[kGroups];
 #pragma unroll
-                            for (int g = 0; g < kGroups; ++g) A[g] = (long long)__float2int_rn(__uint_as_float(v[g][i]));
-                            H = ((A[0] * 128 + A[1]) * 128 + A[2]) * 128 + A[3];
-                            L = ((A[4] * 128 + A[5]) * 128 + A[6]) * 128 + A[7];
+                            for (int g = 0; g < kGroups; ++g) A[g] = __float2int_rn(__uint_as_float(v[g][i]));
                         }
-                        const long long Lh = L >> 28;
-                        const long long Ll = L - (Lh << 28);  // [0, 2^28)
-                        H += Lh;
+                        const long long H = ((long long)(A[0] * 128 + A[1]) << 14) + (A[2] * 128 + A[3]);
+                        const long long L = ((long long)(A[4] * 128 + A[5]) << 14) + (A[6] * 128 + A[7]);
                         float mag;
-                        if (H > -(1ll << 34) && H < (1ll << 34))
-                            mag = fabsf(__ll2float_rn((H << 28) + Ll));
-                        else
-                            mag = fabsf(__fmaf_rn(__ll2float_rn(H), 268435456.0f, __ll2float_rn(Ll)));
+                        if (H > -(1ll << 34) && H < (1ll << 34)) {  // |H 2^28 + L| < 2^63
+                            const long long T = (H << 28) + L;
+                            mag = u64_to_float_rn((unsigned long long)(T < 0 ? -T : T));
+                        } else {
+                            // beyond 64 bits: H' = H + floor(L / 2^28) and L' = L mod 2^28 in [0, 2^28);
+                            // L' is below half an ulp of H' 2^28 (|H'| >= 2^33), so rounding H' is
+                            // rounding the value (up to exact ties)
+                            const long long Hn = H + (L >> 28);
+                            const float hf = u64_to_float_rn((unsigned long long)(Hn < 0 ? -Hn : Hn));
+                            mag = fabsf(__fmaf_rn(Hn < 0 ? -hf : hf, 268435456.0f, (float)(int)(L & ((1ll << 28) - 1))));
+                        }
                         float v2 = mag * scale;
                         if (!(v2 >= 0.f)) v2 = 0.f;  // 0 x inf from a column scale beyond float range
                         // maximum over the warp's 32 columns j (non-negative floats order as their bits)
