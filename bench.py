@@ -55,8 +55,13 @@ def parse():
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a kernel on the headline
 # workload, from one ncu capture of the current kernel (profiles/); None when not captured since the
+# kernel last changed.  The neighbour phase's entry adds its two launches: the cell lists (k_bin_all,
+# 498,176 B) and the list kernel (k_build, 1,428,992 + 296,960 B).
+TRAFFIC = {"k_build": 2224128, "k_pairgrad": None, "k_moments": None, "k_contract_parts": None, "k_gather": None}
+# DRAM bytes per row of the tensor-core grade (rows of 116 doubles read once, one grade written), from
+# one ncu capture of the current kernel at 200,000 rows (profiles/); None when not captured since the
 # kernel last changed
-TRAFFIC = {"k_build": None, "k_pairgrad": None, "k_moments": None, "k_contract_parts": None, "k_gather": None}
+TC_TRAFFIC_PER_ROW = None
 PHASE_KERNEL = {"neighbors": "k_build", "moments": "k_moments", "contract": "k_contract_parts",
                 "pairgrad": "k_pairgrad", "gather": "k_gather"}
 
@@ -271,7 +276,7 @@ def run_ours(args):
     if dom == "neighbors":
         nbytes = flops.neighbor_bytes(n, n_pairs, 4)
         achieved = nbytes / (per_call[dom] * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_build (neighbour phase, binning kernels included)",
+        roofline = {"bound": "hbm", "kernel": "k_bin_all + k_build (neighbour phase)",
                     "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                     "algorithmic_bytes": nbytes, "peak_note": peaks["source"] + ", copy bandwidth",
@@ -429,9 +434,10 @@ def batch_record(args, peaks):
     gam = torch.empty(n, dtype=torch.float64, device="cuda")
     ms_tc = _timed(lambda: mtp.mtp_grade(model.h, n, batoms, gam), steps, 3, stream)
     ms_simt = _timed(lambda: mtp.mtp_grade(m32.h, n, batoms, gam), 3, 1, stream)
-    mp = (m + 63) // 64 * 64
-    tiles = (n + 127) // 128 * (mp // 64)
-    mma_flops = tiles * 36 * (mp // 16) * 2 * 128 * 64 * 16  # digit pairs x K steps x one 128x64x16 MMA
+    # digit-pair products of the padded tiles (64 rows x 128 columns, K in chunks of 32); the kernel
+    # issues 48 pair slots per K step (12 MMAs of 128 x 256 x 16, the zero planes included), 36 useful
+    n_rt, n_ct, n_kc = (n + 63) // 64, (m + 127) // 128, (m + 31) // 32
+    mma_flops = 36 * 2 * (n_rt * 64) * (n_ct * 128) * (n_kc * 32)
     alg_flops = 2.0 * n * m * m
     bf16 = peaks["bf16_tflops"]
     tensor = {"bound": "tensor", "kernel": "k_grade_tc (per-atom grades, 303k x 116 rows)",
@@ -440,7 +446,9 @@ def batch_record(args, peaks):
               "note": "achieved counts the BF16 digit-pair MMAs (36 pairs per product); the algorithmic "
                       "[n x m][m x m] product runs at algorithmic_tflops",
               "algorithmic_tflops": round(alg_flops / (ms_tc * 1e-3) / 1e12, 3), "ms": round(ms_tc, 4),
-              "double_product_ms": round(ms_simt, 4), "peak_note": "bf16 burst, " + peaks["source"]}
+              "double_product_ms": round(ms_simt, 4), "peak_note": "bf16 burst, " + peaks["source"],
+              "traffic": None if TC_TRAFFIC_PER_ROW is None else round(TC_TRAFFIC_PER_ROW * n),
+              "traffic_note": "DRAM bytes per launch, from a capture at 200,000 rows scaled by the rows"}
     return {"workload": f"4096 strained fcc/bcc/hcp cells of 8-256 atoms ({n} atoms), 1-3 species, lev_max=16, "
                         "E+F+W and the grade of every cell", "value": round(n / (ms * 1e-3), 1), "unit": "atoms/s",
             "ms_per_step": round(ms, 4), "eval_only_atoms_per_s": round(n / (ms_eval * 1e-3), 1),

@@ -35,13 +35,15 @@
 // descriptor's leading byte offset; row groups 512 bytes apart: its stride byte offset); planes of
 // the same shape follow each other, so consecutive planes form one taller operand.
 //
-// One persistent CTA per SM (256 threads, ~220 KB of shared memory, all 512 TMEM columns) walks over
-// row tiles of 64 (their exponents found once) and, for each, over the column tiles of 128; K is taken
-// in chunks of 32 through two stages of shared memory: per chunk the column digits of G are copied
-// from global memory by the bulk-copy engine (cp.async.bulk, prepared once per active set), the
-// threads write the row digits, and one thread issues the 24 MMAs and commits them to the stage's
-// mbarrier, so the digits of the next chunk are written while the tensor cores multiply.  Every wait
-// on an mbarrier gives up after ~2 s, sets the error word and leaves the kernel.
+// One persistent CTA per SM (288 threads, ~227 KB of shared memory, all 512 TMEM columns) walks over
+// row tiles of 64 and, for each, over the column tiles of 128; K is taken in chunks of 32 through two
+// stages of shared memory.  Warp specialisation: one thread of the ninth warp copies the column
+// digits of each chunk with the bulk-copy engine (cp.async.bulk, prepared once per active set),
+// issues the chunk's 24 MMAs and commits them to the stage's mbarrier; the eight producer warps find
+// the row exponents (for the next row tile while the tensor cores finish the current one), write the
+// row digits of the next chunk into the other stage, and run the epilogue.  They meet only on
+// mbarriers; every wait gives up after ~2 s and sets the error word, and the producers never branch
+// on a wait's outcome, so every producer reaches every producer barrier.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "mtp_common.cuh"

@@ -6,15 +6,17 @@
 // (small cells are visited several times with different image shifts).  Distances are first
 // taken in float from bin-local coordinates as a prefilter; pairs within 1e-3 Angstrom of the
 // cutoff are decided in double precision with the fixed operation order documented in mtp.h, so
-// the lists are identical to a brute-force double-precision search.  One block handles one bin at a
-// time: the atoms of the surrounding bins are staged once in shared memory and every warp tests
-// them for one atom of the bin, compacting the accepted pairs with a ballot.  Each lane then
-// computes r_ij of one accepted pair: exactly in double precision for the double path, and in
-// double-float arithmetic (error-free float transformations, ~2^-44 relative) rounded once to
-// float for the float path.  Double-precision instructions are few and never divergent: on this
-// part a warp-wide double-precision instruction costs many times a float one.  Accepted pairs are
-// rank-sorted by (j, s) and written in slot-major layout.  A last kernel records, for every pair,
-// the slot of the reverse pair in the neighbour's list (used by the deterministic force gather).
+// the lists are identical to a brute-force double-precision search.  The cell lists of a batch are
+// built by one cooperative launch (phases separated by bounded grid barriers).  One block of the
+// list kernel handles one bin at a time: the atoms of the surrounding bins are staged once in
+// shared memory and every warp tests them for one atom of the bin, compacting the accepted pairs
+// with a ballot.  The accepted keys are rank-sorted by (j, s); in the same pass each lane forms r_ij
+// of its keys, exactly in double precision for the double path and in double-float arithmetic
+// (error-free float transformations, ~2^-44 relative) rounded once to float for the float path, and
+// writes the pair record (r_ij and j | species << 24) in slot-major layout.  Double-precision
+// instructions are few and never divergent: on this part a warp-wide double-precision instruction
+// costs many times a float one.  A last kernel records, for every pair, the slot of the reverse
+// pair in the neighbour's list (used by the deterministic force gather).
 #include <algorithm>
 #include "mtp_internal.h"
 #include "mtp_common.cuh"
