@@ -940,9 +940,11 @@ int eval_all(const EvalCtx<T>& a, cudaStream_t st, int n_sm, cudaEvent_t* marks,
 #if MTPGEN_HAS_PARTS
     if constexpr (sizeof(T) == 4) {
         const int threads = 128;
+        // one warp per (part, tile) item and no grid-stride: the blocks resident at any time are a
+        // window of consecutive part-major items, so an SM mostly runs one part's code (the parts are
+        // long straight-line programs and their instruction fetch bounds the kernel otherwise)
         const long warps = (long)((a.n_atoms + 31) / 32) * G::NPART_;
-        int blocks = (int)((warps + 3) / 4);
-        if (blocks > n_sm * 16) blocks = n_sm * 16;
+        const int blocks = (int)((warps + 3) / 4);
         launch_pdl(k_contract_parts, blocks, threads, 0, st, a);
         ++launches;
         if (a.b_rows) {  // the caller provides per-atom rows whenever b rows are requested
@@ -1449,8 +1451,7 @@ int grad_all(EvalCtx<T>& a, const LossArgs& L, cudaStream_t st, int n_sm) {
 #if MTPGEN_HAS_PARTS
     if constexpr (sizeof(T) == 4) {
         const int n_tiles = (a.n_atoms + 31) / 32;
-        int blocks = (int)(((long)n_tiles * G::NDPART_ + 3) / 4);
-        if (blocks > n_sm * 16) blocks = n_sm * 16;
+        const int blocks = (int)(((long)n_tiles * G::NDPART_ + 3) / 4);  // as for k_contract_parts
         k_contract_tan_parts<<<blocks, 128, 0, st>>>(a);
         int sblocks = (int)(((long)n_tiles * G::C_ + 3) / 4);
         if (sblocks > n_sm * 32) sblocks = n_sm * 32;
