@@ -223,6 +223,26 @@ __device__ __forceinline__ uint32_t bf16_bits(int d) {
     return __float_as_uint(f) >> 16;
 }
 
+// The digits of two elements as BF16 pairs: word s holds digit s of T0 (low half) and of T1 (high
+// half).  The digit's bias is folded into the exponent trick: the float with the bits
+// 0x4B400000 - 64 + u (u an unsigned base-128 digit of U, as in base128_digits) is 1.5 2^23 + u - 64,
+// so subtracting 1.5 2^23 leaves the balanced digit exactly, and its BF16 is the upper half of its
+// bits (one byte permutation packs two of them).
+__device__ __forceinline__ void digit_pair_words(long long T0, long long T1, uint32_t* w) {
+    constexpr long long kBias = 64ll * ((1ll << 56) - 1) / 127;
+    const unsigned long long U0 = (unsigned long long)(T0 + kBias), U1 = (unsigned long long)(T1 + kBias);
+    const unsigned lo0 = (unsigned)(U0 & ((1ull << 28) - 1)), lo1 = (unsigned)(U1 & ((1ull << 28) - 1));
+    const unsigned hi0 = (unsigned)(U0 >> 28), hi1 = (unsigned)(U1 >> 28);
+    auto bits = [](unsigned u) { return __float_as_uint(__uint_as_float(0x4B400000u - 64u + u) - 12582912.0f); };
+#pragma unroll
+    for (int s = 4; s < 8; ++s)
+        w[s] = __byte_perm(bits((lo0 >> (7 * (7 - s))) & 127u), bits((lo1 >> (7 * (7 - s))) & 127u), 0x7632);
+#pragma unroll
+    for (int s = 1; s < 4; ++s)
+        w[s] = __byte_perm(bits((hi0 >> (7 * (3 - s))) & 127u), bits((hi1 >> (7 * (3 - s))) & 127u), 0x7632);
+    w[0] = __byte_perm(bits(hi0 >> 21), bits(hi1 >> 21), 0x7632);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Preparation once per active set: column exponents e_k of D, column scales F_j of G = (A D)^-1 and
 // the digit planes of G in the layout of the MMA's A operand:
@@ -465,11 +485,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_grade_tc(const TcArgs a) {
                     for (int e = 0; e < 8; ++e) x[e] = (r < a.n && k0 + e < a.m) ? brow[k0 + e] : 0.0;
 #pragma unroll
                     for (int e = 0; e < 8; e += 2) {
-                        int q0[kDigits], q1[kDigits];
-                        base128_digits(fixed_point(x[e], 56 - E + s_ek[k0 + e]), q0);
-                        base128_digits(fixed_point(x[e + 1], 56 - E + s_ek[k0 + e + 1]), q1);
+                        uint32_t pw[kDigits];
+                        digit_pair_words(fixed_point(x[e], 56 - E + s_ek[k0 + e]),
+                                         fixed_point(x[e + 1], 56 - E + s_ek[k0 + e + 1]), pw);
 #pragma unroll
-                        for (int q = 0; q < kDigits; ++q) w[q][e >> 1] = bf16_bits(q0[q]) | (bf16_bits(q1[q]) << 16);
+                        for (int q = 0; q < kDigits; ++q) w[q][e >> 1] = pw[q];
                     }
                     const int off = plane_off(rr, kg * 8);
 #pragma unroll
