@@ -4,6 +4,8 @@ MaxVol, against what the algorithm fixes:
 * rows of the active set have c = e_j, so their grade is exactly 1;
 * after MaxVol no row of B has |c_j| > 1 + tol (dominance), so no single swap grows |det A|;
 * on tiny matrices, brute force over all single swaps confirms a local maximum of |det A|;
+* the swap threshold 1 + 1e-3 gives up no |det A| on well-conditioned rows: the selection equals
+  the one at 1 + 1e-9;
 * grades and the selection are invariant to column scaling of B (A -> A D);
 * the interpolation identity: xi with A xi = (E_1..E_m) gives E(cfg) = sum_j c_j E(cfg_j).
 Loss:
@@ -55,6 +57,18 @@ def test_active_rows_have_unit_grade_and_dominance():
     gr = maxvol.grades(B, A)
     np.testing.assert_allclose(gr[sel], 1.0, atol=1e-9)
     assert swaps > 0
+
+
+@pytest.mark.parametrize("K,m,seed", [(34, 17, 1), (200, 17, 2), (232, 116, 3), (500, 60, 5)])
+def test_loose_threshold_keeps_the_determinant(K, m, seed):
+    # at the end of MaxVol any single swap could raise |det A| by at most 1 + tol; on these rows the
+    # threshold of the library (1e-3) and a tight one (1e-9) stop at the same rows
+    B = _tall(K, m, seed, scales=10.0 ** np.linspace(-3, 6, m))
+    loose, _, _ = maxvol.maxvol(B, tol=1e-3)
+    tight, _, g = maxvol.maxvol(B, tol=1e-9)
+    assert g <= 1 + 1e-9
+    assert loose.tolist() == tight.tolist()
+    assert np.linalg.slogdet(B[loose])[1] == np.linalg.slogdet(B[tight])[1]
 
 
 @pytest.mark.parametrize("K,m,seed", [(6, 2, 0), (8, 3, 1), (10, 4, 2), (9, 2, 3)])
