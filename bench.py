@@ -50,18 +50,22 @@ def parse():
                     help="only the timed FP32 steps (for ncu launch lists); prints the bench line without the "
                          "FP64, end-to-end, sub-workload and CPU legs")
     ap.add_argument("--no-sub", action="store_true", help="skip the batched and lev_max-20 sub-records")
+    ap.add_argument("--lanes", default="",
+                    help="lanes per atom of the pair kernels as 'moments,pairs' instead of the autotuned choice "
+                         "(for launch lists under ncu, where the autotuner's timings are distorted)")
     return ap.parse_args()
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a kernel on the headline
-# workload, from one ncu capture of the current kernel (profiles/); None when not captured since the
-# kernel last changed.  The neighbour phase's entry adds its two launches: the cell lists (k_bin_all,
-# 498,176 B) and the list kernel (k_build, 1,428,992 + 296,960 B).
-TRAFFIC = {"k_build": 2224128, "k_pairgrad": None, "k_moments": None, "k_contract_parts": None, "k_gather": None}
+# workload, from one ncu capture of the current kernel (profiles/); None when
+# not captured since the kernel last changed.  The neighbour phase's entry adds its two launches: the
+# cell lists (k_bin_all, 497,920 B) and the list kernel (k_build, 1,463,808 + 329,728 B).
+TRAFFIC = {"k_build": 2291456, "k_pairgrad": 30838272, "k_moments": 12659968, "k_contract_parts": 8654080,
+           "k_gather": 29120000}
 # DRAM bytes per row of the tensor-core grade (rows of 116 doubles read once, one grade written), from
-# one ncu capture of the current kernel at 200,000 rows (profiles/); None when not captured since the
-# kernel last changed
-TC_TRAFFIC_PER_ROW = None
+# one ncu capture of the current kernel at 200,000 rows (profiles/); None when
+# not captured since the kernel last changed
+TC_TRAFFIC_PER_ROW = 958.3872
 PHASE_KERNEL = {"neighbors": "k_build", "moments": "k_moments", "contract": "k_contract_parts",
                 "pairgrad": "k_pairgrad", "gather": "k_gather"}
 
@@ -171,7 +175,11 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     # lanes per atom of the pair kernels for this size class, chosen by the library's autotuner
-    tuned = model.autotune(pos, types, cells, off)[:2]
+    if args.lanes:
+        tuned = tuple(int(v) for v in args.lanes.split(","))
+        model.set_threads_per_atom(*tuned)
+    else:
+        tuned = model.autotune(pos, types, cells, off)[:2]
 
     outs = {}
 
