@@ -547,6 +547,20 @@ def slices(prog: Program, max_comps):
     return [(g, [i for m in g for i in by_mono[m]]) for g in groups]
 
 
+def moment_slices(prog: Program, max_comps):
+    """Slices of the float moments kernel: as few as slices(prog, max_comps) gives, with their sizes
+    balanced (the largest slice sets the running sums held per thread, hence the registers and the
+    resident warps of the kernel).  The pair-gradient and tangent kernels keep slices(prog,
+    max_comps)."""
+    n = len(slices(prog, max_comps))
+    C = len(prog.comp_list)
+    for cap in range(-(-C // n), max_comps + 1):
+        s = slices(prog, cap)
+        if len(s) == n:
+            return s
+    return slices(prog, max_comps)
+
+
 def _mono_name(m):
     return "m%d_%d_%d" % m
 
@@ -652,16 +666,34 @@ def _grad_terms_folded(monos, by_m):
     return decl + body + fin
 
 
+def _mom_function(prog: Program, monos, comps):
+    """mom(x, y, z, f, acc) of one slice: acc[t] += f[mu] x^a y^b z^c for its components (Eq. 5 for
+    one neighbour)."""
+    out = ["  template <class T> static __device__ __forceinline__ void mom(const T x, const T y, const T z, "
+           "const T* __restrict__ f, T* __restrict__ acc) {"]
+    out += ["    " + l for l in _mono_code(_closure(monos), "T")]
+    for t, ci in enumerate(comps):
+        mu, m = prog.comp_list[ci]
+        mv = "T(1)" if m == (0, 0, 0) else _mono_name(m)
+        out.append(f"    acc[{t}] += f[{mu}] * {mv};")
+    out.append("  }")
+    return out
+
+
 def emit_slice_functions(prog: Program, slc, tag, slot_begin=None):
     """Specialisations Slice<tag><S> for every slice S (a list of (monomials, component indices)):
        mom(x,y,z,f,acc):   acc[t] += f[mu] * x^a y^b z^c                    (moments, Sec. 2.1)
        grad(x,y,z,f,df,adj,s,gx,gy,gz):
              s += sum adj * df[mu] * mono;  g += sum adj * f[mu] * grad(mono)   (adjoint)"""
-    name = "SliceF" if tag == "f" else "SliceD"
+    name = {"f": "SliceF", "d": "SliceD", "mf": "SliceMF"}[tag]
     out = [f"template <int S> struct {name};"]
     for si, (monos, comps) in enumerate(slc):
         out.append(f"template <> struct {name}<{si}> {{")
         out.append(f"  static constexpr int BEGIN = {min(comps)}, SIZE = {len(comps)};")
+        if tag == "mf":  # the moments kernel's slices: the accumulation alone
+            out += _mom_function(prog, monos, comps)
+            out.append("};")
+            continue
         if slot_begin is not None:
             # dV/dM of this slice's components: the contraction parts' slots summed in slot
             # order, written to shared memory in groups of four components (one 16-byte vector
@@ -677,15 +709,7 @@ def emit_slice_functions(prog: Program, slc, tag, slot_begin=None):
                 # count); with four or more lanes per atom a lane's share is small and needs none
                 out.append(f'    if (TPA <= 2 && {t + 1} % (16 * TPA) == 0) asm volatile("" ::: "memory");')
             out.append("  }")
-        need = _closure(monos)
-        out.append("  template <class T> static __device__ __forceinline__ void mom(const T x, const T y, const T z, "
-                   "const T* __restrict__ f, T* __restrict__ acc) {")
-        out += ["    " + l for l in _mono_code(need, "T")]
-        for t, ci in enumerate(comps):
-            mu, m = prog.comp_list[ci]
-            mv = "T(1)" if m == (0, 0, 0) else _mono_name(m)
-            out.append(f"    acc[{t}] += f[{mu}] * {mv};")
-        out.append("  }")
+        out += _mom_function(prog, monos, comps)
         # adjoint of one pair: P_mu = sum_m adj[mu,m] m gives the radial part s = sum_mu df_mu P_mu;
         # alpha_m = sum_mu adj[mu,m] f_mu times the gradient of each monomial gives the rest
         grads = set()
@@ -1023,6 +1047,7 @@ def emit_level(L, outdir):
     assert V < 65535
     table = level_table(prog.basis)
     s32 = slices(prog, SLICE_F32)
+    sm32 = moment_slices(prog, SLICE_F32)
     s64 = slices(prog, SLICE_F64)
     fl = flop_counts(prog)
     tag = f"L{L}"
@@ -1030,7 +1055,8 @@ def emit_level(L, outdir):
              "#pragma once", "#include \"mtp_gen_common.h\"", f"namespace mtpgen_{tag} {{"]
     lines.append(f"constexpr int L = {L}, C = {C}, V = {V}, M = {prog.basis.m}, NMU = {prog.n_mu}, "
                  f"NUMAX = {prog.numax};")
-    lines.append(f"constexpr int NS32 = {len(s32)}, NS64 = {len(s64)}, MAXS32 = {max(len(c) for _, c in s32)};")
+    lines.append(f"constexpr int NS32 = {len(s32)}, NS64 = {len(s64)}, MAXS32 = {max(len(c) for _, c in s32)}, "
+                 f"NSM32 = {len(sm32)};")
     lines.append(f"constexpr int FWD_ROWS = {len(fwd_rows)}, ADJ_ROWS = {len(adj_rows)};")
     lines.append(f"constexpr int FWD_LAYERS = {len(fwd_layers)}, ADJ_LAYERS = {len(adj_layers)};")
     lines.append(f"constexpr int PROGRAM_OPS = {len(prog.ops)};")
@@ -1085,14 +1111,16 @@ def emit_level(L, outdir):
         lines.append("#define MTPGEN_HAS_PARTS 0")
     lines += emit_slice_functions(prog, s32, "f", slot_begin if has_parts else None)
     lines += emit_slice_functions(prog, s64, "d")
+    lines += emit_slice_functions(prog, sm32, "mf")
     lines.append("struct Traits {")
     lines.append("  static constexpr int L_ = L, C_ = C, V_ = V, M_ = M, NMU_ = NMU, NUMAX_ = NUMAX, NS32_ = NS32, NS64_ = NS64, "
-                 "MAXS32_ = MAXS32;")
+                 "MAXS32_ = MAXS32, NSM32_ = NSM32;")
     lines.append(f"  static constexpr int NPART_ = {nparts}, NSLOT_ = {max(nslots, 1)};")
     lines.append(f"  static constexpr bool HAS_PARTS_ = {'true' if has_parts else 'false'};")
     lines.append(f"  static constexpr int NDPART_ = {ndparts}, NDSLOT_ = {max(ndslots, 1)};")
     lines.append("  template <int S> using F32 = SliceF<S>;")
     lines.append("  template <int S> using F64 = SliceD<S>;")
+    lines.append("  template <int S> using MF32 = SliceMF<S>;")
     lines.append("};")
     lines.append(f"}}  // namespace mtpgen_{tag}")
     path = os.path.join(outdir, f"mtp_gen_{tag}.h")

@@ -42,6 +42,28 @@ template <>
 struct NumSlices<double> {
     static constexpr int value = G::NS64_;
 };
+// slices of the moments kernel: in float as many as above with balanced sizes (the largest slice
+// sets the running sums a thread holds), in double the same as above
+template <class T, int S>
+struct MomSliceSel;
+template <int S>
+struct MomSliceSel<float, S> {
+    using type = typename G::template MF32<S>;
+};
+template <int S>
+struct MomSliceSel<double, S> {
+    using type = typename G::template F64<S>;
+};
+template <class T>
+struct NumMomSlices;
+template <>
+struct NumMomSlices<float> {
+    static constexpr int value = G::NSM32_;
+};
+template <>
+struct NumMomSlices<double> {
+    static constexpr int value = G::NS64_;
+};
 
 __device__ __forceinline__ int clamp_species(int z, int S) { return z < 0 ? 0 : (z >= S ? S - 1 : z); }
 __device__ __forceinline__ float my_sqrt(float x) { return sqrtf(x); }
@@ -264,7 +286,7 @@ __device__ __forceinline__ PairIn<T> load_pair(const EvalCtx<T>& a, size_t idx) 
 template <class T, int S, int TPA>
 __device__ __forceinline__ void moments_slice(const EvalCtx<T>& a, int i, int sub, bool active, int zi, int cnt,
                                               const T* cs) {
-    using SL = typename SliceSel<T, S>::type;
+    using SL = typename MomSliceSel<T, S>::type;
     T acc[SL::SIZE];
 #pragma unroll
     for (int t = 0; t < SL::SIZE; ++t) acc[t] = T(0);
@@ -345,7 +367,7 @@ __global__ void __launch_bounds__(128) k_moments(const EvalCtx<T> a) {
             zi = clamp_species(a.types[i], a.S);  // out-of-range species are reported by the neighbour build
             cnt = a.count[i];
         }
-        moments_all<T, 0, NumSlices<T>::value, TPA>(a, i, sub, active, zi, cnt, cs);
+        moments_all<T, 0, NumMomSlices<T>::value, TPA>(a, i, sub, active, zi, cnt, cs);
     }
 }
 

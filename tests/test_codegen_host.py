@@ -211,3 +211,44 @@ def test_pdot_is_the_monomial_sum_and_its_tangent(L, tmp_path):
         h = 1e-5
         num = P_of(v, adjt) + (P_of(v + h * u, adj) - P_of(v - h * u, adj)) / (2 * h)
         assert np.abs(Pd - num).max() <= 1e-6 * max(np.abs(num).max(), 1e-300), (L, k)
+
+
+@pytest.mark.parametrize("L", [16, 18, 20])
+def test_moment_slices_accumulate_the_same_components(L, tmp_path):
+    """The float moments kernel has its own slicing (as many slices, sizes balanced); concatenated,
+    its slices accumulate exactly the components of the other kernels' slices, in storage order."""
+    prog = codegen.build_program(L)
+    s32 = codegen.slices(prog, codegen.SLICE_F32)
+    sm32 = codegen.moment_slices(prog, codegen.SLICE_F32)
+    assert len(sm32) == len(s32)
+    assert [i for _, c in sm32 for i in c] == list(range(len(prog.comp_list)))
+    assert max(len(c) for _, c in sm32) <= max(len(c) for _, c in s32)
+    lines = codegen.emit_slice_functions(prog, s32, "f") + codegen.emit_slice_functions(prog, sm32, "mf")
+    src = ["#define __device__", "#define __forceinline__ inline", "namespace gen {"] + lines + ["}"]
+    for name, slc in (("f", s32), ("mf", sm32)):
+        tag = "SliceF" if name == "f" else "SliceMF"
+        src.append(f'extern "C" void all_{name}(double x, double y, double z, const double* f, double* acc) {{')
+        for k, (_, comps) in enumerate(slc):
+            src.append(f"  gen::{tag}<{k}>::mom<double>(x, y, z, f, acc + {min(comps)});")
+        src.append("}")
+    cpp = tmp_path / f"mslices_L{L}.cpp"
+    so = tmp_path / f"mslices_L{L}.so"
+    cpp.write_text("\n".join(src) + "\n")
+    subprocess.run(["g++", "-O1", "-shared", "-fPIC", "-o", str(so), str(cpp)], check=True)
+    lib = ctypes.CDLL(str(so))
+    d = ctypes.c_double
+    p = ctypes.POINTER(ctypes.c_double)
+    lib.all_f.argtypes = lib.all_mf.argtypes = [d, d, d, p, p]
+    rng = np.random.default_rng(L)
+    C = len(prog.comp_list)
+    for _ in range(4):
+        v = rng.standard_normal(3) * 1.9
+        f = np.ascontiguousarray(rng.standard_normal(prog.n_mu))
+        a = np.zeros(C)
+        b = np.zeros(C)
+        lib.all_f(v[0], v[1], v[2], _ptr(f), _ptr(a))
+        lib.all_mf(v[0], v[1], v[2], _ptr(f), _ptr(b))
+        assert np.array_equal(a, b)
+        # and each component is f_mu x^a y^b z^c
+        ref = np.array([f[mu] * v[0] ** m[0] * v[1] ** m[1] * v[2] ** m[2] for mu, m in prog.comp_list])
+        np.testing.assert_allclose(b, ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
