@@ -697,13 +697,15 @@ def emit_slice_functions(prog: Program, slc, tag, slot_begin=None):
         if slot_begin is not None:
             # dV/dM of this slice's components: the contraction parts' slots summed in slot
             # order, written to shared memory in groups of four components (one 16-byte vector
-            # per group and atom, groups NS vectors apart), component t by the lane with
-            # t % TPA == sub of the atom's TPA lanes
-            out.append("  template <class T, int TPA, int NS> static __device__ __forceinline__ void adj_to_shared("
-                       "const T* __restrict__ sl, T* __restrict__ dst, const int sub) {")
+            # per group and atom, groups NS vectors apart) at position t + OFF (OFF = 0: the
+            # slice alone; OFF = BEGIN: every slice of the atom in one array), component t by the
+            # lane with t % TPA == sub of the atom's TPA lanes
+            out.append("  template <class T, int TPA, int NS, int OFF = 0> static __device__ __forceinline__ void "
+                       "adj_to_shared(const T* __restrict__ sl, T* __restrict__ dst, const int sub) {")
             for t, ci in enumerate(comps):
                 terms = [f"sl[{s * 32}]" for s in range(slot_begin[ci], slot_begin[ci + 1])] or ["T(0)"]
-                out.append(f"    if ({t} % TPA == sub) dst[{(t // 4) * 4} * NS + {t % 4}] = " + " + ".join(terms) + ";")
+                out.append(f"    if ({t} % TPA == sub) dst[(({t} + OFF) / 4) * 4 * NS + ({t} + OFF) % 4] = "
+                           + " + ".join(terms) + ";")
                 # a compiler fence after every 16 components of this lane: the loads of one group
                 # are in flight together, not all of them (their registers would set the kernel's
                 # count); with four or more lanes per atom a lane's share is small and needs none

@@ -573,12 +573,12 @@ __global__ void k_brows(const EvalCtx<T> a, const int* cfg_off) {
 // ----------------------------------------------------------------------------------------------
 // dV/dM of one atom held in shared memory: components 4k .. 4k+3 in the vector q[k * NS] (NS atoms
 // per block); repeated reads of one vector are merged by the compiler (no stores in between)
-template <class T, int NS>
+template <class T, int NS, int OFF = 0>
 struct SharedAdj {
     const Vec4<T>* q;
     __device__ __forceinline__ T operator[](int t) const {
-        const Vec4<T> v = q[(t >> 2) * NS];
-        const int c = t & 3;
+        const Vec4<T> v = q[((t + OFF) >> 2) * NS];
+        const int c = (t + OFF) & 3;
         return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
     }
 };
@@ -595,9 +595,19 @@ struct PairgradShared {
 #endif
 };
 
+// With two or more lanes per atom (PairgradMerged) dV/dM of every slice of an atom sits in shared
+// memory at once and each pair is visited once: its record, radial functions and gradient store are
+// not repeated per slice.  With one lane per atom a block holds 128 atoms and that array would not
+// fit beside the coefficients at the largest sizes, so the slices take turns.
+template <class T, int TPA>
+struct PairgradMerged {
+    static constexpr bool value = PairgradShared<T>::value && TPA >= 2 && NumSlices<T>::value > 1;
+};
+
 template <class T, int TPA>
 constexpr size_t pairgrad_adj_bytes() {
-    return PairgradShared<T>::value ? sizeof(T) * (size_t)((G::MAXS32_ + 3) / 4 * 4) * (128 / TPA) : 0;
+    return !PairgradShared<T>::value ? 0
+           : sizeof(T) * (size_t)(((PairgradMerged<T, TPA>::value ? G::C_ : G::MAXS32_) + 3) / 4 * 4) * (128 / TPA);
 }
 
 template <class T, int S, int TPA, class A>
@@ -659,6 +669,60 @@ __device__ __forceinline__ void pairgrad_slice(const EvalCtx<T>& a, int i, int s
     pairgrad_pairs<T, S, TPA>(a, i, sub, zi, cnt, cs, adjs);
 }
 
+#if MTPGEN_HAS_PARTS
+// dV/dM of every slice of the atom into its shared array, at the components' positions
+template <class T, int S, int TPA, int NSA>
+__device__ __forceinline__ void adj_all_to_shared(const T* sl, T* mine, int sub) {
+    if constexpr (S < NumSlices<T>::value) {
+        using SL = typename SliceSel<T, S>::type;
+        SL::template adj_to_shared<T, TPA, NSA, SL::BEGIN>(sl, mine, sub);
+        adj_all_to_shared<T, S + 1, TPA, NSA>(sl, mine, sub);
+    }
+}
+
+// the adjoint terms of every slice for one pair
+template <class T, int S, int NSA>
+__device__ __forceinline__ void grad_all_slices(const T x, const T y, const T z, const T* f, const T* df,
+                                                const Vec4<T>* q, T& s, T& gx, T& gy, T& gz) {
+    if constexpr (S < NumSlices<T>::value) {
+        using SL = typename SliceSel<T, S>::type;
+        SL::template grad<T>(x, y, z, f, df, SharedAdj<T, NSA, SL::BEGIN>{q}, s, gx, gy, gz);
+        grad_all_slices<T, S + 1, NSA>(x, y, z, f, df, q, s, gx, gy, gz);
+    }
+}
+
+// every pair of the atom once, with all slices' adjoint terms (PairgradMerged)
+template <class T, int TPA>
+__device__ __forceinline__ void pairgrad_merged(const EvalCtx<T>& a, int i, int sub, bool active, int zi, int cnt,
+                                                const T* cs, T* sadj) {
+    constexpr int NSA = 128 / TPA;
+    T* mine = sadj + 4 * (threadIdx.x / TPA);
+    __syncwarp();  // the atom's lanes are done with the previous atom
+    if (active)
+        adj_all_to_shared<T, 0, TPA, NSA>(a.aslots + (size_t)(i >> 5) * G::NSLOT_ * 32 + (i & 31), mine, sub);
+    __syncwarp();
+    const Vec4<T>* q = reinterpret_cast<const Vec4<T>*>(mine);
+    const size_t n = (size_t)a.n_atoms;
+    const int csz = coef_row(a);
+    PairIn<T> nx{};
+    if (sub < cnt) nx = load_pair(a, (size_t)sub * n + i);
+#pragma unroll 1
+    for (int p = sub; p < cnt; p += TPA) {
+        const size_t idx = (size_t)p * n + i;
+        const PairIn<T> cur = nx;
+        if (p + TPA < cnt) nx = load_pair(a, (size_t)(p + TPA) * n + i);
+        const T x = cur.x, y = cur.y, z = cur.z;
+        const T r = my_sqrt(x * x + y * y + z * z);
+        T f[G::NMU_], df[G::NMU_];
+        radial<T, true>(r, cs + (zi * a.S + cur.zj) * csz, a.NQ, a.rmin, a.rcut, a.inv_span, f, df);
+        T s = T(0), gx = T(0), gy = T(0), gz = T(0);
+        grad_all_slices<T, 0, NSA>(x, y, z, f, df, q, s, gx, gy, gz);
+        const T sr = s / r;
+        a.g[idx] = Vec4<T>{gx + sr * x, gy + sr * y, gz + sr * z, T(0)};
+    }
+}
+#endif
+
 template <class T, int S, int NS, int TPA>
 __device__ __forceinline__ void pairgrad_all(const EvalCtx<T>& a, int i, int sub, bool active, int zi, int cnt,
                                              const T* cs, T* sadj) {
@@ -691,6 +755,12 @@ __global__ void __launch_bounds__(128) k_pairgrad(const EvalCtx<T> a) {
             zi = clamp_species(a.types[i], a.S);
             cnt = a.count[i];
         }
+#if MTPGEN_HAS_PARTS
+        if constexpr (PairgradMerged<T, TPA>::value) {
+            pairgrad_merged<T, TPA>(a, i, sub, active, zi, cnt, cs, sadj);
+            continue;
+        }
+#endif
         pairgrad_all<T, 0, NumSlices<T>::value, TPA>(a, i, sub, active, zi, cnt, cs, sadj);
     }
 }
