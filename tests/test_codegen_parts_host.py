@@ -219,3 +219,65 @@ def test_dual_parts_are_the_tangent_contraction(L, parts, tmp_path):
     _, fl = _build(L, codegen.CONTRACT_PARTS[L], tmp_path)
     _, _, adj_f = _run(fl, prog, codegen.CONTRACT_PARTS[L], m_tile, xi)
     np.testing.assert_allclose(adj, adj_f, rtol=1e-12, atol=1e-12 * np.abs(adj_f).max())
+
+
+@pytest.mark.parametrize("L,lanes", [(18, 2), (20, 2), (20, 8), (16, 4)])
+def test_adjoint_slots_into_shared_arrays(L, lanes, tmp_path):
+    """The pair-gradient kernel gathers dV/dM of an atom from the contraction parts' slots into shared
+    memory: per slice (OFF = 0, positions 0 .. SIZE-1) or, for all slices at once, at the components'
+    own positions (OFF = BEGIN).  Both give every component the sum of its slots, in vectors of four
+    components NS atoms apart, each written by exactly one of the atom's lanes."""
+    prog = codegen.build_program(L)
+    parts = codegen.CONTRACT_PARTS[L]
+    part_lines = codegen.emit_parts(prog, parts)
+    slot_begin = [int(x) for x in part_lines[2].split("{")[1].rstrip("};").split(",")]
+    slc = codegen.slices(prog, codegen.SLICE_F32)
+    lines = codegen.emit_slice_functions(prog, slc, "f", slot_begin)
+    NS = 128 // lanes
+    C = len(prog.comp_list)
+    src = ["#define __device__", "#define __forceinline__ inline", "namespace gen {"] + lines + ["}"]
+    src.append('extern "C" void gather(int merged, int k, int sub, const double* sl, double* dst) {')
+    src.append("  switch (k) {")
+    for k, (_, comps) in enumerate(slc):
+        off = f"gen::SliceF<{k}>::BEGIN"
+        src.append(f"    case {k}: if (merged) gen::SliceF<{k}>::adj_to_shared<double, {lanes}, {NS}, {off}>(sl, dst, sub);"
+                   f" else gen::SliceF<{k}>::adj_to_shared<double, {lanes}, {NS}>(sl, dst, sub); break;")
+    src.append("  }")
+    src.append("}")
+    cpp = tmp_path / f"adjsh_L{L}.cpp"
+    so = tmp_path / f"adjsh_L{L}.so"
+    cpp.write_text("\n".join(src) + "\n")
+    subprocess.run(["g++", "-O1", "-shared", "-fPIC", "-o", str(so), str(cpp)], check=True)
+    lib = ctypes.CDLL(str(so))
+    p = ctypes.POINTER(ctypes.c_double)
+    lib.gather.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p]
+    rng = np.random.default_rng(L + lanes)
+    nslot = slot_begin[-1]
+    sl = np.zeros(nslot * 32)
+    sl[::32] = rng.standard_normal(nslot)  # this atom's slots (tile stride 32)
+    want = np.array([sl[[s * 32 for s in range(slot_begin[c], slot_begin[c + 1])]].sum() for c in range(C)])
+
+    def at(pos):  # element of component position pos in the atom's strided vectors
+        return (pos // 4) * 4 * NS + pos % 4
+
+    size = ((C + 3) // 4) * 4 * NS
+    merged = np.full(size, np.nan)
+    for k, (_, comps) in enumerate(slc):
+        per = np.full(((len(comps) + 3) // 4) * 4 * NS, np.nan)
+        for sub in range(lanes):
+            lib.gather(0, k, sub, sl.ctypes.data_as(p), per.ctypes.data_as(p))
+            lib.gather(1, k, sub, sl.ctypes.data_as(p), merged.ctypes.data_as(p))
+        got = np.array([per[at(t)] for t in range(len(comps))])
+        np.testing.assert_allclose(got, want[comps], rtol=1e-13, atol=0)
+    np.testing.assert_allclose(np.array([merged[at(c)] for c in range(C)]), want, rtol=1e-13, atol=0)
+    # nothing written outside the components' positions (other atoms' vectors stay untouched)
+    touched = {at(c) for c in range(C)}
+    assert all(np.isnan(merged[i]) for i in range(size) if i not in touched)
+    # each position by exactly one lane of the atom
+    written = []
+    for sub in range(lanes):
+        one = np.full(size, np.nan)
+        for k in range(len(slc)):
+            lib.gather(1, k, sub, sl.ctypes.data_as(p), one.ctypes.data_as(p))
+        written.append(set(np.flatnonzero(~np.isnan(one)).tolist()))
+    assert sum(len(w) for w in written) == C and set().union(*written) == touched
